@@ -1,0 +1,161 @@
+"""Pins for the oracle's DG operator (Sec. II, Eqs. dg_op_auxvars, dg_op_primal, numflux,
+penalty, bc) against facts fixed by the mathematics, not by the oracle itself."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import sympy as sp
+
+import workloads
+from oracle import dg, lgl
+
+
+def _box(n, N, C=1.5, lower=(-1.0,) * 3, upper=(1.0,) * 3):
+    return dg.BoxGrid(tuple(lower), tuple(upper), tuple(n), N, C)
+
+
+def sipg_matrix(grid: dg.BoxGrid) -> np.ndarray:
+    """Independent brute-force assembly of the symmetric interior-penalty bilinear form
+    a(w,u) = sum_K (grad w, grad u)_K - sum_F ({d_n w}[u] + {d_n u}[w])_F + sum_F (sigma_F [w][u])_F
+    with LGL quadrature, sigma_F = C N^2 / h_perp on interior faces and 2 C N^2 / h_perp on
+    Dirichlet faces (the mirror ghost of Eq. bc doubles the jump). Summation by parts on LGL
+    points turns the paper's strong form into exactly this form."""
+    N, E = grid.N, grid.n_elements
+    x, w = lgl.lgl_nodes(N), lgl.lgl_weights(N)
+    Dh = lgl.diff_matrix(N)
+    I = np.eye(N)
+    h = grid.h
+    n3 = N**3
+    G1 = [np.kron(np.kron(I, I), Dh), np.kron(np.kron(I, Dh), I), np.kron(np.kron(Dh, I), I)]  # x, y, z
+    W3 = np.kron(np.kron(w, w), w)  # [k, j, i]
+    J = np.prod(h) / 8
+    ndof = E * n3
+    A = np.zeros((ndof, ndof))
+
+    def blk(e):
+        return slice(e * n3, (e + 1) * n3)
+
+    G = [2.0 / h[d] * G1[d] for d in range(3)]
+    for e in range(E):
+        for d in range(3):
+            A[blk(e), blk(e)] += G[d].T @ (J * W3[:, None] * G[d])
+    kji = np.array(list(itertools.product(range(N), repeat=3)))  # rows (k, j, i)
+
+    def face_rows(d, side):
+        along = kji[:, 2 - d]
+        return np.nonzero(along == (0 if side == 0 else N - 1))[0]
+
+    sigma = grid.penalty * N**2
+    for e in range(E):
+        for d in range(3):
+            tang = [t for t in range(3) if t != d]
+            Jf = np.prod(h[tang]) / 4
+            for side in (0, 1):
+                rows = face_rows(d, side)
+                tw = np.ones(len(rows))
+                for t in tang:
+                    tw = tw * w[kji[rows, 2 - t]]
+                B = np.diag(Jf * tw)
+                s = 1.0 if side else -1.0
+                q = grid.neighbor(e, 2 * d + side)
+                Te = np.zeros((len(rows), ndof))
+                Te[np.arange(len(rows)), e * n3 + rows] = 1.0
+                dTe = np.zeros((len(rows), ndof))
+                dTe[:, blk(e)] = s * G[d][rows]
+                if q == dg.EXTERNAL:
+                    jump, avg, sig = Te, dTe, 2 * sigma / h[d]
+                elif side == 1:  # count each interior face once, from its lower element
+                    rows_q = face_rows(d, 0)
+                    Tq = np.zeros((len(rows), ndof))
+                    Tq[np.arange(len(rows)), q * n3 + rows_q] = 1.0
+                    dTq = np.zeros((len(rows), ndof))
+                    dTq[:, blk(q)] = s * G[d][rows_q]
+                    jump, avg, sig = Te - Tq, 0.5 * (dTe + dTq), sigma / h[d]
+                else:
+                    continue
+                A += -avg.T @ B @ jump - jump.T @ B @ avg + sig * jump.T @ B @ jump
+    return A
+
+
+@pytest.mark.parametrize("n,N", [((1, 1, 1), 2), ((2, 1, 1), 3), ((2, 2, 1), 3), ((2, 2, 2), 4), ((3, 1, 2), 3)])
+def test_strong_form_equals_sipg_bilinear_form(n, N):
+    grid = _box(n, N, lower=(-1.0, -0.5, 0.0), upper=(1.0, 0.5, 3.0))
+    A = dg.assemble(grid.graph())
+    S = sipg_matrix(grid)
+    assert np.abs(A - S).max() <= 1e-12 * np.abs(S).max()
+
+
+@pytest.mark.parametrize("n,N", [((1, 1, 1), 2), ((2, 2, 2), 3), ((2, 1, 3), 5), ((1, 2, 1), 4)])
+def test_symmetric_positive_definite(n, N):
+    A = dg.assemble(_box(n, N).graph())
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    np.linalg.cholesky(A)  # raises if not positive definite
+
+
+def test_polynomial_consistency():
+    """For u vanishing on the boundary and smooth across faces, every flux difference vanishes and
+    D_hat is exact, so A u = M (-Laplace u) at every node."""
+    X, Y, Z = sp.symbols("x y z")
+    U = (1 - X**2) * (1 - Y**2) * (1 - Z**2) * (1 + sp.Rational(3, 10) * X - sp.Rational(1, 5) * Y * Z)
+    lap = sp.lambdify((X, Y, Z), -(sp.diff(U, X, 2) + sp.diff(U, Y, 2) + sp.diff(U, Z, 2)), "numpy")
+    uf = sp.lambdify((X, Y, Z), U, "numpy")
+    for n, N in [((2, 2, 2), 4), ((3, 2, 1), 5), ((1, 1, 1), 6)]:
+        grid = _box(n, N)
+        gr = grid.graph()
+        x, y, z = grid.coordinates()
+        Au = dg.apply(gr, uf(x, y, z))
+        ref = dg.mass_diag(gr) * lap(x, y, z)
+        assert np.abs(Au - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_matrix_free_equals_dense_on_random_vectors():
+    grid = _box((2, 2, 1), 4)
+    gr = grid.graph()
+    A = dg.assemble(gr)
+    u = workloads.uniform_vector(7, A.shape[0])
+    Au = dg.apply(gr, u.reshape(gr.n_elements, 4, 4, 4)).ravel()
+    assert np.abs(Au - A @ u).max() <= 1e-13 * np.abs(Au).max()
+
+
+def _solve(grid):
+    gr = grid.graph()
+    A = dg.assemble(gr)
+    x, y, z = grid.coordinates()
+    b = dg.rhs(gr, workloads.sine_source_3d(x, y, z)).ravel()
+    u = np.linalg.solve(A, b)
+    return math.sqrt(np.mean((u - workloads.sine_solution_3d(x, y, z).ravel()) ** 2))
+
+
+def test_manufactured_p_convergence():
+    """u = sin(pi x) sin(pi y) sin(pi z), f = 3 pi^2 u: the RMS nodal error decays exponentially in N."""
+    errs = [_solve(_box((1, 1, 1), N)) for N in (4, 6, 8, 10)]
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert min(ratios) > 20  # each +2 in N gains more than a factor 20 ...
+    assert ratios[2] > 0.9 * ratios[0]  # ... and the gain does not shrink (exponential, not algebraic)
+    assert errs[3] < 1e-5
+
+
+def test_manufactured_h_convergence():
+    e1 = _solve(_box((1, 1, 1), 4))
+    e2 = _solve(_box((2, 2, 2), 4))
+    assert e1 / e2 > 2 ** 3.5  # at least ~h^N order at N = 4
+
+
+def test_penalty_enters_only_through_jumps():
+    """A(C1) - A(C2) is a pure jump (penalty) term: it annihilates fields continuous across
+    faces and vanishing on the boundary."""
+    grid1, grid2 = _box((2, 2, 2), 3, C=1.0), _box((2, 2, 2), 3, C=2.5)
+    x, y, z = grid1.coordinates()
+    u = (1 - x**2) * (1 - y**2) * (1 - z**2)
+    d = dg.apply(grid1.graph(), u) - dg.apply(grid2.graph(), u)
+    assert np.abs(d).max() < 1e-13
+    r = workloads.uniform_vector(3, u.size).reshape(u.shape)
+    assert np.abs(dg.apply(grid1.graph(), r) - dg.apply(grid2.graph(), r)).max() > 1e-2
+
+
+def test_scaling_with_element_size():
+    """For cubic elements in 3-D every term of A scales as h: A(h) = h A(1)."""
+    a = dg.assemble(_box((2, 1, 1), 3, lower=(0, 0, 0), upper=(2, 1, 1)).graph())
+    b = dg.assemble(_box((2, 1, 1), 3, lower=(0, 0, 0), upper=(0.5, 0.25, 0.25)).graph())
+    assert np.abs(b - 0.25 * a).max() <= 1e-13 * np.abs(a).max()
