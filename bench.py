@@ -1,0 +1,358 @@
+"""Benchmark: multigrid-Schwarz preconditioned FGMRES solves of the 3-D Poisson problem with a
+16-Gaussian source on [-1,1]^3, 8^3 elements, 8 LGL points per dimension (262,144 points),
+3-level h-multigrid, Schwarz overlap 2, penalty C = 1.5, relative residual 1e-10.
+
+One step = one complete solve from u = 0 (every kernel of the hot path: DG operator, Schwarz
+gather / subdomain-inverse GEMM / weighted scatter on every level, restriction, prolongation,
+FGMRES orthogonalisation). The headline value is solves/s with the FP32 preconditioner under
+FP64 FGMRES; the plain FP64 solver, the DG-apply rate and the per-phase roofline are reported
+beside it. Multi-GPU: independent replicas (one solve stream per GPU, no collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle (test infrastructure) on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG-apply GDOF/s; solves/s & p99 latency at 1e-10 residual, mixed vs FP64"
+WORKLOAD = ("poisson-gauss16-8x8x8-N8: 3-D Poisson on [-1,1]^3, 8^3 elements, N=8 LGL points/dim "
+            "(262,144 DOF), 16 seeded Gaussians (widths U[0.1,0.4]), 3-level h-MG V-cycle, Schwarz overlap 2, "
+            "3+3 smoothing, C=1.5, FGMRES to 1e-10 relative residual from u=0")
+N_CFG, n_CFG, LEVELS = 8, (8, 8, 8), 3
+TOL = 1e-10
+
+# CPU sample of the same workload for the oracle timings: the same problem family on 2^3 elements
+# (4,096 DOF, 2 levels); multigrid-Schwarz iteration counts do not depend on h, so the per-solve
+# work scales with the number of points and the rate is scaled by 4,096 / 262,144.
+SAMPLE_N_ELEMS = (2, 2, 2)
+
+_SAMPLE_SCRIPT = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import workloads
+from oracle import dg, solve
+steps, warm = int(sys.argv[2]), int(sys.argv[3])
+grid = dg.BoxGrid((-1.0,)*3, (1.0,)*3, (2, 2, 2), 8, 1.5)
+pr = solve.Problem(grid, mg_levels=0, overlap=2)
+x, y, z = grid.coordinates()
+b = dg.rhs(pr.graphs[0], workloads.gaussian_source(2)(x, y, z))
+times, its = [], []
+for i in range(warm + steps):
+    t0 = time.perf_counter()
+    u, info = pr.solve_linear(b, tol=1e-10)
+    dt = time.perf_counter() - t0
+    if i >= warm:
+        times.append(dt); its.append(info["iterations"])
+print(json.dumps({"times": times, "iterations": its, "dof": int(b.size)}))
+"""
+
+
+def cpu_sample(steps: int, warm: int):
+    """Time the oracle's multigrid-Schwarz FGMRES solve of the 2^3-element sample in a fresh
+    interpreter with all host cores available to its BLAS."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    out = subprocess.run([sys.executable, "-c", _SAMPLE_SCRIPT, ROOT, str(steps), str(warm)], capture_output=True,
+                         text=True, env=env, check=True)
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    scale = res["dof"] / (n_CFG[0] * n_CFG[1] * n_CFG[2] * N_CFG**3)
+    rates = [scale / t for t in res["times"]]  # config-size solves per second
+    return res, rates, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res, rates, cores = cpu_sample(args.steps, min(args.warmup, 1))
+    total = sum(res["times"])
+    value = len(res["times"]) * (res["dof"] / (n_CFG[0] * n_CFG[1] * n_CFG[2] * N_CFG**3)) / total
+    sample = (f"oracle (numpy FP64) MG-Schwarz FGMRES solve of the same problem on 2^3 elements, N=8 "
+              f"({res['dof']} DOF, {res['iterations'][0]} iterations), subdomain matrices built in an untimed "
+              f"warm-up solve, rate scaled by {res['dof']}/262144 DOF")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(res["times"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([c.strip() for c in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads
+    import paper_2111_06767_gb300 as dgg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        # before the first GPU work: the oracle runs in its own interpreter
+        res, rates, cores = cpu_sample(1, 1)
+        cpu = {"value": rates[0], "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": (f"oracle (numpy FP64) MG-Schwarz FGMRES solve of the same problem on 2^3 elements, N=8 "
+                          f"({res['dof']} DOF, {res['iterations'][0]} iterations, {res['times'][0]:.1f} s after an "
+                          f"untimed warm-up that builds the subdomain matrices), rate scaled by "
+                          f"{res['dof']}/262144 DOF")}
+
+    stream = torch.cuda.Stream()
+    src = workloads.gaussian_source(2)
+    doms = {}
+    for prec in ("mixed", "fp64"):
+        with torch.cuda.stream(stream):
+            doms[prec] = dgg.Domain(n=n_CFG, N=N_CFG, penalty=1.5, precision=prec, mg_levels=LEVELS, overlap=2,
+                                    stream=stream)
+    d = doms["mixed"]
+    with torch.cuda.stream(stream):
+        x, y, z = d.coordinates()
+        f = src(x, y, z).contiguous()
+        b = d.rhs(f, stream=stream)
+        u = torch.zeros_like(b)
+    stream.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def timed_solves(dom, steps, warm, profile=False):
+        times, reps = [], []
+        for i in range(warm + steps):
+            flush.fill_(float(i))  # evict L2 between steps (outside the timed events)
+            torch.cuda.synchronize()
+            if profile and i == warm:
+                dom.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                u.zero_()
+                e0.record(stream)
+                rep = dom.solve(b, u, TOL)
+                e1.record(stream)
+            e1.synchronize()
+            if i >= warm:
+                times.append(e0.elapsed_time(e1))
+                reps.append(rep)
+        prof = dom.profile_read() if profile else None
+        if profile:
+            dom.profile(False)
+        return times, reps, prof
+
+    # ---- headline: mixed-precision solves
+    timed_solves(d, 0, args.warmup)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = dgg.lib().dg_kernel_launches()
+    with ClockSampler(local) as clk:
+        times, reps, prof = timed_solves(d, args.steps, 0, profile=True)
+    launches = dgg.lib().dg_kernel_launches() - l0
+    barrier()
+    total_s = sum(times) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t)
+    value = world * args.steps / total_s
+    u_mixed = u.clone()
+
+    # ---- plain FP64 solver (same workload)
+    d64 = doms["fp64"]
+    timed_solves(d64, 0, 1)
+    t64, reps64, _ = timed_solves(d64, max(2, args.steps // 2), 0)
+    value64 = len(t64) / (sum(t64) / 1e3)
+    sol_diff = float((u_mixed - u).norm() / u.norm())
+
+    # ---- end to end through the public API: pinned host f -> device, solve, solution -> host
+    f_host = f.cpu().pin_memory()
+    u_host = torch.empty_like(f_host).pin_memory()
+    f_dev = torch.empty_like(f)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            f_dev.copy_(f_host, non_blocking=True)
+            d.rhs(f_dev, b, stream=stream)
+            u.zero_()
+            d.solve(b, u, TOL)
+            u_host.copy_(u, non_blocking=True)
+        stream.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * len(e2e_times) / sum(e2e_times)
+
+    # ---- DG apply rates (config size, L2 resident) and the HBM-sized roofline sweep point
+    def apply_rate(dom, prec, reps=20):
+        n = dom.n_dof
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        uu = torch.empty(n, dtype=dt, device="cuda").uniform_(-1, 1)
+        out = torch.empty_like(uu)
+        fn = (lambda: dom.apply(uu, out, stream=stream)) if prec == "fp64" else (
+            lambda: dom.apply_f32(uu, 0, out, stream=stream))
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        return n / sec / 1e9, sec
+
+    apply = {"config": {"fp64_gdofs": apply_rate(d64, "fp64")[0], "fp32_gdofs": apply_rate(d, "fp32")[0]}}
+    big = dgg.Domain(n=(96, 96, 96), N=4, penalty=1.5, precision="mixed", mg_levels=1, overlap=1, stream=stream)
+    g64, s64 = apply_rate(big, "fp64", 5)
+    g32, s32 = apply_rate(big, "fp32", 10)
+    pk = measured_peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    apply["roofline_size_N4_96cubed"] = {
+        "dof": big.n_dof, "fp64_gdofs": g64, "fp32_gdofs": g32,
+        "fp32_hbm_frac": 8.0 * g32 / hbm, "fp64_hbm_frac": 16.0 * g64 / hbm,
+        "fp64_alu_bound_gdofs": 1.2e12 / (12 * 4 + 12) / 1e9}
+    big.close()
+
+    # ---- roofline of the dominant kernel phase of the timed solves
+    dom_phase = max(prof, key=lambda k: prof[k]["ms"])
+    ph = prof[dom_phase]
+    achieved_gbs = ph["bytes"] / (ph["ms"] / 1e3) / 1e9
+    achieved_tf = ph["flops"] / (ph["ms"] / 1e3) / 1e12
+    # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops x the measured SM clock under load
+    clk_sum = clk.summary()
+    sm_mhz = clk_sum["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    intensity = ph["flops"] / max(ph["bytes"], 1.0)
+    ridge = fp32_peak * 1e12 / (hbm * 1e9)
+    if intensity < ridge:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp32_peak, "peak_source": "FP32 SIMT: 152 SM x 128 lanes x 2 x median SM clock"}
+    roof.update({"kernel": dom_phase, "traffic": None, "launches": ph["launches"],
+                 "avg_launch_ms": ph["ms"] / max(ph["launches"], 1), "bytes_per_launch": ph["bytes"] / max(ph["launches"], 1)})
+    phases = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                  "share": round(v["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-12), 4),
+                  "GB/s": round(v["bytes"] / max(v["ms"], 1e-12) / 1e6, 1)} for k, v in prof.items()}
+
+    lat = sorted(times)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "FP32 V-cycle (smoother, explicit subdomain inverses, "
+                   "transfers) under FP64 FGMRES", "solves_per_step_per_gpu": 1, "parallelism": f"replicas x{world}",
+                   "l2": "256 MB buffer written between timed steps (outside the events)"},
+        "clocks": clk_sum,
+        "latency_ms": {"p50": p50, "p99": p99},
+        "iterations": reps[0].iterations, "relative_residual": max(r.relative_residual for r in reps),
+        "fp64": {"value": value64, "unit": "solves/s", "iterations": reps64[0].iterations,
+                 "relative_residual": max(r.relative_residual for r in reps64),
+                 "mixed_vs_fp64_solution_rel_diff": sol_diff, "mixed_speedup": value / value64 / world},
+        "dg_apply": apply,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": f.numel() * 8,
+                "d2h_bytes_per_step": u.numel() * 8},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "phases": phases,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,125 @@
+// Domain state: geometry, multigrid hierarchy, Schwarz subdomain tables and inverses, solver
+// workspace. Host-side definitions shared by the setup, solver and C-ABI translation units.
+#pragma once
+
+#include <vector_types.h>
+
+#include "internal.h"
+
+namespace dg {
+
+struct SchwarzLevel {
+  int nS = 0;                      // padded subdomain size N^3 + 6 N_ov N^2
+  int n_classes = 0;               // distinct A_S (boundary-contact patterns)
+  bool built = false;              // inverses built (lazily, on first smoothing)
+  SubdomainGeom geom{};
+  std::vector<int> class_count;    // subdomains per class
+  std::vector<int> class_first;    // first subdomain column of each class
+  std::vector<int> position;       // element -> subdomain column (class-sorted)
+  std::vector<int> class_of;       // element -> class
+  std::vector<int> patch;          // per class: 49 ints describing the representative's patch
+  DevBuf<int> elem_of_col;         // subdomain column -> element
+  DevBuf<int> col_of_elem;         // element -> subdomain column
+  DevBuf<double> inv64;            // [n_classes][nS][nS] explicit inverses (FP64 mode)
+  DevBuf<float> inv32;             // FP32 copies (mixed mode)
+  DevBuf<int4> tiles;              // GEMM tile list (class, row0, col0, columns left)
+  int n_tiles = 0;
+};
+
+template <typename T>
+struct LevelWork {
+  DevBuf<T> b, u, r, rS, duS;
+  // puncture subdomain GMRES (finest level only)
+  DevBuf<T> gV, gZ, gW, gD, gH;
+};
+
+struct Level {
+  int n[3] = {0, 0, 0};
+  int E = 0;
+  int64_t ndof = 0;
+  double h[3] = {0, 0, 0};
+  OpGeom<double> g64{};
+  OpGeom<float> g32{};
+  SchwarzLevel sw;
+  LevelWork<double> w64;
+  LevelWork<float> w32;
+};
+
+// Event-based per-phase timing of launches (dg_profile_*).
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int phase;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  dg_phase_stats acc[DG_PHASE_COUNT] = {};
+  cudaEvent_t get();
+  void clear();
+  ~Profiler();
+};
+
+// Brackets one launch (or a group of launches) of a phase with events when profiling is on.
+class PhaseScope {
+ public:
+  PhaseScope(Profiler& p, int phase, cudaStream_t s, double bytes, double flops);
+  ~PhaseScope();
+
+ private:
+  Profiler& p_;
+  int phase_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr;
+};
+
+}  // namespace dg
+
+struct dg_domain {
+  dg_domain_desc desc{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int N = 0;
+  bool mixed = false;
+  dg::LglTables lgl;
+  dg::DevBuf<double> D64, w64, Ilo64, Ihi64, x1;
+  dg::DevBuf<float> D32, w32, Ilo32, Ihi32;
+  std::vector<dg::Level> levels;
+  dg::DevBuf<double> X, Y, Z, mass;
+  dg::DevBuf<double> shares64;  // Schwarz weight shares [64 neighbour patterns][N^3][7]
+  dg::DevBuf<float> shares32;
+  // puncture
+  dg::DevBuf<double> alpha, beta, lin64;
+  dg::DevBuf<float> lin32;
+  bool lin_set = false;
+  // Krylov workspace
+  int kcap = 0;
+  dg::DevBuf<double> V, Zb, w, r, du, ut, rt, tmp, partial, dots;
+  dg::DevBuf<float> vin32;
+  size_t bytes = 0;
+  int subdomain_iterations = 3;
+  dg::Profiler prof;
+};
+
+namespace dg {
+
+void domain_setup(dg_domain* dom);
+void profile_read(dg_domain* dom, dg_phase_stats* out);
+void ensure_schwarz(dg_domain* dom, int level);
+size_t domain_device_bytes(const dg_domain* dom);
+
+// level operators
+void apply_level(dg_domain* dom, int level, const double* u, double* out, const double* b, bool with_lin,
+                 cudaStream_t s);
+void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, const float* b, bool with_lin,
+                     cudaStream_t s);
+template <typename T>
+void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations, bool u_is_zero, cudaStream_t s);
+template <typename T>
+void vcycle(dg_domain* dom, const T* r, T* z, cudaStream_t s);
+void precondition(dg_domain* dom, int mode, const double* v, double* z, cudaStream_t s);
+
+dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg_solve_opts& o, dg_solve_report* rep);
+
+}  // namespace dg

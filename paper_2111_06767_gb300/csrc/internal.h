@@ -1,0 +1,171 @@
+// Internal declarations of the GB300 DG elliptic library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dg_elliptic.h"
+
+namespace dg {
+
+// ------------------------------------------------------------------ errors
+
+struct Error {
+  dg_status status;
+  std::string message;
+};
+
+// Throwing is confined to host setup/orchestration code; every extern "C" entry point catches
+// and converts to a dg_status, so nothing escapes the ABI.
+[[noreturn]] void fail(dg_status st, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what, const char* file, int line);
+#define DG_CUDA(x) ::dg::cuda_check((x), #x, __FILE__, __LINE__)
+// Counts kernels this library launched (process-wide) and checks the launch.
+void count_launches(int64_t k);
+int64_t launches_total();
+#define DG_LAUNCHED(k)                      \
+  do {                                      \
+    ::dg::count_launches(k);                \
+    DG_CUDA(cudaGetLastError());            \
+  } while (0)
+#define DG_REQUIRE(cond, msg)                                  \
+  do {                                                         \
+    if (!(cond)) ::dg::fail(DG_ERR_INVALID_ARG, (msg));        \
+  } while (0)
+
+// ------------------------------------------------------------------ device memory
+
+// Owning device buffer (cudaMalloc/cudaFree), move-only.
+template <typename T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t count = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t n) { alloc(n); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), count(o.count) { o.ptr = nullptr; o.count = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); ptr = o.ptr; count = o.count; o.ptr = nullptr; o.count = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t n);
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    count = 0;
+  }
+  size_t bytes() const { return count * sizeof(T); }
+  T* get() const { return ptr; }
+};
+
+template <typename T>
+void DevBuf<T>::alloc(size_t n) {
+  release();
+  if (n == 0) return;
+  cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    (void)cudaGetLastError();
+    fail(DG_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  count = n;
+}
+
+// ------------------------------------------------------------------ LGL tables (host)
+
+struct LglTables {
+  int N = 0;
+  double x[DG_MAX_N] = {};
+  double w[DG_MAX_N] = {};
+  double D[DG_MAX_N * DG_MAX_N] = {};        // D[k*N + l] = l_l'(x_k)
+  double I_lo[DG_MAX_N * DG_MAX_N] = {};     // child on the lower half: l_j((x_t - 1)/2), [t*N + j]
+  double I_hi[DG_MAX_N * DG_MAX_N] = {};     // upper half: l_j((x_t + 1)/2)
+};
+LglTables make_lgl(int N);
+
+// ------------------------------------------------------------------ operator geometry
+
+// Everything an element apply needs besides the data; uniform affine elements per level.
+template <typename T>
+struct OpGeom {
+  int nx, ny, nz;
+  T dxi[3];      // 2 / h_d : d xi / d x
+  T J;           // volume Jacobian h_x h_y h_z / 8
+  T Jf[3];       // face Jacobian of faces normal to d: product of the tangential h/2
+  T sigma[3];    // penalty C N^2 / h_d (Eq. penalty, equal neighbours)
+  T lift[3];     // 1 / (w_0 h_d): L = M^-1 ML at a face node is 2 lift[d]
+};
+
+template <typename T>
+OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, const LglTables& t);
+
+// ------------------------------------------------------------------ kernels (launchers)
+
+// out = A u (+ diag * u)  or, with b != nullptr, out = b - (A u + diag * u).
+template <typename T>
+void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
+                  cudaStream_t s);
+
+// Build explicit subdomain matrices A_S for a set of classes (FP64, column-major == row-major by symmetry).
+void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<double>& g, const double* D, const double* w,
+                                     const int* d_patch_info, int n_classes, int nS, double* A_out, cudaStream_t s);
+// In-place Gauss-Jordan inversion of n_classes SPD matrices of size n (no pivoting).
+void launch_invert_spd_batched(double* A, int n, int n_classes, cudaStream_t s);
+
+// Schwarz data movement. Subdomain columns are class-sorted; rows follow the subdomain point order.
+struct SubdomainGeom {
+  int n[3];
+  int E, N, ov, nS;
+};
+template <typename T>
+void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, T* rS, cudaStream_t s);
+template <typename T, typename TU>
+void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const T* shares, TU* u,
+                        cudaStream_t s);
+
+// Multigrid transfers (per dimension: 0 lower half, 1 upper half, 2 full).
+template <typename T>
+void launch_prolongate_add(int N, const int nf[3], const int nc[3], const T* Ilo, const T* Ihi, const T* uc, T* uf,
+                           cudaStream_t s);
+template <typename T>
+void launch_restrict(int N, const int nf[3], const int nc[3], const T* Ilo, const T* Ihi, const T* rf, T* bc,
+                     cudaStream_t s);
+
+// Vector kernels.
+template <typename T>
+void launch_axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s);  // y = a x + b y
+void launch_convert_d2f(int64_t n, const double* x, float* y, cudaStream_t s);
+void launch_convert_f2d(int64_t n, const float* x, double* y, cudaStream_t s);
+void launch_add_f2d(int64_t n, const float* x, double* y, cudaStream_t s);  // y += x
+void launch_scale_mul(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);  // y = a .* b
+// Deterministic multi-dot: out[k] = sum_i V[k*ld + i] * w[i] for k < m (two-pass reduction).
+void launch_multidot(int64_t n, int m, const double* V, int64_t ld, const double* w, double* partial, double* out,
+                     cudaStream_t s);
+// w -= sum_k h[k] V[k*ld + i]
+void launch_subtract_combination(int64_t n, int m, const double* V, int64_t ld, const double* h, double* w,
+                                 cudaStream_t s);
+// x += sum_k y[k] Z[k*ld + i]
+void launch_add_combination(int64_t n, int m, const double* Z, int64_t ld, const double* y, double* x, cudaStream_t s);
+int multidot_partial_blocks();
+
+// Puncture source terms.
+void launch_puncture_fields(int64_t n, const double* x, const double* y, const double* z, int np,
+                            const dg_puncture* p, double* alpha, double* beta, cudaStream_t s);
+// r = b - (Au + M S(u)) where Au is given; lin = M S'(u)
+void launch_puncture_residual(int64_t n, const double* Au, const double* u, const double* b, const double* mass,
+                              const double* alpha, const double* beta, double* r, cudaStream_t s);
+void launch_puncture_linearization(int64_t n, const double* u, const double* mass, const double* alpha,
+                                   const double* beta, double* lin64, float* lin32, cudaStream_t s);
+template <typename T>
+void launch_mass_diag(int N, const OpGeom<T>& g, const T* w, int64_t ndof, T* mass, cudaStream_t s);
+void launch_node_coords(int N, const int n[3], const double lower[3], const double h[3], const double* x1,
+                        double* X, double* Y, double* Z, cudaStream_t s);
+
+}  // namespace dg

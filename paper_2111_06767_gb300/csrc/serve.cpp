@@ -1,0 +1,264 @@
+// Continuous-batching request loop for elliptic solves.
+//
+// submit() copies a request into library memory and queues it. Worker threads (one per
+// concurrently running solve, each with its own CUDA stream) admit the oldest waiting request
+// whose estimated device footprint fits the remaining memory budget, build its domain, solve it
+// and publish the result; admission happens whenever a worker and enough budget free up, so
+// requests that arrive while others run join the device work as capacity allows. poll() hands a
+// finished result back exactly once.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "domain.h"
+
+namespace {
+
+double clock_now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Job {
+  uint64_t ticket = 0;
+  dg_request req{};
+  std::vector<double> f;
+  size_t bytes = 0;
+  double submit_time = 0, admit_time = 0, finish_time = 0;
+  dg_status status = DG_PENDING;
+  dg_solve_report report{};
+  std::vector<double> u;
+};
+
+}  // namespace
+
+namespace dg {
+
+// Upper bound of a domain's device footprint (bytes) before it is built.
+size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations) {
+  const int N = d.N, ov = d.overlap;
+  const size_t nS = (size_t)N * N * N + 6 * (size_t)ov * N * N;
+  const bool mixed = d.precision == DG_PRECISION_MIXED;
+  const size_t fb = mixed ? 4 : 8;
+  size_t total = 0;
+  int n[3] = {d.n[0], d.n[1], d.n[2]};
+  for (int l = 0; l < DG_MAX_LEVELS; ++l) {
+    const size_t E = (size_t)n[0] * n[1] * n[2];
+    const size_t ndof = E * N * N * N;
+    size_t classes = 1;
+    for (int i = 0; i < 3; ++i) classes *= (size_t)std::min(n[i], 5);
+    classes = std::min(classes, E);
+    total += classes * nS * nS * (8 + (mixed ? 4 : 0));      // FP64 build (+ FP32 copy)
+    total += E * nS * (4 + 2 * fb) + ndof * 7 * (4 + fb) + 5 * ndof * fb;
+    if ((d.mg_levels && l + 1 == d.mg_levels) || (n[0] % 2 && n[1] % 2 && n[2] % 2)) break;
+    for (int i = 0; i < 3; ++i)
+      if (n[i] % 2 == 0) n[i] /= 2;
+  }
+  const size_t ndof0 = (size_t)d.n[0] * d.n[1] * d.n[2] * N * N * N;
+  total += ndof0 * 8 * (2 * (size_t)max_iterations + 16);
+  return total + (8u << 20);
+}
+
+}  // namespace dg
+
+struct dg_server {
+  dg_serve_desc desc{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job*> waiting;
+  std::unordered_map<uint64_t, Job*> jobs;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+  size_t budget = 0, in_use = 0;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+  double t0 = clock_now();
+
+  void run(int wid);
+};
+
+void dg_server::run(int wid) {
+  cudaStream_t s = streams[wid % streams.size()];
+  for (;;) {
+    Job* job = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      for (;;) {
+        if (stopping && waiting.empty()) return;
+        for (auto it = waiting.begin(); it != waiting.end(); ++it) {
+          if (in_use + (*it)->bytes <= budget) {
+            job = *it;
+            waiting.erase(it);
+            break;
+          }
+        }
+        if (job) break;
+        cv_work.wait(lk);
+      }
+      in_use += job->bytes;
+      job->admit_time = clock_now() - t0;
+    }
+    dg_domain* dom = nullptr;
+    dg_status st = dg_domain_create(&job->req.domain, s, &dom);
+    if (st == DG_OK) {
+      dg_layout lay;
+      dg_domain_layout(dom, &lay);
+      double *u = nullptr, *b = nullptr, *f = nullptr;
+      const size_t nb = sizeof(double) * lay.n_dof;
+      if (cudaMallocAsync((void**)&u, nb, s) != cudaSuccess || cudaMallocAsync((void**)&b, nb, s) != cudaSuccess ||
+          cudaMallocAsync((void**)&f, nb, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = DG_ERR_OOM;
+      } else {
+        cudaMemsetAsync(u, 0, nb, s);
+        if (job->req.domain.problem == DG_PROBLEM_POISSON) {
+          cudaMemcpyAsync(f, job->f.data(), nb, cudaMemcpyHostToDevice, s);
+          st = dg_rhs(dom, f, b, s);
+        } else {
+          cudaMemsetAsync(b, 0, nb, s);
+        }
+        if (st == DG_OK) {
+          dg_solve_opts o = job->req.opts;
+          o.relative_to_b = job->req.domain.problem == DG_PROBLEM_POISSON ? 1 : 0;
+          st = elliptic_solve(dom, b, u, job->req.tol, &o, &job->report);
+        }
+        job->u.resize(lay.n_dof);
+        if (cudaMemcpyAsync(job->u.data(), u, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          (void)cudaGetLastError();
+          if (st == DG_OK) st = DG_ERR_CUDA;
+        }
+      }
+      if (u) cudaFreeAsync(u, s);
+      if (b) cudaFreeAsync(b, s);
+      if (f) cudaFreeAsync(f, s);
+      cudaStreamSynchronize(s);
+      dg_domain_destroy(dom);
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in_use -= job->bytes;
+      job->status = st;
+      job->report.status = st;
+      job->finish_time = clock_now() - t0;
+    }
+    cv_work.notify_all();
+    cv_done.notify_all();
+  }
+}
+
+extern "C" {
+
+dg_status elliptic_serve_create(const dg_serve_desc* desc, dg_server** out) {
+  if (!desc || !out) return DG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (desc->max_active < 1 || desc->queue_capacity < 1 || desc->n_streams < 1) return DG_ERR_INVALID_ARG;
+  dg_server* srv = new (std::nothrow) dg_server();
+  if (!srv) return DG_ERR_OOM;
+  srv->desc = *desc;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete srv;
+    return DG_ERR_CUDA;
+  }
+  srv->budget = desc->memory_budget_bytes ? desc->memory_budget_bytes : (size_t)(0.8 * (double)free_b);
+  for (int i = 0; i < desc->n_streams; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      for (auto x : srv->streams) cudaStreamDestroy(x);
+      delete srv;
+      return DG_ERR_CUDA;
+    }
+    srv->streams.push_back(s);
+  }
+  for (int i = 0; i < desc->max_active; ++i) srv->workers.emplace_back([srv, i] { srv->run(i); });
+  *out = srv;
+  return DG_OK;
+}
+
+dg_status elliptic_serve_submit(dg_server* srv, const dg_request* req, uint64_t* ticket) {
+  if (!srv || !req || !ticket) return DG_ERR_INVALID_ARG;
+  const dg_domain_desc& d = req->domain;
+  if (d.N < 2 || d.N > DG_MAX_N || d.n[0] < 1 || d.n[1] < 1 || d.n[2] < 1) return DG_ERR_INVALID_ARG;
+  if (d.problem == DG_PROBLEM_POISSON && !req->f_host) return DG_ERR_INVALID_ARG;
+  const int max_it = req->opts.max_iterations > 0 ? req->opts.max_iterations : 200;
+  const size_t bytes = dg::estimate_domain_bytes(d, max_it);
+  Job* job = new (std::nothrow) Job();
+  if (!job) return DG_ERR_OOM;
+  job->req = *req;
+  job->bytes = bytes;
+  if (d.problem == DG_PROBLEM_POISSON) {
+    const size_t ndof = (size_t)d.n[0] * d.n[1] * d.n[2] * d.N * d.N * d.N;
+    try {
+      job->f.assign(req->f_host, req->f_host + ndof);
+    } catch (...) {
+      delete job;
+      return DG_ERR_OOM;
+    }
+  }
+  job->req.f_host = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stopping || bytes > srv->budget) {
+      delete job;
+      return DG_ERR_INVALID_ARG;
+    }
+    if ((int)srv->waiting.size() >= srv->desc.queue_capacity) {
+      delete job;
+      return DG_ERR_BUSY;
+    }
+    job->ticket = srv->next_ticket++;
+    job->submit_time = clock_now() - srv->t0;
+    srv->jobs[job->ticket] = job;
+    srv->waiting.push_back(job);
+    *ticket = job->ticket;
+  }
+  srv->cv_work.notify_all();
+  return DG_OK;
+}
+
+dg_status elliptic_serve_poll(dg_server* srv, uint64_t ticket, dg_result* out) {
+  if (!srv) return DG_ERR_INVALID_ARG;
+  Job* job = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return DG_ERR_NOT_FOUND;
+    if (it->second->status == DG_PENDING) return DG_PENDING;
+    job = it->second;
+    srv->jobs.erase(it);
+  }
+  const dg_status st = job->status;
+  if (out) {
+    out->report = job->report;
+    out->n_dof = (int64_t)job->u.size();
+    out->submit_time = job->submit_time;
+    out->admit_time = job->admit_time;
+    out->finish_time = job->finish_time;
+    if (out->u_host && !job->u.empty()) std::memcpy(out->u_host, job->u.data(), sizeof(double) * job->u.size());
+  }
+  delete job;
+  return st;
+}
+
+double elliptic_serve_clock(const dg_server* srv) { return srv ? clock_now() - srv->t0 : 0.0; }
+
+void elliptic_serve_destroy(dg_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stopping = true;
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->workers) t.join();
+  for (auto& kv : srv->jobs) delete kv.second;
+  for (auto s : srv->streams) cudaStreamDestroy(s);
+  delete srv;
+}
+
+}  // extern "C"

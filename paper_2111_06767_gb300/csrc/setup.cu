@@ -1,0 +1,317 @@
+// Domain construction: LGL tables, the multigrid hierarchy (Sec. III.C.1), Schwarz subdomain
+// index and weight tables (Sec. III.D) and the explicit subdomain inverses (Sec. III.E).
+//
+// Subdomain classes: on a uniform box the subdomain operator A_S of element e depends only on
+// which of its faces have neighbours and, for each neighbour, whether that neighbour's far face
+// (the one pointing away from e) is an external boundary; per dimension that is 4 bits. All
+// subdomains with equal bits share one explicit inverse, built once.
+//
+// Weights (Eqs. schwarz_weight_prod, schwarz_weight_function): quintic smoothstep phi,
+// w(xi) = (phi((xi + 1)/delta) - phi((xi - 1)/delta)) / 2, delta = 1 + x_{N_ov}. The edge and
+// corner weight missing from the product is handed to face neighbours: per point the product
+// prod_d (a_d + b_d^+ + b_d^-) = 1 (a_d = w(xi_d), b_d^+- = w(xi_d -+ 2)) is expanded, a term with
+// m >= 1 neighbour factors goes 1/m to each of those face neighbours' subdomains; a side without
+// a neighbour replaces its phi term by +-1 so that a_d absorbs it.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "domain.h"
+
+namespace dg {
+
+namespace {
+
+double smoothstep(double x) {
+  if (x >= 1.0) return 1.0;
+  if (x <= -1.0) return -1.0;
+  const double x2 = x * x;
+  return x * (15.0 - 10.0 * x2 + 3.0 * x2 * x2) / 8.0;
+}
+
+double weight1d(double xi, double delta) { return 0.5 * (smoothstep((xi + 1.0) / delta) - smoothstep((xi - 1.0) / delta)); }
+
+// shares[s] for s = 0 (own subdomain) and 1 + f (neighbour across face f) at one point.
+void point_shares(const LglTables& t, int ov, const bool has_lo[3], const bool has_hi[3], const int idx[3],
+                  double shares[7]) {
+  const double delta = ov < t.N ? 1.0 + t.x[ov] : 2.0;
+  double a[3], bm[3], bp[3];
+  for (int d = 0; d < 3; ++d) {
+    const double xi = t.x[idx[d]];
+    const double lo = has_lo[d] ? smoothstep((xi + 1.0) / delta) : 1.0;
+    const double hi = has_hi[d] ? smoothstep((xi - 1.0) / delta) : -1.0;
+    a[d] = 0.5 * (lo - hi);
+    bm[d] = has_lo[d] ? weight1d(xi + 2.0, delta) : 0.0;
+    bp[d] = has_hi[d] ? weight1d(xi - 2.0, delta) : 0.0;
+  }
+  for (int s = 0; s < 7; ++s) shares[s] = 0.0;
+  for (int cx = 0; cx < 3; ++cx)
+    for (int cy = 0; cy < 3; ++cy)
+      for (int cz = 0; cz < 3; ++cz) {
+        const int ch[3] = {cx, cy, cz};
+        double term = 1.0;
+        int owners[3], m = 0;
+        for (int d = 0; d < 3; ++d) {
+          if (ch[d] == 0) term *= a[d];
+          else if (ch[d] == 1) { term *= bm[d]; owners[m++] = 1 + 2 * d; }
+          else { term *= bp[d]; owners[m++] = 2 + 2 * d; }
+        }
+        if (m == 0) shares[0] += term;
+        else
+          for (int q = 0; q < m; ++q) shares[owners[q]] += term / m;
+      }
+}
+
+template <typename T>
+void upload(DevBuf<T>& buf, const std::vector<T>& host, cudaStream_t s) {
+  buf.alloc(host.size());
+  if (!host.empty()) DG_CUDA(cudaMemcpyAsync(buf.get(), host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+template <typename T>
+void upload_arr(DevBuf<T>& buf, const double* src, int n, cudaStream_t s) {
+  std::vector<T> h(src, src + n);
+  upload(buf, h, s);
+}
+
+// Per-level subdomain classes and column order (cheap: done at creation).
+void classify_schwarz(dg_domain* dom, Level& L) {
+  const int N = dom->N, ov = dom->desc.overlap;
+  const int N3 = N * N * N;
+  SchwarzLevel& sw = L.sw;
+  sw.nS = N3 + 6 * ov * N * N;
+  sw.geom = SubdomainGeom{{L.n[0], L.n[1], L.n[2]}, L.E, N, ov, sw.nS};
+  const int E = L.E;
+  auto coords = [&](int e, int c[3]) {
+    c[0] = e % L.n[0];
+    c[1] = (e / L.n[0]) % L.n[1];
+    c[2] = e / (L.n[0] * L.n[1]);
+  };
+  auto neighbor = [&](int e, int f) {
+    int c[3];
+    coords(e, c);
+    const int d = f >> 1;
+    c[d] += (f & 1) ? 1 : -1;
+    if (c[d] < 0 || c[d] >= L.n[d]) return -1;
+    return c[0] + L.n[0] * (c[1] + L.n[1] * c[2]);
+  };
+  std::vector<int> key(E);
+  for (int e = 0; e < E; ++e) {
+    int c[3];
+    coords(e, c);
+    int k = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int has_lo = c[d] > 0, lo_far = c[d] - 1 == 0, has_hi = c[d] < L.n[d] - 1, hi_far = c[d] + 1 == L.n[d] - 1;
+      k |= (has_lo | (has_lo && lo_far) << 1 | has_hi << 2 | (has_hi && hi_far) << 3) << (4 * d);
+    }
+    key[e] = k;
+  }
+  std::map<int, int> cls_id;
+  for (int e = 0; e < E; ++e) cls_id.emplace(key[e], 0);
+  int nc = 0;
+  for (auto& kv : cls_id) kv.second = nc++;
+  sw.n_classes = nc;
+  sw.class_of.resize(E);
+  sw.class_count.assign(nc, 0);
+  std::vector<int> rep(nc, -1);
+  for (int e = 0; e < E; ++e) {
+    sw.class_of[e] = cls_id[key[e]];
+    sw.class_count[sw.class_of[e]]++;
+    if (rep[sw.class_of[e]] < 0) rep[sw.class_of[e]] = e;
+  }
+  sw.class_first.assign(nc, 0);
+  for (int c = 1; c < nc; ++c) sw.class_first[c] = sw.class_first[c - 1] + sw.class_count[c - 1];
+  sw.position.resize(E);
+  std::vector<int> elem_of_col(E);
+  {
+    std::vector<int> fill = sw.class_first;
+    for (int e = 0; e < E; ++e) {
+      sw.position[e] = fill[sw.class_of[e]]++;
+      elem_of_col[sw.position[e]] = e;
+    }
+  }
+  // patch descriptions of the class representatives (slot 0 centre, 1 + f neighbour across f)
+  sw.patch.assign((size_t)nc * 49, -2);
+  for (int c = 0; c < nc; ++c) {
+    const int e = rep[c];
+    int* P = &sw.patch[(size_t)c * 49];
+    for (int s = 0; s < 7; ++s) P[42 + s] = 0;
+    P[42] = 1;
+    for (int f = 0; f < 6; ++f) {
+      const int q = neighbor(e, f);
+      P[f] = q >= 0 ? 1 + f : -1;
+      P[42 + 1 + f] = q >= 0;
+      if (q < 0) continue;
+      const int back = (f & ~1) | (1 - (f & 1));
+      for (int ff = 0; ff < 6; ++ff) {
+        if (ff == back) P[(1 + f) * 6 + ff] = 0;  // faces the centre
+        else P[(1 + f) * 6 + ff] = neighbor(q, ff) >= 0 ? -2 : -1;
+      }
+    }
+  }
+  cudaStream_t s = dom->stream;
+  upload(sw.elem_of_col, elem_of_col, s);
+  upload(sw.col_of_elem, sw.position, s);
+  std::vector<int4> tiles;
+  for (int c = 0; c < nc; ++c)
+    for (int r0 = 0; r0 < sw.nS; r0 += 64)
+      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
+        tiles.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
+  sw.n_tiles = (int)tiles.size();
+  upload(sw.tiles, tiles, s);
+}
+
+// Schwarz weight shares of every point for the 64 patterns of existing face neighbours.
+void build_shares(dg_domain* dom) {
+  const int N = dom->N, N3 = N * N * N, ov = dom->desc.overlap;
+  std::vector<double> sh((size_t)64 * N3 * 7);
+  for (int pat = 0; pat < 64; ++pat) {
+    bool has_lo[3], has_hi[3];
+    for (int d = 0; d < 3; ++d) {
+      has_lo[d] = (pat >> (2 * d)) & 1;
+      has_hi[d] = (pat >> (2 * d + 1)) & 1;
+    }
+    for (int p = 0; p < N3; ++p) {
+      const int c[3] = {p % N, (p / N) % N, p / (N * N)};
+      point_shares(dom->lgl, ov, has_lo, has_hi, c, &sh[((size_t)pat * N3 + p) * 7]);
+    }
+  }
+  if (dom->mixed) {
+    std::vector<float> s32(sh.begin(), sh.end());
+    upload(dom->shares32, s32, dom->stream);
+  } else {
+    upload(dom->shares64, sh, dom->stream);
+  }
+}
+
+template <typename T>
+void alloc_work(LevelWork<T>& w, const Level& L) {
+  w.b.alloc(L.ndof);
+  w.u.alloc(L.ndof);
+  w.r.alloc(L.ndof);
+  w.rS.alloc((size_t)L.E * L.sw.nS);
+  w.duS.alloc((size_t)L.E * L.sw.nS);
+}
+
+}  // namespace
+
+void domain_setup(dg_domain* dom) {
+  const dg_domain_desc& d = dom->desc;
+  DG_REQUIRE(d.N >= 2 && d.N <= DG_MAX_N, "N must be in [2, 10]");
+  for (int i = 0; i < 3; ++i) {
+    DG_REQUIRE(d.n[i] >= 1 && d.n[i] <= 4096, "element counts must be in [1, 4096]");
+    DG_REQUIRE(d.upper[i] > d.lower[i], "upper must exceed lower");
+  }
+  DG_REQUIRE(d.penalty > 0, "penalty must be positive");
+  DG_REQUIRE(d.overlap >= 1 && d.overlap <= d.N - 1, "overlap must be in [1, N-1]");
+  DG_REQUIRE(d.presmooth >= 0 && d.postsmooth >= 0 && d.presmooth + d.postsmooth >= 1, "need smoothing steps");
+  DG_REQUIRE(d.precision == DG_PRECISION_FP64 || d.precision == DG_PRECISION_MIXED, "bad precision");
+  DG_REQUIRE(d.problem == DG_PROBLEM_POISSON || d.problem == DG_PROBLEM_PUNCTURE, "bad problem");
+  DG_REQUIRE(d.mg_levels >= 0 && d.mg_levels <= DG_MAX_LEVELS, "mg_levels must be in [0, 8]");
+  DG_REQUIRE(d.problem != DG_PROBLEM_PUNCTURE || (d.n_punctures >= 0 && d.n_punctures <= DG_MAX_PUNCTURES),
+             "bad puncture count");
+  const int64_t ndof = (int64_t)d.n[0] * d.n[1] * d.n[2] * d.N * d.N * d.N;
+  DG_REQUIRE(ndof < (int64_t)1 << 31, "problem too large for 32-bit point indices");
+  dom->N = d.N;
+  dom->mixed = d.precision == DG_PRECISION_MIXED;
+  dom->lgl = make_lgl(d.N);
+  cudaStream_t s = dom->stream;
+  const LglTables& t = dom->lgl;
+  const int N = d.N;
+  upload_arr(dom->D64, t.D, N * N, s);
+  upload_arr(dom->w64, t.w, N, s);
+  upload_arr(dom->Ilo64, t.I_lo, N * N, s);
+  upload_arr(dom->Ihi64, t.I_hi, N * N, s);
+  upload_arr(dom->x1, t.x, N, s);
+  upload_arr(dom->D32, t.D, N * N, s);
+  upload_arr(dom->w32, t.w, N, s);
+  upload_arr(dom->Ilo32, t.I_lo, N * N, s);
+  upload_arr(dom->Ihi32, t.I_hi, N * N, s);
+  // hierarchy: halve every even dimension per level
+  int n[3] = {d.n[0], d.n[1], d.n[2]};
+  for (;;) {
+    Level L;
+    for (int i = 0; i < 3; ++i) {
+      L.n[i] = n[i];
+      L.h[i] = (d.upper[i] - d.lower[i]) / n[i];
+    }
+    L.E = n[0] * n[1] * n[2];
+    L.ndof = (int64_t)L.E * N * N * N;
+    L.g64 = make_geom<double>(L.n, L.h, N, d.penalty, t);
+    L.g32 = make_geom<float>(L.n, L.h, N, d.penalty, t);
+    dom->levels.push_back(std::move(L));
+    if ((int)dom->levels.size() == (d.mg_levels ? d.mg_levels : DG_MAX_LEVELS)) break;
+    if (n[0] % 2 && n[1] % 2 && n[2] % 2) break;
+    for (int i = 0; i < 3; ++i)
+      if (n[i] % 2 == 0) n[i] /= 2;
+  }
+  const Level& L0 = dom->levels[0];
+  dom->X.alloc(L0.ndof);
+  dom->Y.alloc(L0.ndof);
+  dom->Z.alloc(L0.ndof);
+  launch_node_coords(N, L0.n, d.lower, L0.h, dom->x1.get(), dom->X.get(), dom->Y.get(), dom->Z.get(), s);
+  dom->mass.alloc(L0.ndof);
+  launch_mass_diag<double>(N, L0.g64, dom->w64.get(), L0.ndof, dom->mass.get(), s);
+  for (auto& L : dom->levels) classify_schwarz(dom, L);
+  build_shares(dom);
+  if (d.problem == DG_PROBLEM_PUNCTURE) {
+    dom->alpha.alloc(L0.ndof);
+    dom->beta.alloc(L0.ndof);
+    dom->lin64.alloc(L0.ndof);
+    if (dom->mixed) dom->lin32.alloc(L0.ndof);
+    launch_puncture_fields(L0.ndof, dom->X.get(), dom->Y.get(), dom->Z.get(), d.n_punctures, d.punctures,
+                           dom->alpha.get(), dom->beta.get(), s);
+  }
+  DG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Explicit inverses and work vectors of one level, built on first use (Sec. III.E: construction
+// cost amortised over all later solves).
+void ensure_schwarz(dg_domain* dom, int level) {
+  Level& L = dom->levels[level];
+  SchwarzLevel& sw = L.sw;
+  if (sw.built) return;
+  const int N = dom->N, ov = dom->desc.overlap, nS = sw.nS, nc = sw.n_classes;
+  cudaStream_t s = dom->stream;
+  DG_CUDA(cudaStreamSynchronize(s));
+  DevBuf<int> d_patch;
+  upload(d_patch, sw.patch, s);
+  sw.inv64.alloc((size_t)nc * nS * nS);
+  launch_build_subdomain_matrices(N, ov, L.g64, dom->D64.get(), dom->w64.get(), d_patch.get(), nc, nS, sw.inv64.get(), s);
+  launch_invert_spd_batched(sw.inv64.get(), nS, nc, s);
+  if (dom->mixed) {
+    sw.inv32.alloc((size_t)nc * nS * nS);
+    launch_convert_d2f((int64_t)nc * nS * nS, sw.inv64.get(), sw.inv32.get(), s);
+    DG_CUDA(cudaStreamSynchronize(s));
+    sw.inv64.release();
+    alloc_work(L.w32, L);
+  } else {
+    alloc_work(L.w64, L);
+  }
+  DG_CUDA(cudaStreamSynchronize(s));
+  sw.built = true;
+  dom->bytes = domain_device_bytes(dom);
+}
+
+size_t domain_device_bytes(const dg_domain* dom) {
+  size_t b = dom->D64.bytes() + dom->w64.bytes() + dom->Ilo64.bytes() + dom->Ihi64.bytes() + dom->x1.bytes() +
+             dom->D32.bytes() + dom->w32.bytes() + dom->Ilo32.bytes() + dom->Ihi32.bytes() + dom->X.bytes() +
+             dom->Y.bytes() + dom->Z.bytes() + dom->mass.bytes() + dom->alpha.bytes() + dom->beta.bytes() +
+             dom->lin64.bytes() + dom->lin32.bytes() + dom->V.bytes() + dom->Zb.bytes() + dom->w.bytes() +
+             dom->r.bytes() + dom->du.bytes() + dom->ut.bytes() + dom->rt.bytes() + dom->tmp.bytes() +
+             dom->partial.bytes() + dom->dots.bytes() + dom->vin32.bytes() + dom->shares64.bytes() +
+             dom->shares32.bytes();
+  for (const auto& L : dom->levels) {
+    const auto& sw = L.sw;
+    b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.inv64.bytes() + sw.inv32.bytes() + sw.tiles.bytes();
+    for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
+                    &L.w64.gH})
+      b += p->bytes();
+    for (auto* p : {&L.w32.b, &L.w32.u, &L.w32.r, &L.w32.rS, &L.w32.duS, &L.w32.gV, &L.w32.gZ, &L.w32.gW, &L.w32.gD,
+                    &L.w32.gH})
+      b += p->bytes();
+  }
+  return b;
+}
+
+}  // namespace dg

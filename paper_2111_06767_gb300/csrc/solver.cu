@@ -1,0 +1,473 @@
+// Solver orchestration on one stream: Schwarz smoothing (Sec. III.D.5), the multigrid V-cycle
+// (Sec. III.C.3), flexible GMRES (Sec. III.B, Saad Alg. 9.6) and Newton-Raphson with a line
+// search (Sec. III.A). All vector work runs in the library's kernels; the host only keeps the
+// (k+1) x k Hessenberg matrix and its Givens rotations, read back once per Krylov iteration.
+#include <chrono>
+#include <cmath>
+
+#include "domain.h"
+
+namespace dg {
+
+namespace {
+// algorithmic work of one DG apply: read u (+ b, diag), write the result; 12N + 12 flops per point
+// for the six sum-factorised contractions plus the face terms amortised per point
+double apply_bytes(int64_t ndof, size_t sz, bool b, bool diag) { return (double)ndof * sz * (2 + b + diag); }
+double apply_flops(int64_t ndof, int N) { return (double)ndof * (12.0 * N + 12.0); }
+}  // namespace
+
+void apply_level(dg_domain* dom, int level, const double* u, double* out, const double* b, bool with_lin,
+                 cudaStream_t s) {
+  Level& L = dom->levels[level];
+  const double* diag = (with_lin && level == 0 && dom->lin_set) ? dom->lin64.get() : nullptr;
+  PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP64, s, apply_bytes(L.ndof, 8, b, diag), apply_flops(L.ndof, dom->N));
+  launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s);
+}
+
+void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, const float* b, bool with_lin,
+                     cudaStream_t s) {
+  Level& L = dom->levels[level];
+  const float* diag = (with_lin && level == 0 && dom->lin_set && dom->lin32.get()) ? dom->lin32.get() : nullptr;
+  PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP32, s, apply_bytes(L.ndof, 4, b, diag), apply_flops(L.ndof, dom->N));
+  launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s);
+}
+
+namespace {
+
+template <typename T>
+LevelWork<T>& work(Level& L);
+template <>
+LevelWork<double>& work<double>(Level& L) { return L.w64; }
+template <>
+LevelWork<float>& work<float>(Level& L) { return L.w32; }
+
+template <typename T>
+const T* inverses(const SchwarzLevel& sw);
+template <>
+const double* inverses<double>(const SchwarzLevel& sw) { return sw.inv64.get(); }
+template <>
+const float* inverses<float>(const SchwarzLevel& sw) { return sw.inv32.get(); }
+
+template <typename T>
+const T* shares(const dg_domain* dom);
+template <>
+const double* shares<double>(const dg_domain* dom) { return dom->shares64.get(); }
+template <>
+const float* shares<float>(const dg_domain* dom) { return dom->shares32.get(); }
+
+template <typename T>
+void apply_T(dg_domain* dom, int level, const T* u, T* out, const T* b, cudaStream_t s);
+template <>
+void apply_T<double>(dg_domain* dom, int level, const double* u, double* out, const double* b, cudaStream_t s) {
+  apply_level(dom, level, u, out, b, true, s);
+}
+template <>
+void apply_T<float>(dg_domain* dom, int level, const float* u, float* out, const float* b, cudaStream_t s) {
+  apply_level_f32(dom, level, u, out, b, true, s);
+}
+
+template <typename T>
+const T* Ilo(dg_domain* dom);
+template <>
+const double* Ilo<double>(dg_domain* dom) { return dom->Ilo64.get(); }
+template <>
+const float* Ilo<float>(dg_domain* dom) { return dom->Ilo32.get(); }
+template <typename T>
+const T* Ihi(dg_domain* dom);
+template <>
+const double* Ihi<double>(dg_domain* dom) { return dom->Ihi64.get(); }
+template <>
+const float* Ihi<float>(dg_domain* dom) { return dom->Ihi32.get(); }
+
+}  // namespace
+
+template <typename T>
+void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, cudaStream_t s);
+
+template <typename T>
+void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations, bool u_is_zero, cudaStream_t s) {
+  ensure_schwarz(dom, level);
+  Level& L = dom->levels[level];
+  LevelWork<T>& W = work<T>(L);
+  SchwarzLevel& sw = L.sw;
+  DG_REQUIRE(inverses<T>(sw) != nullptr && shares<T>(dom) != nullptr,
+             "Schwarz data of this precision are not built for this domain");
+  for (int it = 0; it < iterations; ++it) {
+    const T* r = b;  // with u = 0 the residual is b itself
+    if (!(it == 0 && u_is_zero)) {
+      apply_T<T>(dom, level, u, W.r.get(), b, s);  // r = b - A u
+      r = W.r.get();
+    }
+    const double sz = sizeof(T), vec = (double)L.E * sw.nS * sz;
+    {
+      PhaseScope ps(dom->prof, DG_PHASE_GATHER, s, L.ndof * sz + vec, 0.0);
+      launch_gather<T>(sw.geom, r, sw.elem_of_col.get(), W.rS.get(), s);
+    }
+    {
+      PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * sz + 2 * vec,
+                    2.0 * sw.nS * (double)sw.nS * L.E);
+      launch_class_gemm_tiles<T>(inverses<T>(sw), W.rS.get(), W.duS.get(), sw.nS, sw.tiles.get(), sw.n_tiles, s);
+    }
+    {
+      PhaseScope ps(dom->prof, DG_PHASE_SCATTER, s, vec + 2.0 * L.ndof * sz, 0.0);
+      launch_scatter_add<T, T>(sw.geom, W.duS.get(), sw.col_of_elem.get(), shares<T>(dom), u, s);
+    }
+  }
+}
+
+template void schwarz_smooth<double>(dg_domain*, int, const double*, double*, int, bool, cudaStream_t);
+template void schwarz_smooth<float>(dg_domain*, int, const float*, float*, int, bool, cudaStream_t);
+
+// One V-cycle from a zero initial guess: z ~= A^-1 r.
+template <typename T>
+void vcycle(dg_domain* dom, const T* r, T* z, cudaStream_t s) {
+  const int nl = (int)dom->levels.size();
+  const int pre = dom->desc.presmooth, post = dom->desc.postsmooth;
+  const int N = dom->N;
+  // level 0 works directly in (r, z)
+  for (int l = 0; l < nl; ++l) ensure_schwarz(dom, l);
+  auto B = [&](int l) -> const T* { return l == 0 ? r : work<T>(dom->levels[l]).b.get(); };
+  auto U = [&](int l) -> T* { return l == 0 ? z : work<T>(dom->levels[l]).u.get(); };
+  for (int l = 0; l < nl; ++l) DG_CUDA(cudaMemsetAsync(U(l), 0, sizeof(T) * dom->levels[l].ndof, s));
+  for (int l = 0; l < nl - 1; ++l) {
+    Level& L = dom->levels[l];
+    schwarz_smooth<T>(dom, l, B(l), U(l), pre, true, s);
+    apply_T<T>(dom, l, U(l), work<T>(L).r.get(), B(l), s);  // Eq. mg_res
+    PhaseScope ps(dom->prof, DG_PHASE_TRANSFER, s, (double)(L.ndof + dom->levels[l + 1].ndof) * sizeof(T),
+                  6.0 * N * L.ndof);
+    launch_restrict<T>(N, L.n, dom->levels[l + 1].n, Ilo<T>(dom), Ihi<T>(dom), work<T>(L).r.get(),
+                       work<T>(dom->levels[l + 1]).b.get(), s);
+  }
+  schwarz_smooth<T>(dom, nl - 1, B(nl - 1), U(nl - 1), pre, true, s);
+  schwarz_smooth<T>(dom, nl - 1, B(nl - 1), U(nl - 1), post, pre == 0, s);
+  for (int l = nl - 2; l >= 0; --l) {
+    Level& L = dom->levels[l];
+    {
+      PhaseScope ps(dom->prof, DG_PHASE_TRANSFER, s, (double)(2 * L.ndof + dom->levels[l + 1].ndof) * sizeof(T),
+                    6.0 * N * L.ndof);
+      launch_prolongate_add<T>(N, L.n, dom->levels[l + 1].n, Ilo<T>(dom), Ihi<T>(dom), U(l + 1), U(l), s);
+    }
+    schwarz_smooth<T>(dom, l, B(l), U(l), post, false, s);
+  }
+}
+
+template void vcycle<double>(dg_domain*, const double*, double*, cudaStream_t);
+template void vcycle<float>(dg_domain*, const float*, float*, cudaStream_t);
+
+// z = M^-1 v in FP64 vectors; mode 0 identity, 1 Schwarz only, 2 V-cycle.
+void precondition(dg_domain* dom, int mode, const double* v, double* z, cudaStream_t s) {
+  const int64_t n = dom->levels[0].ndof;
+  if (mode == 0) {
+    DG_CUDA(cudaMemcpyAsync(z, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  const int steps = dom->desc.presmooth + dom->desc.postsmooth;
+  if (!dom->mixed) {
+    if (mode == 1) {
+      DG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
+      schwarz_smooth<double>(dom, 0, v, z, steps, true, s);
+    } else {
+      vcycle<double>(dom, v, z, s);
+    }
+    return;
+  }
+  // mixed: the whole preconditioner in FP32
+  if (!dom->vin32.get()) dom->vin32.alloc(2 * n);
+  float* v32 = dom->vin32.get();
+  float* z32 = v32 + n;
+  launch_convert_d2f(n, v, v32, s);
+  if (mode == 1) {
+    DG_CUDA(cudaMemsetAsync(z32, 0, sizeof(float) * n, s));
+    schwarz_smooth<float>(dom, 0, v32, z32, steps, true, s);
+  } else {
+    vcycle<float>(dom, v32, z32, s);
+  }
+  launch_convert_f2d(n, z32, z, s);
+}
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void ensure_workspace(dg_domain* dom, int k) {
+  const int64_t n = dom->levels[0].ndof;
+  if (dom->kcap >= k) return;
+  dom->V.alloc((size_t)(k + 1) * n);
+  dom->Zb.alloc((size_t)k * n);
+  dom->w.alloc(n);
+  dom->r.alloc(n);
+  dom->du.alloc(n);
+  dom->ut.alloc(n);
+  dom->rt.alloc(n);
+  dom->tmp.alloc(n);
+  dom->partial.alloc((size_t)multidot_partial_blocks() * (k + 2));
+  dom->dots.alloc(3 * (size_t)(k + 2));
+  dom->kcap = k;
+}
+
+double norm2(dg_domain* dom, const double* x, cudaStream_t s) {
+  const int64_t n = dom->levels[0].ndof;
+  launch_multidot(n, 1, x, n, x, dom->partial.get(), dom->dots.get(), s);
+  double h;
+  DG_CUDA(cudaMemcpyAsync(&h, dom->dots.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  return std::sqrt(h);
+}
+
+struct LinearResult {
+  int iterations = 0;
+  double r0 = 0, final_res = 0;
+  dg_status status = DG_OK;
+};
+
+// FGMRES on the current operator (dg_apply semantics, linearization included), x updated in place.
+// Converged when the Givens estimate reaches tol * ref; the true residual is recomputed at exit.
+LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, double ref_b_norm, int max_it, int pmode,
+                    bool rel_to_b) {
+  cudaStream_t s = dom->stream;
+  const int64_t n = dom->levels[0].ndof;
+  ensure_workspace(dom, max_it);
+  LinearResult R;
+  double* V = dom->V.get();
+  double* Z = dom->Zb.get();
+  double* w = dom->w.get();
+  apply_level(dom, 0, x, dom->r.get(), b, true, s);  // r = b - A x
+  const double beta = norm2(dom, dom->r.get(), s);
+  R.r0 = beta;
+  const double ref = rel_to_b ? ref_b_norm : beta;
+  if (!std::isfinite(beta)) { R.status = DG_ERR_BREAKDOWN; return R; }
+  if (beta <= tol * ref || beta == 0.0) { R.final_res = beta; return R; }
+  launch_axpby<double>(n, 1.0 / beta, dom->r.get(), 0.0, V, s);
+  std::vector<double> H((size_t)(max_it + 1) * max_it, 0.0), cs(max_it), sn(max_it), g(max_it + 1, 0.0);
+  g[0] = beta;
+  int k = 0;
+  double* dh = dom->dots.get();  // [h1 (k+2) | h2 (k+2) | norm]
+  std::vector<double> hh(2 * (max_it + 2) + 1);
+  for (int j = 0; j < max_it; ++j) {
+    precondition(dom, pmode, V + (size_t)j * n, Z + (size_t)j * n, s);
+    apply_level(dom, 0, Z + (size_t)j * n, w, nullptr, true, s);
+    // classical Gram-Schmidt, twice
+    PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, 8.0 * n * (4.0 * (j + 1) + 5.0), 8.0 * n * (j + 1) + 2.0 * n);
+    launch_multidot(n, j + 1, V, n, w, dom->partial.get(), dh, s);
+    launch_subtract_combination(n, j + 1, V, n, dh, w, s);
+    launch_multidot(n, j + 1, V, n, w, dom->partial.get(), dh + (max_it + 2), s);
+    launch_subtract_combination(n, j + 1, V, n, dh + (max_it + 2), w, s);
+    launch_multidot(n, 1, w, n, w, dom->partial.get(), dh + 2 * (max_it + 2), s);
+    DG_CUDA(cudaMemcpyAsync(hh.data(), dh, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    double* col = &H[(size_t)j * (max_it + 1)];
+    for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[(max_it + 2) + i];
+    const double hn = std::sqrt(std::max(0.0, hh[2 * (max_it + 2)]));
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {  // previous rotations
+      const double a = col[i], c = col[i + 1];
+      col[i] = cs[i] * a + sn[i] * c;
+      col[i + 1] = -sn[i] * a + cs[i] * c;
+    }
+    const double den = std::hypot(col[j], col[j + 1]);
+    if (den == 0.0 || !std::isfinite(den)) { R.status = DG_ERR_BREAKDOWN; break; }
+    cs[j] = col[j] / den;
+    sn[j] = col[j + 1] / den;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    k = j + 1;
+    const double est = std::fabs(g[j + 1]);
+    if (!std::isfinite(est)) { R.status = DG_ERR_BREAKDOWN; break; }
+    if (est <= tol * ref || hn == 0.0) break;
+    launch_axpby<double>(n, 1.0 / hn, w, 0.0, V + (size_t)(j + 1) * n, s);
+  }
+  if (k > 0) {
+    std::vector<double> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int l = i + 1; l < k; ++l) acc -= H[(size_t)l * (max_it + 1) + i] * y[l];
+      y[i] = acc / H[(size_t)i * (max_it + 1) + i];
+    }
+    DG_CUDA(cudaMemcpyAsync(dh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    launch_add_combination(n, k, Z, n, dh, x, s);
+  }
+  R.iterations = k;
+  apply_level(dom, 0, x, dom->r.get(), b, true, s);
+  R.final_res = norm2(dom, dom->r.get(), s);
+  if (R.status == DG_OK) {
+    if (!std::isfinite(R.final_res)) R.status = DG_ERR_BREAKDOWN;
+    else if (R.final_res > tol * ref * (1.0 + 1e-6)) R.status = DG_ERR_NOT_CONVERGED;
+  }
+  return R;
+}
+
+void set_linearization(dg_domain* dom, const double* u, cudaStream_t s) {
+  launch_puncture_linearization(dom->levels[0].ndof, u, dom->mass.get(), dom->alpha.get(), dom->beta.get(),
+                                dom->lin64.get(), dom->lin32.get(), s);
+  dom->lin_set = true;
+}
+
+// r = b - A(u)
+void nonlinear_residual(dg_domain* dom, const double* u, const double* b, double* r, cudaStream_t s) {
+  const bool was = dom->lin_set;
+  dom->lin_set = false;
+  apply_level(dom, 0, u, dom->tmp.get(), nullptr, false, s);
+  dom->lin_set = was;
+  launch_puncture_residual(dom->levels[0].ndof, dom->tmp.get(), u, b, dom->mass.get(), dom->alpha.get(),
+                           dom->beta.get(), r, s);
+}
+
+}  // namespace
+
+void puncture_residual_api(dg_domain* dom, const double* u, const double* b, double* r, cudaStream_t s) {
+  ensure_workspace(dom, 1);
+  nonlinear_residual(dom, u, b, r, s);
+}
+void puncture_linearize_api(dg_domain* dom, const double* u, cudaStream_t s) {
+  if (!u) { dom->lin_set = false; return; }
+  set_linearization(dom, u, s);
+}
+
+dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg_solve_opts& o, dg_solve_report* rep) {
+  const double t0 = now_s();
+  cudaStream_t s = dom->stream;
+  const int64_t n = dom->levels[0].ndof;
+  const int max_it = o.max_iterations > 0 ? o.max_iterations : 200;
+  const int pmode = o.precondition;
+  DG_REQUIRE(pmode >= 0 && pmode <= 2, "precondition must be 0, 1 or 2");
+  DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  ensure_workspace(dom, max_it);
+  dg_solve_report R{};
+  if (dom->desc.problem == DG_PROBLEM_POISSON) {
+    const double bn = o.relative_to_b ? norm2(dom, b, s) : 0.0;
+    dom->lin_set = false;
+    LinearResult L = fgmres(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0);
+    R.iterations = L.iterations;
+    R.initial_residual = L.r0;
+    R.final_residual = L.final_res;
+    const double ref = o.relative_to_b ? bn : L.r0;
+    R.relative_residual = ref > 0 ? L.final_res / ref : 0.0;
+    R.status = L.status;
+  } else {
+    // Newton-Raphson with line search (sufficient decrease c = 1e-4, quadratic backtracking)
+    const double c = 1e-4;
+    const double lin_tol = o.linear_tol > 0 ? o.linear_tol : 1e-4;
+    const int max_steps = o.max_newton_steps > 0 ? o.max_newton_steps : 20;
+    dom->subdomain_iterations = o.subdomain_iterations > 0 ? o.subdomain_iterations : 3;
+    double* r = dom->rt.get();
+    nonlinear_residual(dom, u, b, r, s);
+    double rn = norm2(dom, r, s);
+    const double r0 = rn;
+    const double ref = o.relative_to_b ? norm2(dom, b, s) : r0;
+    R.initial_residual = r0;
+    R.status = DG_OK;
+    if (!std::isfinite(rn)) R.status = DG_ERR_BREAKDOWN;
+    int step = 0;
+    while (R.status == DG_OK && rn > tol * ref && rn > 0.0) {
+      if (step >= max_steps) { R.status = DG_ERR_NOT_CONVERGED; break; }
+      set_linearization(dom, u, s);
+      DG_CUDA(cudaMemsetAsync(dom->du.get(), 0, sizeof(double) * n, s));
+      // the linear right-hand side is r (copied: the Krylov solver overwrites dom->r)
+      DG_CUDA(cudaMemcpyAsync(dom->ut.get(), r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      LinearResult L = fgmres(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false);
+      R.iterations += L.iterations;
+      if (L.status == DG_ERR_BREAKDOWN) { R.status = L.status; break; }
+      double lam = 1.0, rn_new = 0.0;
+      for (int bt = 0; bt <= 10; ++bt) {
+        DG_CUDA(cudaMemcpyAsync(dom->ut.get(), u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        launch_axpby<double>(n, lam, dom->du.get(), 1.0, dom->ut.get(), s);
+        nonlinear_residual(dom, dom->ut.get(), b, r, s);
+        rn_new = norm2(dom, r, s);
+        if (std::isfinite(rn_new) && rn_new <= (1.0 - c * lam) * rn) break;
+        const double g0 = 0.5 * rn * rn, g1 = 0.5 * rn_new * rn_new, dg0 = -rn * rn;
+        double lq = std::isfinite(g1) ? -dg0 * lam * lam / (2.0 * (g1 - g0 - dg0 * lam)) : 0.1 * lam;
+        lam = std::min(std::max(lq, 0.1 * lam), 0.5 * lam);
+        R.line_search_steps++;
+      }
+      DG_CUDA(cudaMemcpyAsync(u, dom->ut.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      rn = rn_new;
+      ++step;
+      if (!std::isfinite(rn)) R.status = DG_ERR_BREAKDOWN;
+    }
+    dom->lin_set = false;
+    R.newton_steps = step;
+    R.final_residual = rn;
+    R.relative_residual = ref > 0 ? rn / ref : 0.0;
+  }
+  DG_CUDA(cudaStreamSynchronize(s));
+  R.seconds = now_s() - t0;
+  if (rep) *rep = R;
+  return (dg_status)R.status;
+}
+
+}  // namespace dg
+
+namespace dg {
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  DG_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void Profiler::clear() {
+  for (auto& r : pending) {
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  pending.clear();
+  for (auto& a : acc) a = dg_phase_stats{};
+}
+
+Profiler::~Profiler() {
+  for (auto& r : pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+PhaseScope::PhaseScope(Profiler& p, int phase, cudaStream_t s, double bytes, double flops)
+    : p_(p), phase_(phase), s_(s) {
+  if (!p_.on) return;
+  p_.acc[phase].launches++;
+  p_.acc[phase].bytes += bytes;
+  p_.acc[phase].flops += flops;
+  a_ = p_.get();
+  DG_CUDA(cudaEventRecord(a_, s_));
+}
+
+PhaseScope::~PhaseScope() {
+  if (!a_) return;
+  cudaEvent_t b = nullptr;
+  if (!p_.pool.empty()) {
+    b = p_.pool.back();
+    p_.pool.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    p_.pool.push_back(a_);  // drop this record rather than throw from a destructor
+    return;
+  }
+  if (cudaEventRecord(b, s_) != cudaSuccess) (void)cudaGetLastError();
+  p_.pending.push_back({a_, b, phase_});
+}
+
+void profile_read(dg_domain* dom, dg_phase_stats* out) {
+  Profiler& p = dom->prof;
+  for (auto& r : p.pending) {
+    DG_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0;
+    DG_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    p.acc[r.phase].milliseconds += ms;
+    p.pool.push_back(r.a);
+    p.pool.push_back(r.b);
+  }
+  p.pending.clear();
+  for (int i = 0; i < DG_PHASE_COUNT; ++i) out[i] = p.acc[i];
+}
+
+}  // namespace dg

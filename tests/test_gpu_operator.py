@@ -1,0 +1,94 @@
+"""GPU parity of the DG operator (Sec. II) and the multigrid transfers (Sec. III.C.2) against the
+FP64 oracle, through the C ABI. FP64 tolerance 1e-12 relative (rounding of the ~12N-flop
+contractions); FP32 tolerance 2e-5 relative (FP32 unit roundoff 6e-8 times the same depth and
+the conditioning of the face terms)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import box, rand, rel
+from oracle import dg, mg
+
+pytestmark = pytest.mark.gpu
+
+dgg = pytest.importorskip("paper_2111_06767_gb300")
+
+CASES = [((1, 1, 1), 2), ((2, 1, 1), 3), ((3, 2, 1), 4), ((2, 2, 2), 5), ((2, 3, 2), 6), ((1, 2, 3), 7),
+         ((2, 2, 2), 8), ((2, 1, 2), 9), ((1, 1, 2), 10), ((5, 3, 4), 4)]
+
+
+@pytest.mark.parametrize("n,N", CASES)
+def test_apply_fp64_and_fp32_match_oracle(n, N):
+    lower, upper = (-1.0, -0.5, 0.0), (1.0, 0.7, 2.5)
+    d = dgg.Domain(lower, upper, n, N, penalty=1.5, mg_levels=1, overlap=1)
+    grid = box(n, N, lower=lower, upper=upper)
+    u = rand(10 + N, (grid.n_elements, N, N, N))
+    ref = dg.apply(grid.graph(), u)
+    out = d.apply(torch.from_numpy(u.ravel()).cuda()).cpu().numpy()
+    assert rel(out, ref) < 1e-12
+    out32 = d.apply_f32(torch.from_numpy(u.ravel()).float().cuda()).double().cpu().numpy()
+    assert rel(out32, ref) < 2e-5
+
+
+def test_apply_full_size_gaussian_config():
+    """8^3 elements, N = 8 (262,144 points): the workload of the Gaussian-source benchmark."""
+    n, N = (8, 8, 8), 8
+    d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=2)
+    grid = box(n, N)
+    u = rand(5, (grid.n_elements, N, N, N))
+    ref = dg.apply(grid.graph(), u)
+    out = d.apply(torch.from_numpy(u.ravel()).cuda()).cpu().numpy()
+    assert rel(out, ref) < 1e-12
+
+
+def test_apply_sampled_elements_at_roofline_size():
+    """N = 4 on 64^3 elements (16.8M points): oracle on sampled elements with their face neighbours."""
+    n, N = (64, 64, 64), 4
+    d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=1)
+    grid = box(n, N)
+    E = grid.n_elements
+    u_dev = torch.empty(E * N**3, dtype=torch.float64, device="cuda").uniform_(-1, 1, generator=torch.Generator("cuda").manual_seed(3))
+    out = d.apply(u_dev).view(E, N, N, N).cpu().numpy()
+    u = u_dev.view(E, N, N, N).cpu().numpy()
+    full = grid.graph()
+    for e in [0, 1, 63, 64 * 64 - 1, 123456, E // 2 + 17, E - 1]:
+        slots = [e] + [int(q) for q in full.nbr[e] if q >= 0]
+        pos = {g: s for s, g in enumerate(slots)}
+        pn = np.full((len(slots), 6), dg.ZERO)
+        for s, g in enumerate(slots):
+            for f in range(6):
+                q = full.nbr[g, f]
+                pn[s, f] = dg.EXTERNAL if q == dg.EXTERNAL else pos.get(int(q), dg.ZERO)
+        patch = dg.ElementGraph(N, full.penalty, full.h[slots], pn, full.h_ext[slots])
+        ref = dg.apply(patch, u[slots])[0]
+        assert rel(out[e], ref) < 1e-12, e
+
+
+@pytest.mark.parametrize("n,N", [((2, 2, 2), 3), ((4, 2, 6), 4), ((4, 4, 4), 6), ((2, 4, 3), 5)])
+def test_transfers_match_oracle(n, N):
+    d = dgg.Domain(n=n, N=N, mg_levels=2, overlap=1)
+    fine = box(n, N)
+    coarse = mg.hierarchy(fine, 2)[1]
+    assert tuple(d.layout.level_n[1]) == coarse.n
+    rf = rand(21, (fine.n_elements, N, N, N))
+    uc = rand(22, (coarse.n_elements, N, N, N))
+    ref_b = mg.restrict(fine, coarse, rf)
+    out_b = d.restrict(0, torch.from_numpy(rf.ravel()).cuda()).cpu().numpy()
+    assert rel(out_b, ref_b) < 1e-13
+    base = rand(23, (fine.n_elements, N, N, N))
+    ref_u = base + mg.prolongate(fine, coarse, uc)
+    out_u = d.prolongate_add(0, torch.from_numpy(uc.ravel()).cuda(), torch.from_numpy(base.ravel()).cuda()).cpu().numpy()
+    assert rel(out_u, ref_u) < 1e-13
+
+
+def test_rhs_and_coordinates():
+    n, N = (3, 2, 2), 5
+    lower, upper = (-1.0, 0.0, 2.0), (2.0, 1.0, 3.0)
+    d = dgg.Domain(lower, upper, n, N, mg_levels=1, overlap=1)
+    grid = box(n, N, lower=lower, upper=upper)
+    x, y, z = grid.coordinates()
+    X, Y, Z = (t.cpu().numpy() for t in d.coordinates())
+    assert max(np.abs(X - x.ravel()).max(), np.abs(Y - y.ravel()).max(), np.abs(Z - z.ravel()).max()) < 1e-14
+    f = rand(4, x.shape)
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda()).cpu().numpy()
+    assert rel(b, dg.rhs(grid.graph(), f)) < 1e-14

@@ -1,0 +1,80 @@
+"""End-to-end GPU solves (FGMRES + multigrid-Schwarz, Secs. III.B-III.D) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import box, rand, rel
+from oracle import dg, solve
+
+pytestmark = pytest.mark.gpu
+
+dgg = pytest.importorskip("paper_2111_06767_gb300")
+
+
+def test_sine_2x2x2_N6_matches_direct_solution():
+    """3-D sine problem on 2^3 elements, N = 6, C = 1.5, two levels: the solution must agree with the
+    oracle's dense direct solve to 1e-10 relative at a 1e-10 residual, with FGMRES iteration
+    counts within one of the oracle's."""
+    n, N = (2, 2, 2), 6
+    grid = box(n, N)
+    pr = solve.Problem(grid)
+    x, y, z = grid.coordinates()
+    f = workloads.sine_source_3d(x, y, z)
+    b_ref = dg.rhs(pr.graphs[0], f)
+    u_direct = np.linalg.solve(dg.assemble(pr.graphs[0]), b_ref.ravel())
+    _, info = pr.solve_linear(b_ref, tol=1e-10)
+    for precision in ("fp64", "mixed"):
+        d = dgg.Domain(n=n, N=N, precision=precision)
+        b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-10)
+        assert rep.relative_residual <= 1e-10
+        assert rel(u.cpu().numpy(), u_direct) < 1e-9
+        if precision == "fp64":
+            assert abs(rep.iterations - info["iterations"]) <= 1
+        # the oracle's operator confirms the residual
+        assert np.linalg.norm(b_ref.ravel() - dg.apply(pr.graphs[0], u.cpu().numpy().reshape(-1, N, N, N)).ravel()) \
+            <= 1.01e-10 * np.linalg.norm(b_ref)
+
+
+def test_gaussian_4x4x4_matches_oracle_solution():
+    n, N = (4, 4, 4), 5
+    grid = box(n, N)
+    pr = solve.Problem(grid, mg_levels=3)
+    src = workloads.gaussian_source(2)
+    x, y, z = grid.coordinates()
+    f = src(x, y, z)
+    b_ref = dg.rhs(pr.graphs[0], f)
+    u_ref, info = pr.solve_linear(b_ref, tol=1e-13)
+    for precision in ("fp64", "mixed"):
+        d = dgg.Domain(n=n, N=N, precision=precision, mg_levels=3)
+        b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-10)
+        assert rep.relative_residual <= 1e-10
+        assert rel(u.cpu().numpy(), u_ref) < 1e-9
+
+
+def test_unpreconditioned_and_schwarz_only_modes():
+    n, N = (4, 4, 4), 4
+    grid = box(n, N)
+    x, y, z = grid.coordinates()
+    f = workloads.gaussian_source(2)(x, y, z)
+    d = dgg.Domain(n=n, N=N)
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    its = []
+    for mode in (0, 1, 2):
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(precondition=mode))
+        assert rep.relative_residual <= 1e-10
+        its.append(rep.iterations)
+    assert its[0] > its[1] >= its[2]
+
+
+def test_zero_rhs_returns_immediately():
+    d = dgg.Domain(n=(2, 2, 2), N=4)
+    b = torch.zeros(d.n_dof, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(b)
+    rep = d.solve(b, u, tol=1e-10)
+    assert rep.iterations == 0 and float(u.abs().max()) == 0.0
