@@ -216,8 +216,10 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     l0 = dgg.lib().dg_kernel_launches()
+    torch.cuda.nvtx.range_push("timed")
     with ClockSampler(local) as clk:
         times, reps, prof = timed_solves(d, args.steps, 0, profile=True)
+    torch.cuda.nvtx.range_pop()
     launches = dgg.lib().dg_kernel_launches() - l0
     barrier()
     total_s = sum(times) / 1e3

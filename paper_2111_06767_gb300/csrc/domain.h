@@ -20,6 +20,7 @@ struct SchwarzLevel {
   std::vector<int> patch;          // per class: 49 ints describing the representative's patch
   DevBuf<int> elem_of_col;         // subdomain column -> element
   DevBuf<int> col_of_elem;         // element -> subdomain column
+  DevBuf<int> xform_of_elem;       // canonical -> actual orientation: perm (2 bits x 3) | flip << 6
   DevBuf<double> inv64;            // [n_classes][nS][nS] explicit inverses (FP64 mode)
   DevBuf<float> inv32;             // FP32 copies (mixed mode)
   DevBuf<int4> tiles;              // GEMM tile list (class, row0, col0, columns left)

@@ -125,10 +125,19 @@ struct SubdomainGeom {
   int E, N, ov, nS;
 };
 template <typename T>
-void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, T* rS, cudaStream_t s);
+void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* xform, T* rS,
+                   cudaStream_t s);
 template <typename T, typename TU>
-void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const T* shares, TU* u,
-                        cudaStream_t s);
+void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* xform,
+                        const T* shares, TU* u, cudaStream_t s);
+
+// Subdomain GMRES for linearized problems (columns of n_S values, E columns per basis vector).
+template <typename T>
+void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream_t s);
+template <typename T>
+void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* Z, T* H, cudaStream_t s);
+template <typename T>
+void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s);
 
 // Multigrid transfers (per dimension: 0 lower half, 1 upper half, 2 full).
 template <typename T>

@@ -12,10 +12,11 @@
 //             point over its own subdomain and at most 6 face neighbours' subdomains:
 //             deterministic, atomic-free.
 //
-// Subdomain point order: the central element's N^3 points (element order), then for faces
-// f = 2 d + side the neighbour's N_overlap layers counted from the shared face, each layer in
-// (a2, a1) order of the tangential indices. Missing neighbours keep their slots as padding
-// (identity rows and columns in A_S, zero data), so every subdomain has n_S = N^3 + 6 N_ov N^2.
+// Subdomain point order (in the subdomain's canonical orientation, see setup.cu): the central
+// element's N^3 points (element order), then for faces f = 2 d + side the neighbour's N_overlap
+// layers counted from the shared face, each layer in (a2, a1) order of the tangential indices.
+// Missing neighbours keep their slots as padding (identity rows and columns in A_S, zero data),
+// so every subdomain has n_S = N^3 + 6 N_ov N^2.
 #include "internal.h"
 
 namespace dg {
@@ -247,58 +248,90 @@ __device__ __forceinline__ int nbr_elem(const SubdomainGeom& g, int e, int f) {
   return c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
 }
 
-// r_S[col * nS + q] = r at subdomain point q of the subdomain in column col (0 outside the domain)
+// Orientation of a subdomain: canonical axis a is actual axis perm(a), reflected if flip(a).
+struct Orient {
+  int p0, p1, p2, f0, f1, f2;
+  __device__ explicit Orient(int code)
+      : p0(code & 3), p1((code >> 2) & 3), p2((code >> 4) & 3), f0((code >> 6) & 1), f1((code >> 7) & 1),
+        f2((code >> 8) & 1) {}
+  __device__ int perm(int a) const { return a == 0 ? p0 : (a == 1 ? p1 : p2); }
+  __device__ int flip(int a) const { return a == 0 ? f0 : (a == 1 ? f1 : f2); }
+  __device__ int inv(int d) const { return p0 == d ? 0 : (p1 == d ? 1 : 2); }
+};
+
+__device__ __forceinline__ int pick3(int i, int a, int b, int c) { return i == 0 ? a : (i == 1 ? b : c); }
+
+// r_S[col * nS + q] = r at canonical subdomain point q of the subdomain in column col (0 outside)
 template <typename T>
 __global__ void gather_kernel(SubdomainGeom g, const T* __restrict__ r, const int* __restrict__ elem_of_col,
-                              T* __restrict__ rS) {
+                              const int* __restrict__ xform, T* __restrict__ rS) {
   const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, nS = g.nS;
   const int64_t total = (int64_t)g.E * nS;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int col = (int)(t / nS);
     const int q = (int)(t - (int64_t)col * nS);
     const int e = elem_of_col[col];
-    T v = 0;
+    const Orient o(xform[e]);
+    int cc0, cc1, cc2, src = e;
     if (q < N3) {
-      v = r[(int64_t)e * N3 + q];
+      cc0 = q % N; cc1 = (q / N) % N; cc2 = q / N2;
     } else {
       const int rr = q - N3;
-      const int f = rr / (ov * N2);
-      const int k = rr - f * ov * N2;
+      const int fc = rr / (ov * N2);
+      const int k = rr - fc * ov * N2;
       const int depth = k / N2, a2 = (k / N) % N, a1 = k % N;
-      const int nb = nbr_elem(g, e, f);
-      if (nb >= 0) {
-        const int d = f >> 1, side = f & 1;
-        const int idx = side ? depth : N - 1 - depth;
-        int c0, c1, c2;
-        if (d == 0) { c0 = idx; c1 = a1; c2 = a2; }
-        else if (d == 1) { c0 = a1; c1 = idx; c2 = a2; }
-        else { c0 = a1; c1 = a2; c2 = idx; }
-        v = r[(int64_t)nb * N3 + (c2 * N + c1) * N + c0];
-      }
+      const int a = fc >> 1, sc = fc & 1;
+      const int along = sc ? depth : N - 1 - depth;
+      cc0 = a == 0 ? along : a1;
+      cc1 = a == 1 ? along : (a == 0 ? a1 : a2);
+      cc2 = a == 2 ? along : a2;
+      const int d = o.perm(a);
+      const int sa = o.flip(a) ? 1 - sc : sc;
+      src = nbr_elem(g, e, 2 * d + sa);
+    }
+    T v = 0;
+    if (src >= 0) {
+      // canonical -> actual node coordinates
+      const int ia0 = o.inv(0), ia1 = o.inv(1), ia2 = o.inv(2);
+      const int x0 = pick3(ia0, cc0, cc1, cc2), x1 = pick3(ia1, cc0, cc1, cc2), x2 = pick3(ia2, cc0, cc1, cc2);
+      const int ca0 = o.flip(ia0) ? N - 1 - x0 : x0;
+      const int ca1 = o.flip(ia1) ? N - 1 - x1 : x1;
+      const int ca2 = o.flip(ia2) ? N - 1 - x2 : x2;
+      v = r[(int64_t)src * N3 + (ca2 * N + ca1) * N + ca0];
     }
     rS[t] = v;
   }
 }
 
 template <typename T>
-void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, T* rS, cudaStream_t s) {
+void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* xform, T* rS,
+                   cudaStream_t s) {
   const int64_t total = (int64_t)g.E * g.nS;
   if (total == 0) return;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  gather_kernel<T><<<blocks, 256, 0, s>>>(g, r, elem_of_col, rS);
+  gather_kernel<T><<<blocks, 256, 0, s>>>(g, r, elem_of_col, xform, rS);
   DG_LAUNCHED(1);
+}
+
+// canonical coordinates of actual node (ca0, ca1, ca2) under orientation o
+__device__ __forceinline__ void to_canonical(const Orient& o, int N, int ca0, int ca1, int ca2, int& cc0, int& cc1,
+                                             int& cc2) {
+  const int y0 = pick3(o.p0, ca0, ca1, ca2), y1 = pick3(o.p1, ca0, ca1, ca2), y2 = pick3(o.p2, ca0, ca1, ca2);
+  cc0 = o.f0 ? N - 1 - y0 : y0;
+  cc1 = o.f1 ? N - 1 - y1 : y1;
+  cc2 = o.f2 ? N - 1 - y2 : y2;
 }
 
 // u += sum over the subdomains containing each point of w_S du_S (Eq. schwarz_weighting)
 template <typename T, typename TU>
 __global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const int* __restrict__ col_of_elem,
-                               const T* __restrict__ shares, TU* __restrict__ u) {
+                               const int* __restrict__ xform, const T* __restrict__ shares, TU* __restrict__ u) {
   const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, nS = g.nS;
   const int64_t ndof = (int64_t)g.E * N3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ndof; t += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(t / N3);
     const int p = (int)(t - (int64_t)q * N3);
-    const int c[3] = {p % N, (p / N) % N, p / N2};
+    const int ca0 = p % N, ca1 = (p / N) % N, ca2 = p / N2;
     int nb[6], pattern = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
@@ -306,18 +339,24 @@ __global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const
       pattern |= (nb[f] >= 0) << f;
     }
     const T* sh = shares + ((int64_t)pattern * N3 + p) * 7;
-    T acc = sh[0] * duS[(int64_t)col_of_elem[q] * nS + p];
+    int c0, c1, c2;
+    to_canonical(Orient(xform[q]), N, ca0, ca1, ca2, c0, c1, c2);
+    T acc = sh[0] * duS[(int64_t)col_of_elem[q] * nS + (c2 * N + c1) * N + c0];
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       if (nb[f] < 0) continue;
       const int d = f >> 1, side = f & 1;
-      // the neighbour sees this element across its face on the other side (slot 1 + back)
-      const int back = 2 * d + (1 - side);
-      const int depth = (1 - side) ? c[d] : N - 1 - c[d];
+      // the neighbour e sees this element across its actual face (d, 1 - side)
+      const Orient o(xform[nb[f]]);
+      const int a = o.inv(d);
+      const int sc = o.flip(a) ? side : 1 - side;
+      to_canonical(o, N, ca0, ca1, ca2, c0, c1, c2);
+      const int along = pick3(a, c0, c1, c2);
+      const int depth = sc ? along : N - 1 - along;
       if (depth >= ov) continue;
-      const int a1 = d == 0 ? c[1] : c[0];
-      const int a2 = d == 2 ? c[1] : c[2];
-      const int row = N3 + back * ov * N2 + (depth * N + a2) * N + a1;
+      const int a1 = a == 0 ? c1 : c0;
+      const int a2 = a == 2 ? c1 : c2;
+      const int row = N3 + (2 * a + sc) * ov * N2 + (depth * N + a2) * N + a1;
       acc += sh[1 + f] * duS[(int64_t)col_of_elem[nb[f]] * nS + row];
     }
     u[t] += (TU)acc;
@@ -325,12 +364,12 @@ __global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const
 }
 
 template <typename T, typename TU>
-void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const T* shares, TU* u,
-                        cudaStream_t s) {
+void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* xform,
+                        const T* shares, TU* u, cudaStream_t s) {
   const int64_t ndof = (int64_t)g.E * g.N * g.N * g.N;
   if (ndof == 0) return;
   const int blocks = (int)std::min<int64_t>((ndof + 255) / 256, 152 * 16);
-  scatter_kernel<T, TU><<<blocks, 256, 0, s>>>(g, duS, col_of_elem, shares, u);
+  scatter_kernel<T, TU><<<blocks, 256, 0, s>>>(g, duS, col_of_elem, xform, shares, u);
   DG_LAUNCHED(1);
 }
 
@@ -392,12 +431,154 @@ void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4*
   DG_LAUNCHED(1);
 }
 
-template void launch_gather<double>(const SubdomainGeom&, const double*, const int*, double*, cudaStream_t);
-template void launch_gather<float>(const SubdomainGeom&, const float*, const int*, float*, cudaStream_t);
-template void launch_scatter_add<double, double>(const SubdomainGeom&, const double*, const int*, const double*,
-                                                 double*, cudaStream_t);
-template void launch_scatter_add<float, float>(const SubdomainGeom&, const float*, const int*, const float*, float*,
-                                               cudaStream_t);
+// ------------------------------------------------------------------ subdomain GMRES (linearized problems)
+//
+// Sec. III.E: each subdomain problem (A_S + D_S) du_S = r_S of a linearized operator (D_S the
+// diagonal linearization term) is solved by GMRES from du_S = 0 for a fixed number of iterations,
+// right-preconditioned by the explicit inverse of the Poisson subdomain matrix A_S (the
+// Laplacian approximation). With z = A_S^-1 v, (A_S + D_S) z = v + D_S z, so every iteration is
+// one class GEMM plus per-subdomain vector work. One CTA per subdomain column.
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+  return t;
+}
+
+// V_0 = r_S / ||r_S|| per column; beta[col] = ||r_S||
+template <typename T>
+__global__ void sub_normalize_kernel(int nS, const T* __restrict__ rS, T* __restrict__ V0, T* __restrict__ beta) {
+  __shared__ T red[32];
+  const int col = blockIdx.x;
+  const T* r = rS + (size_t)col * nS;
+  T acc = 0;
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) acc += r[i] * r[i];
+  const T nrm = sqrt(block_sum(acc, red));
+  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) V0[(size_t)col * nS + i] = r[i] * inv;
+  if (threadIdx.x == 0) beta[col] = nrm;
+}
+
+// Arnoldi step j: w = V_j + D Z_j, modified Gram-Schmidt against V_0..V_j, V_{j+1} = w / ||w||.
+// H is [col][m+1][m]; V and Z are blocks of E*nS values per basis index.
+template <typename T>
+__global__ void sub_arnoldi_kernel(int nS, int64_t stride, int j, int m, const T* __restrict__ D, T* __restrict__ V,
+                                   const T* __restrict__ Z, T* __restrict__ H) {
+  extern __shared__ unsigned char smem_raw[];
+  T* w = reinterpret_cast<T*>(smem_raw);
+  __shared__ T red[32];
+  const int col = blockIdx.x;
+  const size_t off = (size_t)col * nS;
+  const T* vj = V + (size_t)j * stride + off;
+  const T* zj = Z + (size_t)j * stride + off;
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) w[i] = vj[i] + D[off + i] * zj[i];
+  __syncthreads();
+  T* h = H + (size_t)col * (m + 1) * m;
+  for (int i = 0; i <= j; ++i) {
+    const T* vi = V + (size_t)i * stride + off;
+    T acc = 0;
+    for (int t = threadIdx.x; t < nS; t += blockDim.x) acc += w[t] * vi[t];
+    const T hij = block_sum(acc, red);
+    for (int t = threadIdx.x; t < nS; t += blockDim.x) w[t] -= hij * vi[t];
+    if (threadIdx.x == 0) h[i * m + j] = hij;
+    __syncthreads();
+  }
+  T acc = 0;
+  for (int t = threadIdx.x; t < nS; t += blockDim.x) acc += w[t] * w[t];
+  const T hn = sqrt(block_sum(acc, red));
+  if (threadIdx.x == 0) h[(j + 1) * m + j] = hn;
+  const T inv = hn > T(0) ? T(1) / hn : T(0);
+  T* vn = V + (size_t)(j + 1) * stride + off;
+  for (int t = threadIdx.x; t < nS; t += blockDim.x) vn[t] = w[t] * inv;
+}
+
+// y = argmin || beta e1 - H y || (Givens, in registers of thread 0), then du_S = sum_j y_j Z_j.
+template <typename T>
+__global__ void sub_lsq_combine_kernel(int nS, int64_t stride, int m, const T* __restrict__ beta,
+                                       const T* __restrict__ H, const T* __restrict__ Z, T* __restrict__ duS) {
+  __shared__ T y[16];
+  const int col = blockIdx.x;
+  if (threadIdx.x == 0) {
+    T R[17][16], g[17];
+    const T* h = H + (size_t)col * (m + 1) * m;
+    for (int i = 0; i <= m; ++i) {
+      g[i] = 0;
+      for (int c = 0; c < m; ++c) R[i][c] = h[i * m + c];
+    }
+    g[0] = beta[col];
+    int k = m;  // stop at a (happy) breakdown: zero subdiagonal
+    for (int c = 0; c < m; ++c) {
+      const T a = R[c][c], b = R[c + 1][c];
+      const T den = sqrt(a * a + b * b);
+      if (den == T(0)) { k = c; break; }
+      const T cs = a / den, sn = b / den;
+      for (int cc = c; cc < m; ++cc) {
+        const T x0 = R[c][cc], x1 = R[c + 1][cc];
+        R[c][cc] = cs * x0 + sn * x1;
+        R[c + 1][cc] = -sn * x0 + cs * x1;
+      }
+      const T g0 = g[c];
+      g[c] = cs * g0;
+      g[c + 1] = -sn * g0;
+      if (b == T(0)) { k = c + 1; break; }
+    }
+    for (int c = 0; c < m; ++c) y[c] = 0;
+    for (int i = k - 1; i >= 0; --i) {
+      T acc = g[i];
+      for (int c = i + 1; c < k; ++c) acc -= R[i][c] * y[c];
+      y[i] = acc / R[i][i];
+    }
+  }
+  __syncthreads();
+  const size_t off = (size_t)col * nS;
+  for (int t = threadIdx.x; t < nS; t += blockDim.x) {
+    T acc = 0;
+    for (int c = 0; c < m; ++c) acc += y[c] * Z[(size_t)c * stride + off + t];
+    duS[off + t] = acc;
+  }
+}
+
+template <typename T>
+void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream_t s) {
+  sub_normalize_kernel<T><<<E, 256, 0, s>>>(nS, rS, V0, beta);
+  DG_LAUNCHED(1);
+}
+template <typename T>
+void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* Z, T* H, cudaStream_t s) {
+  const size_t smem = nS * sizeof(T);
+  if (smem > 48 * 1024)
+    DG_CUDA(cudaFuncSetAttribute(sub_arnoldi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sub_arnoldi_kernel<T><<<E, 256, smem, s>>>(nS, (int64_t)E * nS, j, m, D, V, Z, H);
+  DG_LAUNCHED(1);
+}
+template <typename T>
+void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s) {
+  sub_lsq_combine_kernel<T><<<E, 256, 0, s>>>(nS, (int64_t)E * nS, m, beta, H, Z, duS);
+  DG_LAUNCHED(1);
+}
+template void launch_sub_normalize<double>(int, int, const double*, double*, double*, cudaStream_t);
+template void launch_sub_normalize<float>(int, int, const float*, float*, float*, cudaStream_t);
+template void launch_sub_arnoldi<double>(int, int, int, int, const double*, double*, const double*, double*,
+                                         cudaStream_t);
+template void launch_sub_arnoldi<float>(int, int, int, int, const float*, float*, const float*, float*, cudaStream_t);
+template void launch_sub_lsq_combine<double>(int, int, int, const double*, const double*, const double*, double*,
+                                             cudaStream_t);
+template void launch_sub_lsq_combine<float>(int, int, int, const float*, const float*, const float*, float*,
+                                            cudaStream_t);
+
+template void launch_gather<double>(const SubdomainGeom&, const double*, const int*, const int*, double*,
+                                   cudaStream_t);
+template void launch_gather<float>(const SubdomainGeom&, const float*, const int*, const int*, float*, cudaStream_t);
+template void launch_scatter_add<double, double>(const SubdomainGeom&, const double*, const int*, const int*,
+                                                 const double*, double*, cudaStream_t);
+template void launch_scatter_add<float, float>(const SubdomainGeom&, const float*, const int*, const int*,
+                                               const float*, float*, cudaStream_t);
 template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int,
                                               cudaStream_t);
 template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, cudaStream_t);

@@ -3,8 +3,9 @@
 //
 // Subdomain classes: on a uniform box the subdomain operator A_S of element e depends only on
 // which of its faces have neighbours and, for each neighbour, whether that neighbour's far face
-// (the one pointing away from e) is an external boundary; per dimension that is 4 bits. All
-// subdomains with equal bits share one explicit inverse, built once.
+// (the one pointing away from e) is an external boundary. Up to reflections and exchanges of
+// equal-width dimensions (the operator's symmetries) the subdomains fall into a handful of
+// classes, each with one explicit inverse built once (see classify_schwarz).
 //
 // Weights (Eqs. schwarz_weight_prod, schwarz_weight_function): quintic smoothstep phi,
 // w(xi) = (phi((xi + 1)/delta) - phi((xi - 1)/delta)) / 2, delta = 1 + x_{N_ov}. The edge and
@@ -75,6 +76,15 @@ void upload_arr(DevBuf<T>& buf, const double* src, int n, cudaStream_t s) {
 }
 
 // Per-level subdomain classes and column order (cheap: done at creation).
+//
+// Per dimension a subdomain sees, on each side, no neighbour (code 0), a neighbour whose far face
+// is internal (1) or a neighbour whose far face is an external boundary (2). A_S depends only on
+// these six codes (uniform affine elements). The DG operator is invariant under reflecting a
+// dimension and under swapping dimensions of equal element width, so every subdomain is mapped
+// to a canonical orientation: each dimension reflected so that its lower code is the smaller,
+// then dimensions of equal width sorted by their code pair. Subdomains with equal canonical codes
+// share one explicit inverse, stored in the canonical point order; the gather and scatter kernels
+// apply each subdomain's reflection/permutation on the fly.
 void classify_schwarz(dg_domain* dom, Level& L) {
   const int N = dom->N, ov = dom->desc.overlap;
   const int N3 = N * N * N;
@@ -82,29 +92,33 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   sw.nS = N3 + 6 * ov * N * N;
   sw.geom = SubdomainGeom{{L.n[0], L.n[1], L.n[2]}, L.E, N, ov, sw.nS};
   const int E = L.E;
-  auto coords = [&](int e, int c[3]) {
-    c[0] = e % L.n[0];
-    c[1] = (e / L.n[0]) % L.n[1];
-    c[2] = e / (L.n[0] * L.n[1]);
-  };
-  auto neighbor = [&](int e, int f) {
-    int c[3];
-    coords(e, c);
-    const int d = f >> 1;
-    c[d] += (f & 1) ? 1 : -1;
-    if (c[d] < 0 || c[d] >= L.n[d]) return -1;
-    return c[0] + L.n[0] * (c[1] + L.n[1] * c[2]);
-  };
-  std::vector<int> key(E);
+  std::vector<int> key(E), xform(E);
   for (int e = 0; e < E; ++e) {
-    int c[3];
-    coords(e, c);
-    int k = 0;
+    const int c[3] = {e % L.n[0], (e / L.n[0]) % L.n[1], e / (L.n[0] * L.n[1])};
+    int lo[3], hi[3], flip[3];
     for (int d = 0; d < 3; ++d) {
-      const int has_lo = c[d] > 0, lo_far = c[d] - 1 == 0, has_hi = c[d] < L.n[d] - 1, hi_far = c[d] + 1 == L.n[d] - 1;
-      k |= (has_lo | (has_lo && lo_far) << 1 | has_hi << 2 | (has_hi && hi_far) << 3) << (4 * d);
+      const int n = L.n[d];
+      lo[d] = c[d] > 0 ? (c[d] - 1 == 0 ? 2 : 1) : 0;
+      hi[d] = c[d] < n - 1 ? (c[d] + 1 == n - 1 ? 2 : 1) : 0;
+      flip[d] = lo[d] > hi[d];
+      if (flip[d]) std::swap(lo[d], hi[d]);
+    }
+    // canonical axis a <- actual axis perm[a]; only dimensions of equal width may be exchanged
+    int perm[3] = {0, 1, 2};
+    auto pair_key = [&](int d) { return lo[d] * 3 + hi[d]; };
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j + 1 < 3 - i; ++j) {
+        const int a = perm[j], b = perm[j + 1];
+        if (L.h[a] == L.h[b] && pair_key(a) > pair_key(b)) std::swap(perm[j], perm[j + 1]);
+      }
+    int k = 0, code = 0;
+    for (int a = 0; a < 3; ++a) {
+      k = k * 9 + pair_key(perm[a]);
+      code |= perm[a] << (2 * a);
+      code |= flip[perm[a]] << (6 + a);
     }
     key[e] = k;
+    xform[e] = code;
   }
   std::map<int, int> cls_id;
   for (int e = 0; e < E; ++e) cls_id.emplace(key[e], 0);
@@ -113,11 +127,9 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   sw.n_classes = nc;
   sw.class_of.resize(E);
   sw.class_count.assign(nc, 0);
-  std::vector<int> rep(nc, -1);
   for (int e = 0; e < E; ++e) {
     sw.class_of[e] = cls_id[key[e]];
     sw.class_count[sw.class_of[e]]++;
-    if (rep[sw.class_of[e]] < 0) rep[sw.class_of[e]] = e;
   }
   sw.class_first.assign(nc, 0);
   for (int c = 1; c < nc; ++c) sw.class_first[c] = sw.class_first[c - 1] + sw.class_count[c - 1];
@@ -130,28 +142,38 @@ void classify_schwarz(dg_domain* dom, Level& L) {
       elem_of_col[sw.position[e]] = e;
     }
   }
-  // patch descriptions of the class representatives (slot 0 centre, 1 + f neighbour across f)
+  // canonical patch of every class (slot 0 centre, 1 + f neighbour across canonical face f)
   sw.patch.assign((size_t)nc * 49, -2);
-  for (int c = 0; c < nc; ++c) {
-    const int e = rep[c];
-    int* P = &sw.patch[(size_t)c * 49];
+  for (auto& kv : cls_id) {
+    int codes[3][2];  // [canonical axis][side]
+    int k = kv.first;
+    for (int a = 2; a >= 0; --a) {
+      codes[a][0] = (k % 9) / 3;
+      codes[a][1] = k % 3;
+      k /= 9;
+    }
+    int* P = &sw.patch[(size_t)kv.second * 49];
     for (int s = 0; s < 7; ++s) P[42 + s] = 0;
     P[42] = 1;
     for (int f = 0; f < 6; ++f) {
-      const int q = neighbor(e, f);
-      P[f] = q >= 0 ? 1 + f : -1;
-      P[42 + 1 + f] = q >= 0;
-      if (q < 0) continue;
-      const int back = (f & ~1) | (1 - (f & 1));
+      const int a = f >> 1, side = f & 1;
+      const int cd = codes[a][side];
+      P[f] = cd ? 1 + f : -1;
+      P[42 + 1 + f] = cd != 0;
+      if (!cd) continue;
+      const int back = 2 * a + (1 - side);
       for (int ff = 0; ff < 6; ++ff) {
-        if (ff == back) P[(1 + f) * 6 + ff] = 0;  // faces the centre
-        else P[(1 + f) * 6 + ff] = neighbor(q, ff) >= 0 ? -2 : -1;
+        const int aa = ff >> 1, ss = ff & 1;
+        if (ff == back) P[(1 + f) * 6 + ff] = 0;                 // faces the centre
+        else if (ff == f) P[(1 + f) * 6 + ff] = cd == 2 ? -1 : -2;  // far face
+        else P[(1 + f) * 6 + ff] = codes[aa][ss] ? -2 : -1;     // tangential: as the centre's
       }
     }
   }
   cudaStream_t s = dom->stream;
   upload(sw.elem_of_col, elem_of_col, s);
   upload(sw.col_of_elem, sw.position, s);
+  upload(sw.xform_of_elem, xform, s);
   std::vector<int4> tiles;
   for (int c = 0; c < nc; ++c)
     for (int r0 = 0; r0 < sw.nS; r0 += 64)
@@ -303,7 +325,8 @@ size_t domain_device_bytes(const dg_domain* dom) {
              dom->shares32.bytes();
   for (const auto& L : dom->levels) {
     const auto& sw = L.sw;
-    b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.inv64.bytes() + sw.inv32.bytes() + sw.tiles.bytes();
+    b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.xform_of_elem.bytes() + sw.inv64.bytes() +
+         sw.inv32.bytes() + sw.tiles.bytes();
     for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
                     &L.w64.gH})
       b += p->bytes();

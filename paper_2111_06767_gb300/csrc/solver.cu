@@ -56,6 +56,13 @@ template <>
 const float* shares<float>(const dg_domain* dom) { return dom->shares32.get(); }
 
 template <typename T>
+const T* lin_diag(const dg_domain* dom);
+template <>
+const double* lin_diag<double>(const dg_domain* dom) { return dom->lin64.get(); }
+template <>
+const float* lin_diag<float>(const dg_domain* dom) { return dom->lin32.get(); }
+
+template <typename T>
 void apply_T(dg_domain* dom, int level, const T* u, T* out, const T* b, cudaStream_t s);
 template <>
 void apply_T<double>(dg_domain* dom, int level, const double* u, double* out, const double* b, cudaStream_t s) {
@@ -101,16 +108,41 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     const double sz = sizeof(T), vec = (double)L.E * sw.nS * sz;
     {
       PhaseScope ps(dom->prof, DG_PHASE_GATHER, s, L.ndof * sz + vec, 0.0);
-      launch_gather<T>(sw.geom, r, sw.elem_of_col.get(), W.rS.get(), s);
+      launch_gather<T>(sw.geom, r, sw.elem_of_col.get(), sw.xform_of_elem.get(), W.rS.get(), s);
     }
-    {
+    const bool linearized = level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE &&
+                            dom->subdomain_iterations > 0 && lin_diag<T>(dom) != nullptr;
+    auto gemm = [&](const T* X, T* Y) {
       PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * sz + 2 * vec,
                     2.0 * sw.nS * (double)sw.nS * L.E);
-      launch_class_gemm_tiles<T>(inverses<T>(sw), W.rS.get(), W.duS.get(), sw.nS, sw.tiles.get(), sw.n_tiles, s);
+      launch_class_gemm_tiles<T>(inverses<T>(sw), X, Y, sw.nS, sw.tiles.get(), sw.n_tiles, s);
+    };
+    if (!linearized) {
+      gemm(W.rS.get(), W.duS.get());
+    } else {
+      // GMRES on (A_S + D_S), right-preconditioned by the Poisson inverse A_S^-1 (Sec. III.E)
+      const int m = dom->subdomain_iterations;
+      const size_t blk = (size_t)L.E * sw.nS;
+      if (W.gV.count < (m + 1) * blk) {
+        W.gV.alloc((m + 1) * blk);
+        W.gZ.alloc(m * blk);
+        W.gD.alloc(blk);
+        W.gH.alloc((size_t)L.E * ((m + 1) * m + 1));
+      }
+      T* beta = W.gH.get() + (size_t)L.E * (m + 1) * m;
+      launch_gather<T>(sw.geom, lin_diag<T>(dom), sw.elem_of_col.get(), sw.xform_of_elem.get(), W.gD.get(), s);
+      PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, (double)blk * sz * (4.0 * m + 3.0), 6.0 * blk * m);
+      launch_sub_normalize<T>(L.E, sw.nS, W.rS.get(), W.gV.get(), beta, s);
+      for (int j = 0; j < m; ++j) {
+        gemm(W.gV.get() + j * blk, W.gZ.get() + j * blk);
+        launch_sub_arnoldi<T>(L.E, sw.nS, j, m, W.gD.get(), W.gV.get(), W.gZ.get(), W.gH.get(), s);
+      }
+      launch_sub_lsq_combine<T>(L.E, sw.nS, m, beta, W.gH.get(), W.gZ.get(), W.duS.get(), s);
     }
     {
       PhaseScope ps(dom->prof, DG_PHASE_SCATTER, s, vec + 2.0 * L.ndof * sz, 0.0);
-      launch_scatter_add<T, T>(sw.geom, W.duS.get(), sw.col_of_elem.get(), shares<T>(dom), u, s);
+      launch_scatter_add<T, T>(sw.geom, W.duS.get(), sw.col_of_elem.get(), sw.xform_of_elem.get(), shares<T>(dom), u,
+                               s);
     }
   }
 }
@@ -352,12 +384,13 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
     const double c = 1e-4;
     const double lin_tol = o.linear_tol > 0 ? o.linear_tol : 1e-4;
     const int max_steps = o.max_newton_steps > 0 ? o.max_newton_steps : 20;
-    dom->subdomain_iterations = o.subdomain_iterations > 0 ? o.subdomain_iterations : 3;
+    dom->subdomain_iterations = o.subdomain_iterations >= 0 ? o.subdomain_iterations : 3;
+    DG_REQUIRE(dom->subdomain_iterations <= 16, "subdomain_iterations must be at most 16");
     double* r = dom->rt.get();
     nonlinear_residual(dom, u, b, r, s);
     double rn = norm2(dom, r, s);
     const double r0 = rn;
-    const double ref = o.relative_to_b ? norm2(dom, b, s) : r0;
+    const double ref = (o.relative_to_b && b) ? norm2(dom, b, s) : r0;
     R.initial_residual = r0;
     R.status = DG_OK;
     if (!std::isfinite(rn)) R.status = DG_ERR_BREAKDOWN;
