@@ -158,6 +158,13 @@ dg_status dg_schwarz_smooth(struct dg_domain* dom, int32_t level, const double* 
  * Sec. III.C.3, with presmooth/postsmooth Schwarz steps on every level, both at the coarsest). */
 dg_status dg_vcycle(struct dg_domain* dom, const double* r, double* z, void* stream);
 
+/* out[k] = sum_i V[k * ld + i] * w[i] for k < m (i < n_dof): the inner products of the FGMRES
+ * orthogonalisation (Sec. III.B), FP64, as a deterministic two-pass reduction (fixed per-block
+ * partial sums, then one ordered sum per output): bitwise reproducible. V, w, out are device
+ * pointers (out: m doubles); ld >= n_dof. Uses the domain's workspace (allocated on first use). */
+dg_status dg_dot(struct dg_domain* dom, int32_t m, const double* V, int64_t ld, const double* w, double* out,
+                 void* stream);
+
 /* PUNCTURE: r = b - A(u) with A(u) = A u + M S(u), S(u) = -beta (1 + alpha (1 + u))^-7. */
 dg_status dg_nonlinear_residual(struct dg_domain* dom, const double* u, const double* b, double* r, void* stream);
 /* PUNCTURE: linearize at u (Eq. linearized): dg_apply then applies A + M diag(S'(u)). NULL clears. */

@@ -156,6 +156,13 @@ class Domain:
         check(_lib.dg_vcycle(self._h, _ptr(r), _ptr(out), _stream(stream)), self._h)
         return out
 
+    def dot(self, V, w, out=None, stream=None):
+        """out[k] = V[k] . w for the rows of a (m, n_dof) FP64 CUDA tensor V."""
+        m = V.shape[0]
+        out = torch.empty(m, dtype=torch.float64, device="cuda") if out is None else out
+        check(_lib.dg_dot(self._h, m, _ptr(V), V.stride(0), _ptr(w), _ptr(out), _stream(stream)), self._h)
+        return out
+
     def nonlinear_residual(self, u, b=None, out=None, stream=None):
         out = self._new() if out is None else out
         check(_lib.dg_nonlinear_residual(self._h, _ptr(u), _ptr(b), _ptr(out), _stream(stream)), self._h)

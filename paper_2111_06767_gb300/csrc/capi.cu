@@ -204,6 +204,17 @@ dg_status dg_vcycle(dg_domain* dom, const double* r, double* z, void* stream) {
   });
 }
 
+dg_status dg_dot(dg_domain* dom, int32_t m, const double* V, int64_t ld, const double* w, double* out, void* stream) {
+  if (!dom) return DG_ERR_INVALID_ARG;
+  return guarded(dom, [&] {
+    const int64_t n = dom->levels[0].ndof;
+    DG_REQUIRE(V && w && out && m >= 1 && ld >= n, "bad arguments");
+    if ((int64_t)dom->partial.count < (int64_t)dg::multidot_partial_blocks() * m)
+      dom->partial.alloc((size_t)dg::multidot_partial_blocks() * m);
+    dg::launch_multidot(n, m, V, ld, w, dom->partial.get(), out, pick(dom, stream));
+  });
+}
+
 dg_status dg_nonlinear_residual(dg_domain* dom, const double* u, const double* b, double* r, void* stream) {
   if (!dom) return DG_ERR_INVALID_ARG;
   return guarded(dom, [&] {

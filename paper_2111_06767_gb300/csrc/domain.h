@@ -10,6 +10,7 @@ namespace dg {
 
 struct SchwarzLevel {
   int nS = 0;                      // padded subdomain size N^3 + 6 N_ov N^2
+  int ld = 0;                      // storage stride: nS rounded up to 32
   int n_classes = 0;               // distinct A_S (boundary-contact patterns)
   bool built = false;              // inverses built (lazily, on first smoothing)
   SubdomainGeom geom{};

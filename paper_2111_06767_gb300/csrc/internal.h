@@ -123,7 +123,10 @@ void launch_invert_spd_batched(double* A, int n, int n_classes, cudaStream_t s);
 struct SubdomainGeom {
   int n[3];
   int E, N, ov, nS;
+  int ld;  // column stride of subdomain vectors and row stride of inverses: nS rounded up to 32
 };
+template <typename T>
+void launch_pad_convert(const double* src, int n, int ld, int n_classes, T* dst, cudaStream_t s);
 template <typename T>
 void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* xform, T* rS,
                    cudaStream_t s);

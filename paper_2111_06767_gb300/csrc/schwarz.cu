@@ -234,6 +234,28 @@ void launch_invert_spd_batched(double* A, int n, int n_classes, cudaStream_t s) 
   DG_CUDA(cudaStreamSynchronize(s));  // row/col are freed on return
 }
 
+// Copy compact [n_classes][n][n] FP64 inverses into [n_classes][ld][ld] storage of type T with
+// zero padding (ld = n rounded up to 32 so rows are 128-byte aligned for TMA and vector loads).
+template <typename T>
+__global__ void pad_convert_kernel(const double* __restrict__ src, int n, int ld, int64_t total, T* __restrict__ dst) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cls = t / ((int64_t)ld * ld);
+    const int64_t rem = t - cls * ld * ld;
+    const int r = (int)(rem / ld), c = (int)(rem - (int64_t)r * ld);
+    dst[t] = (r < n && c < n) ? (T)src[cls * n * n + (int64_t)r * n + c] : T(0);
+  }
+}
+
+template <typename T>
+void launch_pad_convert(const double* src, int n, int ld, int n_classes, T* dst, cudaStream_t s) {
+  const int64_t total = (int64_t)n_classes * ld * ld;
+  if (total == 0) return;
+  pad_convert_kernel<T><<<(int)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(src, n, ld, total, dst);
+  DG_LAUNCHED(1);
+}
+template void launch_pad_convert<double>(const double*, int, int, int, double*, cudaStream_t);
+template void launch_pad_convert<float>(const double*, int, int, int, float*, cudaStream_t);
+
 // ------------------------------------------------------------------ gather / scatter
 
 // Subdomain rows and neighbours are computed from element coordinates, so the only tables are the
@@ -265,11 +287,15 @@ __device__ __forceinline__ int pick3(int i, int a, int b, int c) { return i == 0
 template <typename T>
 __global__ void gather_kernel(SubdomainGeom g, const T* __restrict__ r, const int* __restrict__ elem_of_col,
                               const int* __restrict__ xform, T* __restrict__ rS) {
-  const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, nS = g.nS;
-  const int64_t total = (int64_t)g.E * nS;
+  const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, nS = g.nS, ld = g.ld;
+  const int64_t total = (int64_t)g.E * ld;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(t / nS);
-    const int q = (int)(t - (int64_t)col * nS);
+    const int col = (int)(t / ld);
+    const int q = (int)(t - (int64_t)col * ld);
+    if (q >= nS) {  // column padding up to the aligned stride
+      rS[t] = T(0);
+      continue;
+    }
     const int e = elem_of_col[col];
     const Orient o(xform[e]);
     int cc0, cc1, cc2, src = e;
@@ -306,7 +332,7 @@ __global__ void gather_kernel(SubdomainGeom g, const T* __restrict__ r, const in
 template <typename T>
 void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* xform, T* rS,
                    cudaStream_t s) {
-  const int64_t total = (int64_t)g.E * g.nS;
+  const int64_t total = (int64_t)g.E * g.ld;
   if (total == 0) return;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
   gather_kernel<T><<<blocks, 256, 0, s>>>(g, r, elem_of_col, xform, rS);
@@ -326,7 +352,7 @@ __device__ __forceinline__ void to_canonical(const Orient& o, int N, int ca0, in
 template <typename T, typename TU>
 __global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const int* __restrict__ col_of_elem,
                                const int* __restrict__ xform, const T* __restrict__ shares, TU* __restrict__ u) {
-  const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, nS = g.nS;
+  const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, ld = g.ld;
   const int64_t ndof = (int64_t)g.E * N3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ndof; t += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(t / N3);
@@ -341,7 +367,7 @@ __global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const
     const T* sh = shares + ((int64_t)pattern * N3 + p) * 7;
     int c0, c1, c2;
     to_canonical(Orient(xform[q]), N, ca0, ca1, ca2, c0, c1, c2);
-    T acc = sh[0] * duS[(int64_t)col_of_elem[q] * nS + (c2 * N + c1) * N + c0];
+    T acc = sh[0] * duS[(int64_t)col_of_elem[q] * ld + (c2 * N + c1) * N + c0];
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       if (nb[f] < 0) continue;
@@ -357,7 +383,7 @@ __global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const
       const int a1 = a == 0 ? c1 : c0;
       const int a2 = a == 2 ? c1 : c2;
       const int row = N3 + (2 * a + sc) * ov * N2 + (depth * N + a2) * N + a1;
-      acc += sh[1 + f] * duS[(int64_t)col_of_elem[nb[f]] * nS + row];
+      acc += sh[1 + f] * duS[(int64_t)col_of_elem[nb[f]] * ld + row];
     }
     u[t] += (TU)acc;
   }

@@ -90,7 +90,8 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   const int N3 = N * N * N;
   SchwarzLevel& sw = L.sw;
   sw.nS = N3 + 6 * ov * N * N;
-  sw.geom = SubdomainGeom{{L.n[0], L.n[1], L.n[2]}, L.E, N, ov, sw.nS};
+  sw.ld = (sw.nS + 31) / 32 * 32;
+  sw.geom = SubdomainGeom{{L.n[0], L.n[1], L.n[2]}, L.E, N, ov, sw.nS, sw.ld};
   const int E = L.E;
   std::vector<int> key(E), xform(E);
   for (int e = 0; e < E; ++e) {
@@ -176,7 +177,7 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   upload(sw.xform_of_elem, xform, s);
   std::vector<int4> tiles;
   for (int c = 0; c < nc; ++c)
-    for (int r0 = 0; r0 < sw.nS; r0 += 64)
+    for (int r0 = 0; r0 < sw.ld; r0 += 64)
       for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
         tiles.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles = (int)tiles.size();
@@ -211,8 +212,8 @@ void alloc_work(LevelWork<T>& w, const Level& L) {
   w.b.alloc(L.ndof);
   w.u.alloc(L.ndof);
   w.r.alloc(L.ndof);
-  w.rS.alloc((size_t)L.E * L.sw.nS);
-  w.duS.alloc((size_t)L.E * L.sw.nS);
+  w.rS.alloc((size_t)L.E * L.sw.ld);
+  w.duS.alloc((size_t)L.E * L.sw.ld);
 }
 
 }  // namespace
@@ -296,20 +297,25 @@ void ensure_schwarz(dg_domain* dom, int level) {
   const int N = dom->N, ov = dom->desc.overlap, nS = sw.nS, nc = sw.n_classes;
   cudaStream_t s = dom->stream;
   DG_CUDA(cudaStreamSynchronize(s));
+  const int ld = sw.ld;
   DevBuf<int> d_patch;
   upload(d_patch, sw.patch, s);
-  sw.inv64.alloc((size_t)nc * nS * nS);
-  launch_build_subdomain_matrices(N, ov, L.g64, dom->D64.get(), dom->w64.get(), d_patch.get(), nc, nS, sw.inv64.get(), s);
-  launch_invert_spd_batched(sw.inv64.get(), nS, nc, s);
-  if (dom->mixed) {
-    sw.inv32.alloc((size_t)nc * nS * nS);
-    launch_convert_d2f((int64_t)nc * nS * nS, sw.inv64.get(), sw.inv32.get(), s);
+  {
+    DevBuf<double> compact((size_t)nc * nS * nS);
+    launch_build_subdomain_matrices(N, ov, L.g64, dom->D64.get(), dom->w64.get(), d_patch.get(), nc, nS, compact.get(),
+                                    s);
+    launch_invert_spd_batched(compact.get(), nS, nc, s);
+    if (dom->mixed) {
+      sw.inv32.alloc((size_t)nc * ld * ld);
+      launch_pad_convert<float>(compact.get(), nS, ld, nc, sw.inv32.get(), s);
+    } else {
+      sw.inv64.alloc((size_t)nc * ld * ld);
+      launch_pad_convert<double>(compact.get(), nS, ld, nc, sw.inv64.get(), s);
+    }
     DG_CUDA(cudaStreamSynchronize(s));
-    sw.inv64.release();
-    alloc_work(L.w32, L);
-  } else {
-    alloc_work(L.w64, L);
   }
+  if (dom->mixed) alloc_work(L.w32, L);
+  else alloc_work(L.w64, L);
   DG_CUDA(cudaStreamSynchronize(s));
   sw.built = true;
   dom->bytes = domain_device_bytes(dom);

@@ -106,6 +106,7 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
       r = W.r.get();
     }
     const double sz = sizeof(T), vec = (double)L.E * sw.nS * sz;
+    const int ld = sw.ld;
     {
       PhaseScope ps(dom->prof, DG_PHASE_GATHER, s, L.ndof * sz + vec, 0.0);
       launch_gather<T>(sw.geom, r, sw.elem_of_col.get(), sw.xform_of_elem.get(), W.rS.get(), s);
@@ -115,14 +116,14 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     auto gemm = [&](const T* X, T* Y) {
       PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * sz + 2 * vec,
                     2.0 * sw.nS * (double)sw.nS * L.E);
-      launch_class_gemm_tiles<T>(inverses<T>(sw), X, Y, sw.nS, sw.tiles.get(), sw.n_tiles, s);
+      launch_class_gemm_tiles<T>(inverses<T>(sw), X, Y, ld, sw.tiles.get(), sw.n_tiles, s);
     };
     if (!linearized) {
       gemm(W.rS.get(), W.duS.get());
     } else {
       // GMRES on (A_S + D_S), right-preconditioned by the Poisson inverse A_S^-1 (Sec. III.E)
       const int m = dom->subdomain_iterations;
-      const size_t blk = (size_t)L.E * sw.nS;
+      const size_t blk = (size_t)L.E * ld;
       if (W.gV.count < (m + 1) * blk) {
         W.gV.alloc((m + 1) * blk);
         W.gZ.alloc(m * blk);
@@ -132,12 +133,12 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
       T* beta = W.gH.get() + (size_t)L.E * (m + 1) * m;
       launch_gather<T>(sw.geom, lin_diag<T>(dom), sw.elem_of_col.get(), sw.xform_of_elem.get(), W.gD.get(), s);
       PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, (double)blk * sz * (4.0 * m + 3.0), 6.0 * blk * m);
-      launch_sub_normalize<T>(L.E, sw.nS, W.rS.get(), W.gV.get(), beta, s);
+      launch_sub_normalize<T>(L.E, ld, W.rS.get(), W.gV.get(), beta, s);
       for (int j = 0; j < m; ++j) {
         gemm(W.gV.get() + j * blk, W.gZ.get() + j * blk);
-        launch_sub_arnoldi<T>(L.E, sw.nS, j, m, W.gD.get(), W.gV.get(), W.gZ.get(), W.gH.get(), s);
+        launch_sub_arnoldi<T>(L.E, ld, j, m, W.gD.get(), W.gV.get(), W.gZ.get(), W.gH.get(), s);
       }
-      launch_sub_lsq_combine<T>(L.E, sw.nS, m, beta, W.gH.get(), W.gZ.get(), W.duS.get(), s);
+      launch_sub_lsq_combine<T>(L.E, ld, m, beta, W.gH.get(), W.gZ.get(), W.duS.get(), s);
     }
     {
       PhaseScope ps(dom->prof, DG_PHASE_SCATTER, s, vec + 2.0 * L.ndof * sz, 0.0);

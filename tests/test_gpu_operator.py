@@ -92,3 +92,21 @@ def test_rhs_and_coordinates():
     f = rand(4, x.shape)
     b = d.rhs(torch.from_numpy(f.ravel()).cuda()).cpu().numpy()
     assert rel(b, dg.rhs(grid.graph(), f)) < 1e-14
+
+
+def test_krylov_dot_products_deterministic_and_accurate():
+    """FGMRES inner products (Sec. III.B): FP64 two-pass reduction, equal to an exact-sum reference
+    to rounding and bitwise reproducible."""
+    import math
+
+    d = dgg.Domain(n=(4, 4, 2), N=5, mg_levels=1, overlap=1)
+    n = d.n_dof
+    V = rand(61, (7, n))
+    w = rand(62, (n,))
+    Vt = torch.from_numpy(V).cuda()
+    wt = torch.from_numpy(w).cuda()
+    out1 = d.dot(Vt, wt).cpu().numpy()
+    out2 = d.dot(Vt, wt).cpu().numpy()
+    assert np.array_equal(out1, out2)
+    exact = np.array([math.fsum(V[k] * w) for k in range(7)])
+    assert np.abs(out1 - exact).max() <= 1e-13 * np.abs(V).sum(axis=1).max()

@@ -31,9 +31,14 @@ def test_schwarz_smooth_matches_oracle(n, N, ov):
 
 
 def test_subdomain_class_count():
+    """Per dimension an element is at the boundary, next to it, or inside (5 positions on 8 elements);
+    up to reflections and exchanges of the cube's axes that leaves 10 classes on 8^3 elements, 4 on
+    4^3 and 1 on 2^3; an anisotropic box keeps the unequal axis apart."""
     d = dgg.Domain(n=(8, 8, 8), N=4, mg_levels=3, overlap=2)
-    assert list(d.layout.n_classes)[:3] == [125, 64, 8]
+    assert list(d.layout.n_classes)[:3] == [10, 4, 1]
     assert d.layout.subdomain_size == 4**3 + 12 * 4**2
+    d2 = dgg.Domain((0.0,) * 3, (1.0, 1.0, 2.0), (4, 4, 4), N=3, mg_levels=1, overlap=1)
+    assert d2.layout.n_classes[0] == 3 * 2  # per axis {0,3} or {1,2}; x and y interchangeable, z apart
 
 
 @pytest.mark.parametrize("n,N,levels", [((2, 2, 2), 4, 0), ((4, 4, 2), 3, 0), ((4, 4, 4), 4, 2)])
