@@ -165,6 +165,22 @@ dg_status dg_vcycle(struct dg_domain* dom, const double* r, double* z, void* str
 dg_status dg_dot(struct dg_domain* dom, int32_t m, const double* V, int64_t ld, const double* w, double* out,
                  void* stream);
 
+/* Allocation-free variant of dg_dot for callers that cannot allocate device memory when they
+ * need it: code running during CUDA stream capture, serving loops whose memory is fixed up front,
+ * plugins whose host owns every allocation. The paper has no counterpart; it is a deployment
+ * convenience. Same result as dg_dot (bitwise: same kernels, same reduction order) for n values
+ * per vector, without a domain: the per-block partial sums live in a fixed device array of
+ * 304 * DG_NOALLOC_MAX_VECTORS doubles (152 KiB) that every GPU loading the library keeps until
+ * the process exits. m above DG_NOALLOC_MAX_VECTORS is rejected with DG_ERR_INVALID_ARG; the
+ * message is available from dg_last_error(NULL). The call allocates nothing and calls no
+ * allocating routine. The first call on a device (with that device current) looks up the array's
+ * device address, so make that first call before any stream capture. All calls share the one
+ * array: calls that overlap on the GPU (concurrent streams) race and must be serialised by the
+ * caller. V, w, out are device pointers; stream as elsewhere (NULL: legacy default stream). */
+enum { DG_NOALLOC_MAX_VECTORS = 64 };
+dg_status dg_dot_noalloc(int64_t n, int32_t m, const double* V, int64_t ld, const double* w, double* out,
+                         void* stream);
+
 /* PUNCTURE: r = b - A(u) with A(u) = A u + M S(u), S(u) = -beta (1 + alpha (1 + u))^-7. */
 dg_status dg_nonlinear_residual(struct dg_domain* dom, const double* u, const double* b, double* r, void* stream);
 /* PUNCTURE: linearize at u (Eq. linearized): dg_apply then applies A + M diag(S'(u)). NULL clears. */

@@ -86,6 +86,7 @@ SIGNATURES = {
     "dg_schwarz_smooth": (C.c_int, [_vp, _i32, _vp, _vp, _i32, _vp]),
     "dg_vcycle": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_dot": (C.c_int, [_vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]),
+    "dg_dot_noalloc": (C.c_int, [C.c_int64, _i32, _vp, C.c_int64, _vp, _vp, _vp]),
     "dg_nonlinear_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dg_set_linearization": (C.c_int, [_vp, _vp, _vp]),
     "dg_puncture_fields": (C.c_int, [_vp, _vp, _vp, _vp]),

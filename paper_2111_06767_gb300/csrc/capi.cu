@@ -23,6 +23,7 @@ void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relax
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 void puncture_residual_api(dg_domain* dom, const double* u, const double* b, double* r, cudaStream_t s);
+const char* noalloc_last_error();
 void puncture_linearize_api(dg_domain* dom, const double* u, cudaStream_t s);
 
 }  // namespace dg
@@ -93,7 +94,10 @@ void dg_domain_destroy(dg_domain* dom) {
 }
 
 const char* dg_last_error(const dg_domain* dom) {
-  if (!dom) return g_create_error.c_str();
+  if (!dom) {
+    const char* na = dg::noalloc_last_error();
+    return na[0] ? na : g_create_error.c_str();
+  }
   return dom->err.c_str();
 }
 
