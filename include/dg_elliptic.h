@@ -79,7 +79,14 @@ typedef struct dg_domain_desc {
   int32_t problem;     /* enum dg_problem */
   int32_t n_punctures; /* DG_PROBLEM_PUNCTURE only, 0..DG_MAX_PUNCTURES */
   dg_puncture punctures[DG_MAX_PUNCTURES];
+  int32_t subdomain_gemm; /* how du_S = A_S^-1 r_S is applied in a MIXED domain: enum dg_subdomain_gemm */
 } dg_domain_desc;
+
+enum dg_subdomain_gemm {
+  DG_GEMM_DEFAULT = 0,      /* MIXED: tensor cores (TF32 inputs, FP32 accumulate); FP64: FP64 SIMT */
+  DG_GEMM_SIMT = 1,         /* FP32 (or FP64) CUDA-core GEMM */
+  DG_GEMM_TENSOR_TF32 = 2   /* tcgen05 tensor cores, TF32 inputs, FP32 accumulate (MIXED only) */
+};
 
 typedef struct dg_layout {
   int64_t n_dof;                        /* nodal values per vector on the finest level */

@@ -35,8 +35,11 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+GEMM_MODES = {"default": 0, "simt": 1, "tf32": 2}
+
+
 def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, overlap=2, presmooth=3,
-              postsmooth=3, problem="poisson", punctures=()):
+              postsmooth=3, problem="poisson", punctures=(), gemm="default"):
     d = nat.dg_domain_desc()
     for i in range(3):
         d.lower[i], d.upper[i], d.n[i] = lower[i], upper[i], n[i]
@@ -50,6 +53,7 @@ def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, ov
             d.punctures[q].position[i] = p.position[i]
             d.punctures[q].momentum[i] = p.momentum[i]
         d.punctures[q].mass = p.mass
+    d.subdomain_gemm = GEMM_MODES[gemm]
     return d
 
 
@@ -75,9 +79,10 @@ class Domain:
     """A discretized box with its multigrid hierarchy and Schwarz subdomain inverses."""
 
     def __init__(self, lower=(-1.0,) * 3, upper=(1.0,) * 3, n=(2, 2, 2), N=6, penalty=1.5, precision="fp64",
-                 mg_levels=0, overlap=2, presmooth=3, postsmooth=3, problem="poisson", punctures=(), stream=None):
+                 mg_levels=0, overlap=2, presmooth=3, postsmooth=3, problem="poisson", punctures=(), stream=None,
+                 gemm="default"):
         self.desc = make_desc(lower, upper, n, N, penalty, precision, mg_levels, overlap, presmooth, postsmooth,
-                              problem, punctures)
+                              problem, punctures, gemm)
         self._h = C.c_void_p()
         st = _lib.dg_domain_create(C.byref(self.desc), _stream(stream), C.byref(self._h))
         if st != nat.DG_OK:

@@ -26,7 +26,8 @@ class dg_domain_desc(C.Structure):
     _fields_ = [("lower", C.c_double * 3), ("upper", C.c_double * 3), ("n", C.c_int32 * 3), ("N", C.c_int32),
                 ("penalty", C.c_double), ("precision", C.c_int32), ("mg_levels", C.c_int32),
                 ("overlap", C.c_int32), ("presmooth", C.c_int32), ("postsmooth", C.c_int32),
-                ("problem", C.c_int32), ("n_punctures", C.c_int32), ("punctures", dg_puncture * DG_MAX_PUNCTURES)]
+                ("problem", C.c_int32), ("n_punctures", C.c_int32), ("punctures", dg_puncture * DG_MAX_PUNCTURES),
+                ("subdomain_gemm", C.c_int32)]
 
 
 class dg_layout(C.Structure):

@@ -24,8 +24,10 @@ struct SchwarzLevel {
   DevBuf<int> xform_of_elem;       // canonical -> actual orientation: perm (2 bits x 3) | flip << 6
   DevBuf<double> inv64;            // [n_classes][nS][nS] explicit inverses (FP64 mode)
   DevBuf<float> inv32;             // FP32 copies (mixed mode)
-  DevBuf<int4> tiles;              // GEMM tile list (class, row0, col0, columns left)
+  DevBuf<int4> tiles;              // SIMT GEMM tile list (class, row0, col0, columns left): 64 x 64
   int n_tiles = 0;
+  DevBuf<int4> tiles_tc;           // tensor-core GEMM tiles: 128 rows x 64 columns
+  int n_tiles_tc = 0;
 };
 
 template <typename T>
@@ -102,6 +104,8 @@ struct dg_domain {
   size_t bytes = 0;
   int subdomain_iterations = 3;
   dg::Profiler prof;
+  bool use_tc = false;            // subdomain GEMM on tcgen05 tensor cores (MIXED)
+  dg::DevBuf<int> err_flag;       // set by device code whose bounded wait gave up
 };
 
 namespace dg {

@@ -134,6 +134,11 @@ template <typename T, typename TU>
 void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* xform,
                         const T* shares, TU* u, cudaStream_t s);
 
+// Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
+bool tc_gemm_available();
+void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
+                          const int4* d_tiles, int n_tiles, int* err, cudaStream_t s);
+
 // Subdomain GMRES for linearized problems (columns of n_S values, E columns per basis vector).
 template <typename T>
 void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream_t s);

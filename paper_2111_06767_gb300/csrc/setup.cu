@@ -182,6 +182,13 @@ void classify_schwarz(dg_domain* dom, Level& L) {
         tiles.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles = (int)tiles.size();
   upload(sw.tiles, tiles, s);
+  std::vector<int4> tiles_tc;
+  for (int c = 0; c < nc; ++c)
+    for (int r0 = 0; r0 < sw.ld; r0 += 128)
+      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
+        tiles_tc.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
+  sw.n_tiles_tc = (int)tiles_tc.size();
+  upload(sw.tiles_tc, tiles_tc, s);
 }
 
 // Schwarz weight shares of every point for the 64 patterns of existing face neighbours.
@@ -231,12 +238,22 @@ void domain_setup(dg_domain* dom) {
   DG_REQUIRE(d.precision == DG_PRECISION_FP64 || d.precision == DG_PRECISION_MIXED, "bad precision");
   DG_REQUIRE(d.problem == DG_PROBLEM_POISSON || d.problem == DG_PROBLEM_PUNCTURE, "bad problem");
   DG_REQUIRE(d.mg_levels >= 0 && d.mg_levels <= DG_MAX_LEVELS, "mg_levels must be in [0, 8]");
+  DG_REQUIRE(d.subdomain_gemm >= DG_GEMM_DEFAULT && d.subdomain_gemm <= DG_GEMM_TENSOR_TF32, "bad subdomain_gemm");
+  DG_REQUIRE(d.subdomain_gemm != DG_GEMM_TENSOR_TF32 || d.precision == DG_PRECISION_MIXED,
+             "tensor-core subdomain GEMM needs a MIXED domain");
   DG_REQUIRE(d.problem != DG_PROBLEM_PUNCTURE || (d.n_punctures >= 0 && d.n_punctures <= DG_MAX_PUNCTURES),
              "bad puncture count");
   const int64_t ndof = (int64_t)d.n[0] * d.n[1] * d.n[2] * d.N * d.N * d.N;
   DG_REQUIRE(ndof < (int64_t)1 << 31, "problem too large for 32-bit point indices");
   dom->N = d.N;
   dom->mixed = d.precision == DG_PRECISION_MIXED;
+  dom->use_tc = dom->mixed && d.subdomain_gemm != DG_GEMM_SIMT;
+  if (dom->use_tc && !tc_gemm_available()) {
+    DG_REQUIRE(d.subdomain_gemm != DG_GEMM_TENSOR_TF32, "tensor-core GEMM requested but TMA encoding is unavailable");
+    dom->use_tc = false;
+  }
+  dom->err_flag.alloc(1);
+  DG_CUDA(cudaMemsetAsync(dom->err_flag.get(), 0, sizeof(int), dom->stream));
   dom->lgl = make_lgl(d.N);
   cudaStream_t s = dom->stream;
   const LglTables& t = dom->lgl;

@@ -91,6 +91,26 @@ const float* Ihi<float>(dg_domain* dom) { return dom->Ihi32.get(); }
 template <typename T>
 void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, cudaStream_t s);
 
+namespace {
+// du_S = A_S^-1 r_S for every subdomain of every class
+template <typename T>
+void class_gemm(dg_domain* dom, const Level& L, const T* X, T* Y, cudaStream_t s);
+template <>
+void class_gemm<double>(dg_domain* dom, const Level& L, const double* X, double* Y, cudaStream_t s) {
+  const SchwarzLevel& sw = L.sw;
+  launch_class_gemm_tiles<double>(sw.inv64.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, s);
+}
+template <>
+void class_gemm<float>(dg_domain* dom, const Level& L, const float* X, float* Y, cudaStream_t s) {
+  const SchwarzLevel& sw = L.sw;
+  if (dom->use_tc)
+    launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, sw.tiles_tc.get(), sw.n_tiles_tc,
+                         dom->err_flag.get(), s);
+  else
+    launch_class_gemm_tiles<float>(sw.inv32.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, s);
+}
+}  // namespace
+
 template <typename T>
 void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations, bool u_is_zero, cudaStream_t s) {
   ensure_schwarz(dom, level);
@@ -116,7 +136,7 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     auto gemm = [&](const T* X, T* Y) {
       PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * sz + 2 * vec,
                     2.0 * sw.nS * (double)sw.nS * L.E);
-      launch_class_gemm_tiles<T>(inverses<T>(sw), X, Y, ld, sw.tiles.get(), sw.n_tiles, s);
+      class_gemm<T>(dom, L, X, Y, s);
     };
     if (!linearized) {
       gemm(W.rS.get(), W.duS.get());
@@ -427,7 +447,13 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
     R.final_residual = rn;
     R.relative_residual = ref > 0 ? rn / ref : 0.0;
   }
+  int flag = 0;
+  DG_CUDA(cudaMemcpyAsync(&flag, dom->err_flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
+  if (flag) {
+    DG_CUDA(cudaMemsetAsync(dom->err_flag.get(), 0, sizeof(int), s));
+    R.status = DG_ERR_TIMEOUT;
+  }
   R.seconds = now_s() - t0;
   if (rep) *rep = R;
   return (dg_status)R.status;

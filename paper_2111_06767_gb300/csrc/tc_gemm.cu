@@ -1,0 +1,260 @@
+// Subdomain-inverse GEMM on the 5th-generation tensor cores (tcgen05, TF32 inputs, FP32 accumulate).
+//
+// du_S = A_S^-1 r_S for all subdomains of a class (Sec. III.E, explicit-inverse solver) is the one
+// dense contraction of the method: Y[:, cols] = Inv_c (ld x ld, row-major) * X[:, cols] with every
+// subdomain column of X contiguous. Both operands are K-major, so each CTA computes a 128 x 64
+// output tile: TMA streams 128 x 32 tiles of Inv_c and 64 x 32 tiles of X (128-byte swizzle) into a
+// 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
+// instruction) accumulating in tensor memory, and the four warps read the accumulator back with
+// tcgen05.ld and store it column-contiguously. Every wait is bounded: on timeout the CTA raises an
+// error flag, drains and frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace dg {
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
+constexpr int B_BYTES = BN * BK * 4;  // 8 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 128;  // >= BN: the accumulator uses BN columns
+constexpr int SLACK = 8 * 1024;  // spare shared memory after the ring
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 256;
+constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls before a wait gives up (far above any real wait)
+
+// instruction descriptor: F32 accumulate, TF32 A and B, both K-major, N = BN, M = BM
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and the error flag set) if it never completes.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte swizzle layout written
+// by TMA: rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)(16 >> 4) << 16;           // leading-dimension byte offset (single atom along K)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride-dimension byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "setp.ne.b32 P1, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, P1;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   float* __restrict__ Y, int ld, const int4* __restrict__ tiles, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES + SLACK);  // full[STAGES], empty[STAGES], acc
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  int* s_issued = (int*)(tmem_slot + 1);    // TMA chunks issued by the producer
+  int* s_consumed = (int*)(tmem_slot + 2);  // chunks the MMA thread saw arrive
+
+  const int4 tile = tiles[blockIdx.x];
+  const int cls = tile.x, row0 = tile.y, col0 = tile.z, ncol = min(tile.w, BN);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = ld / BK;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
+
+  if (threadIdx.x == 0) {
+    *s_issued = 0;
+    *s_consumed = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads into the ring
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % STAGES;
+      if (kc >= STAGES && !mbar_wait(empty0 + 8 * s, ((kc / STAGES) & 1) ^ 1, err)) break;
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      tma_load_3d(smem_u32(sA + s * A_BYTES), &mapA, full0 + 8 * s, kc * BK, row0, cls);
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &mapB, full0 + 8 * s, kc * BK, col0);
+      *s_issued = kc + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 4 instructions of K = 8 per 32-wide K chunk
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % STAGES;
+      if (!mbar_wait(full0 + 8 * s, (kc / STAGES) & 1, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk)
+        mma_tf32(tmem, smem_desc(a0 + 32 * kk), smem_desc(b0 + 32 * kk), (kc | kk) != 0);
+      mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+      *s_consumed = kc + 1;
+    }
+    mma_commit(accb);
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0, err));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = row0 + warp * 32 + lane;
+#pragma unroll
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    if (!ok) break;
+    uint32_t v[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+    if (row < ld) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < ncol) Y[(size_t)(col0 + c0 + j) * ld + row] = __uint_as_float(v[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && !ok) {
+    // a wait gave up: let the copies already issued land (bounded) before the CTA exits
+    for (int kc = *s_consumed; kc < *s_issued; ++kc) mbar_wait(full0 + 8 * (kc % STAGES), (kc / STAGES) & 1, err);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+CUtensorMap make_map(const float* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                     const cuuint32_t* box) {
+  CUtensorMap m;
+  auto fn = encode_fn();
+  if (!fn) fail(DG_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(DG_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+}  // namespace
+
+bool tc_gemm_available() { return encode_fn() != nullptr; }
+
+void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
+                          const int4* d_tiles, int n_tiles, int* err, cudaStream_t s) {
+  if (n_tiles == 0) return;
+  DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
+  const cuuint64_t dA[3] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)n_classes};
+  const cuuint64_t sAr[2] = {(cuuint64_t)ld * 4, (cuuint64_t)ld * ld * 4};
+  const cuuint32_t bA[3] = {BK, BM, 1};
+  const cuuint64_t dB[2] = {(cuuint64_t)ld, (cuuint64_t)n_cols};
+  const cuuint64_t sBr[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t bB[2] = {BK, BN};
+  const CUtensorMap mA = make_map(inv, 3, dA, sAr, bA);
+  const CUtensorMap mB = make_map(X, 2, dB, sBr, bB);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  tc_gemm_kernel<<<n_tiles, 128, SMEM_BYTES, s>>>(mA, mB, Y, ld, d_tiles, err);
+  DG_LAUNCHED(1);
+}
+
+}  // namespace dg

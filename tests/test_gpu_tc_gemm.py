@@ -1,0 +1,45 @@
+"""The subdomain-inverse GEMM on tcgen05 tensor cores (TF32 inputs, FP32 accumulate) against the
+FP32 CUDA-core GEMM, and solves that use it. TF32 keeps 10 mantissa bits of each input, so one
+smoothing step agrees with the FP32 path to ~1e-3 relative; FGMRES absorbs the difference and the
+solution still meets the 1e-10 residual."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import box, rand, rel
+
+pytestmark = pytest.mark.gpu
+
+dgg = pytest.importorskip("paper_2111_06767_gb300")
+
+
+@pytest.mark.parametrize("n,N,ov", [((2, 2, 2), 4, 2), ((4, 3, 2), 5, 2), ((8, 8, 8), 8, 2), ((3, 3, 3), 6, 1)])
+def test_tensor_core_smoothing_matches_simt(n, N, ov):
+    grid = box(n, N)
+    b = torch.from_numpy(rand(81, (grid.n_elements * N**3,))).cuda()
+    u0 = torch.from_numpy(rand(82, (grid.n_elements * N**3,))).cuda()
+    outs = {}
+    for gemm in ("simt", "tf32"):
+        d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=ov, precision="mixed", gemm=gemm)
+        outs[gemm] = d.schwarz_smooth(0, b, u0.clone(), 1).cpu().numpy()
+    du_s = outs["simt"] - u0.cpu().numpy()
+    du_t = outs["tf32"] - u0.cpu().numpy()
+    assert rel(du_t, du_s) < 3e-3
+
+
+def test_tensor_core_solve_meets_tolerance():
+    n, N = (8, 8, 8), 8
+    grid = box(n, N)
+    x, y, z = grid.coordinates()
+    f = torch.from_numpy(workloads.gaussian_source(2)(x, y, z).ravel()).cuda()
+    sols = {}
+    for prec, gemm in (("fp64", "default"), ("mixed", "tf32")):
+        d = dgg.Domain(n=n, N=N, mg_levels=3, overlap=2, precision=prec, gemm=gemm)
+        b = d.rhs(f)
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-10)
+        assert rep.relative_residual <= 1e-10
+        sols[prec] = (u.cpu().numpy(), rep.iterations)
+    assert rel(sols["mixed"][0], sols["fp64"][0]) < 1e-9
+    assert sols["mixed"][1] <= sols["fp64"][1] + 2
