@@ -211,17 +211,20 @@ def run_ours(args):
             dom.profile(False)
         return times, reps, prof
 
-    # ---- headline: mixed-precision solves
+    # ---- headline: mixed-precision solves (no instrumentation inside the timed region)
     timed_solves(d, 0, args.warmup)
     barrier()
     torch.cuda.synchronize()
     l0 = dgg.lib().dg_kernel_launches()
     torch.cuda.nvtx.range_push("timed")
     with ClockSampler(local) as clk:
-        times, reps, prof = timed_solves(d, args.steps, 0, profile=True)
+        times, reps, _ = timed_solves(d, args.steps, 0)
     torch.cuda.nvtx.range_pop()
     launches = dgg.lib().dg_kernel_launches() - l0
     barrier()
+    # the same K solves again with per-phase CUDA events (event nodes inside the V-cycle graph,
+    # read after every replay) for the kernel roofline and the phase breakdown
+    _, _, prof = timed_solves(d, args.steps, 0, profile=True)
     total_s = sum(times) / 1e3
     if world > 1:
         t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
@@ -307,6 +310,8 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / fp32_peak, "peak_source": "FP32 SIMT: 152 SM x 128 lanes x 2 x median SM clock"}
     roof.update({"kernel": dom_phase, "traffic": None, "launches": ph["launches"],
+                 "measured": "CUDA events around every launch of the phase, on the solve stream, over a second run "
+                             "of the same K solves right after the timed region",
                  "avg_launch_ms": ph["ms"] / max(ph["launches"], 1), "bytes_per_launch": ph["bytes"] / max(ph["launches"], 1)})
     phases = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                   "share": round(v["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-12), 4),

@@ -292,6 +292,12 @@ dg_status dg_profile_enable(dg_domain* dom, int32_t enable) {
     DG_CUDA(cudaStreamSynchronize(dom->stream));
     dom->prof.clear();
     dom->prof.on = enable != 0;
+    // events for graph capture come from this pool (no event creation while capturing)
+    while (dom->prof.on && dom->prof.pool.size() < 1024) {
+      cudaEvent_t e;
+      DG_CUDA(cudaEventCreate(&e));
+      dom->prof.pool.push_back(e);
+    }
   });
 }
 

@@ -21,7 +21,7 @@ struct SchwarzLevel {
   std::vector<int> patch;          // per class: 49 ints describing the representative's patch
   DevBuf<int> elem_of_col;         // subdomain column -> element
   DevBuf<int> col_of_elem;         // element -> subdomain column
-  DevBuf<int> xform_of_elem;       // canonical -> actual orientation: perm (2 bits x 3) | flip << 6
+  DevBuf<int> xform_of_elem;       // orientation index 8 perm + flips (canonical -> actual frame)
   DevBuf<double> inv64;            // [n_classes][nS][nS] explicit inverses (FP64 mode)
   DevBuf<float> inv32;             // FP32 copies (mixed mode)
   DevBuf<int4> tiles;              // SIMT GEMM tile list (class, row0, col0, columns left): 64 x 64
@@ -59,8 +59,14 @@ struct Profiler {
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
   dg_phase_stats acc[DG_PHASE_COUNT] = {};
+  // records captured into the V-cycle graph: event nodes re-recorded by every replay
+  bool capturing = false;
+  std::vector<Rec> graph_recs;
+  dg_phase_stats graph_acc[DG_PHASE_COUNT] = {};
   cudaEvent_t get();
   void clear();
+  void drop_graph_records();
+  void add_graph_replay();  // after a replay has completed: accumulate its event times
   ~Profiler();
 };
 
@@ -93,6 +99,8 @@ struct dg_domain {
   dg::DevBuf<double> X, Y, Z, mass;
   dg::DevBuf<double> shares64;  // Schwarz weight shares [64 neighbour patterns][N^3][7]
   dg::DevBuf<float> shares32;
+  dg::DevBuf<int> orient_map;   // [48][nS]: canonical subdomain row -> (actual slot, point)
+  dg::DevBuf<int> orient_inv;   // [48][7][N^3]: (actual slot, point) -> canonical row or -1
   // puncture
   dg::DevBuf<double> alpha, beta, lin64;
   dg::DevBuf<float> lin32;
@@ -106,6 +114,18 @@ struct dg_domain {
   dg::Profiler prof;
   bool use_tc = false;            // subdomain GEMM on tcgen05 tensor cores (MIXED)
   dg::DevBuf<int> err_flag;       // set by device code whose bounded wait gave up
+  // the V-cycle replayed as one CUDA graph (fixed input/output buffers; captured on the second use)
+  bool graphs = true;
+  int vcycle_calls = 0;
+  cudaGraphExec_t vgraph = nullptr;
+  bool vgraph_lin = false;
+  bool vgraph_prof = false;
+  int64_t vgraph_kernels = 0;  // kernels in the captured graph (counted again at every replay)
+  int vgraph_m = -1;
+  dg::DevBuf<double> vin64, vout64;
+  ~dg_domain() {
+    if (vgraph) cudaGraphExecDestroy(vgraph);
+  }
 };
 
 namespace dg {

@@ -126,13 +126,13 @@ struct SubdomainGeom {
   int ld;  // column stride of subdomain vectors and row stride of inverses: nS rounded up to 32
 };
 template <typename T>
-void launch_pad_convert(const double* src, int n, int ld, int n_classes, T* dst, cudaStream_t s);
-template <typename T>
-void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* xform, T* rS,
-                   cudaStream_t s);
+void launch_gather_tab(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* orient, const int* map,
+                       T* rS, cudaStream_t s);
 template <typename T, typename TU>
-void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* xform,
-                        const T* shares, TU* u, cudaStream_t s);
+void launch_scatter_tab(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* orient,
+                        const int* inv, const T* shares, TU* u, cudaStream_t s);
+template <typename T>
+void launch_pad_convert(const double* src, int n, int ld, int n_classes, T* dst, cudaStream_t s);
 
 // Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
 bool tc_gemm_available();

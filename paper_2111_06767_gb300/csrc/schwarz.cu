@@ -258,9 +258,7 @@ template void launch_pad_convert<float>(const double*, int, int, int, float*, cu
 
 // ------------------------------------------------------------------ gather / scatter
 
-// Subdomain rows and neighbours are computed from element coordinates, so the only tables are the
-// element <-> subdomain-column maps and the per-point weight shares of the 64 neighbour patterns.
-
+// Face neighbour of element e across face f (-1 at the domain boundary).
 __device__ __forceinline__ int nbr_elem(const SubdomainGeom& g, int e, int f) {
   const int c0 = e % g.n[0], c1 = (e / g.n[0]) % g.n[1], c2 = e / (g.n[0] * g.n[1]);
   int c[3] = {c0, c1, c2};
@@ -270,134 +268,105 @@ __device__ __forceinline__ int nbr_elem(const SubdomainGeom& g, int e, int f) {
   return c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
 }
 
-// Orientation of a subdomain: canonical axis a is actual axis perm(a), reflected if flip(a).
-struct Orient {
-  int p0, p1, p2, f0, f1, f2;
-  __device__ explicit Orient(int code)
-      : p0(code & 3), p1((code >> 2) & 3), p2((code >> 4) & 3), f0((code >> 6) & 1), f1((code >> 7) & 1),
-        f2((code >> 8) & 1) {}
-  __device__ int perm(int a) const { return a == 0 ? p0 : (a == 1 ? p1 : p2); }
-  __device__ int flip(int a) const { return a == 0 ? f0 : (a == 1 ? f1 : f2); }
-  __device__ int inv(int d) const { return p0 == d ? 0 : (p1 == d ? 1 : 2); }
-};
+// ------------------------------------------------------------------ table-driven gather / scatter
+//
+// The point maps depend only on (N, N_overlap) and the subdomain's orientation (48 reflections x
+// axis permutations), so they are tabulated once per domain: map[o][q] = (actual slot << 16) |
+// actual point for canonical subdomain row q, and its inverse inv[o][slot][p] = canonical row of
+// point p of the given actual slot (or -1 outside the subdomain). One CTA per subdomain column
+// (gather) or per element (scatter) resolves its neighbours once in shared memory; each point then
+// costs one table load instead of a chain of integer divisions.
 
-__device__ __forceinline__ int pick3(int i, int a, int b, int c) { return i == 0 ? a : (i == 1 ? b : c); }
-
-// r_S[col * nS + q] = r at canonical subdomain point q of the subdomain in column col (0 outside)
 template <typename T>
-__global__ void gather_kernel(SubdomainGeom g, const T* __restrict__ r, const int* __restrict__ elem_of_col,
-                              const int* __restrict__ xform, T* __restrict__ rS) {
-  const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, nS = g.nS, ld = g.ld;
-  const int64_t total = (int64_t)g.E * ld;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(t / ld);
-    const int q = (int)(t - (int64_t)col * ld);
-    if (q >= nS) {  // column padding up to the aligned stride
-      rS[t] = T(0);
-      continue;
-    }
-    const int e = elem_of_col[col];
-    const Orient o(xform[e]);
-    int cc0, cc1, cc2, src = e;
-    if (q < N3) {
-      cc0 = q % N; cc1 = (q / N) % N; cc2 = q / N2;
-    } else {
-      const int rr = q - N3;
-      const int fc = rr / (ov * N2);
-      const int k = rr - fc * ov * N2;
-      const int depth = k / N2, a2 = (k / N) % N, a1 = k % N;
-      const int a = fc >> 1, sc = fc & 1;
-      const int along = sc ? depth : N - 1 - depth;
-      cc0 = a == 0 ? along : a1;
-      cc1 = a == 1 ? along : (a == 0 ? a1 : a2);
-      cc2 = a == 2 ? along : a2;
-      const int d = o.perm(a);
-      const int sa = o.flip(a) ? 1 - sc : sc;
-      src = nbr_elem(g, e, 2 * d + sa);
-    }
+__global__ void gather_tab_kernel(SubdomainGeom g, const T* __restrict__ r, const int* __restrict__ elem_of_col,
+                                  const int* __restrict__ orient, const int* __restrict__ map, T* __restrict__ rS) {
+  __shared__ int nb[7];
+  const int col = blockIdx.x;
+  const int e = elem_of_col[col];
+  if (threadIdx.x < 7) nb[threadIdx.x] = threadIdx.x == 0 ? e : nbr_elem(g, e, threadIdx.x - 1);
+  __syncthreads();
+  const int nS = g.nS, ld = g.ld, N3 = g.N * g.N * g.N;
+  const int* m = map + (size_t)orient[e] * nS;
+  T* out = rS + (size_t)col * ld;
+  for (int q = threadIdx.x; q < ld; q += blockDim.x) {
     T v = 0;
-    if (src >= 0) {
-      // canonical -> actual node coordinates
-      const int ia0 = o.inv(0), ia1 = o.inv(1), ia2 = o.inv(2);
-      const int x0 = pick3(ia0, cc0, cc1, cc2), x1 = pick3(ia1, cc0, cc1, cc2), x2 = pick3(ia2, cc0, cc1, cc2);
-      const int ca0 = o.flip(ia0) ? N - 1 - x0 : x0;
-      const int ca1 = o.flip(ia1) ? N - 1 - x1 : x1;
-      const int ca2 = o.flip(ia2) ? N - 1 - x2 : x2;
-      v = r[(int64_t)src * N3 + (ca2 * N + ca1) * N + ca0];
+    if (q < nS) {
+      const int code = __ldg(m + q);
+      const int src = nb[code >> 16];
+      if (src >= 0) v = r[(int64_t)src * N3 + (code & 0xFFFF)];
     }
-    rS[t] = v;
+    out[q] = v;
+  }
+}
+
+template <typename T, typename TU>
+__global__ void scatter_tab_kernel(SubdomainGeom g, const T* __restrict__ duS, const int* __restrict__ col_of_elem,
+                                   const int* __restrict__ orient, const int* __restrict__ inv,
+                                   const T* __restrict__ shares, TU* __restrict__ u) {
+  __shared__ int s_col[7], s_inv[7], s_pat;
+  const int q = blockIdx.x;
+  const int N3 = g.N * g.N * g.N, ld = g.ld;
+  if (threadIdx.x < 7) {
+    const int f = threadIdx.x - 1;
+    const int e = threadIdx.x == 0 ? q : nbr_elem(g, q, f);
+    if (e >= 0) {
+      s_col[threadIdx.x] = col_of_elem[e];
+      // own subdomain: slot 0 of q's orientation; neighbour e sees q across its actual face
+      // opposite to f, i.e. in slot 1 + (f ^ 1) of e's orientation
+      const int slot = threadIdx.x == 0 ? 0 : 1 + (f ^ 1);
+      s_inv[threadIdx.x] = (orient[e] * 7 + slot) * N3;
+    } else {
+      s_col[threadIdx.x] = -1;
+      s_inv[threadIdx.x] = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int pat = 0;
+    for (int f = 0; f < 6; ++f) pat |= (s_col[1 + f] >= 0) << f;
+    s_pat = pat;
+  }
+  __syncthreads();
+  const T* sh0 = shares + (size_t)s_pat * N3 * 7;
+  for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+    const T* sh = sh0 + (size_t)p * 7;
+    T acc = sh[0] * duS[(int64_t)s_col[0] * ld + __ldg(inv + s_inv[0] + p)];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      if (s_col[1 + f] < 0) continue;
+      const int row = __ldg(inv + s_inv[1 + f] + p);
+      if (row >= 0) acc += sh[1 + f] * duS[(int64_t)s_col[1 + f] * ld + row];
+    }
+    u[(int64_t)q * N3 + p] += (TU)acc;
   }
 }
 
 template <typename T>
-void launch_gather(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* xform, T* rS,
-                   cudaStream_t s) {
-  const int64_t total = (int64_t)g.E * g.ld;
-  if (total == 0) return;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  gather_kernel<T><<<blocks, 256, 0, s>>>(g, r, elem_of_col, xform, rS);
+void launch_gather_tab(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* orient, const int* map,
+                       T* rS, cudaStream_t s) {
+  if (g.E == 0) return;
+  gather_tab_kernel<T><<<g.E, 256, 0, s>>>(g, r, elem_of_col, orient, map, rS);
   DG_LAUNCHED(1);
 }
 
-// canonical coordinates of actual node (ca0, ca1, ca2) under orientation o
-__device__ __forceinline__ void to_canonical(const Orient& o, int N, int ca0, int ca1, int ca2, int& cc0, int& cc1,
-                                             int& cc2) {
-  const int y0 = pick3(o.p0, ca0, ca1, ca2), y1 = pick3(o.p1, ca0, ca1, ca2), y2 = pick3(o.p2, ca0, ca1, ca2);
-  cc0 = o.f0 ? N - 1 - y0 : y0;
-  cc1 = o.f1 ? N - 1 - y1 : y1;
-  cc2 = o.f2 ? N - 1 - y2 : y2;
-}
-
-// u += sum over the subdomains containing each point of w_S du_S (Eq. schwarz_weighting)
 template <typename T, typename TU>
-__global__ void scatter_kernel(SubdomainGeom g, const T* __restrict__ duS, const int* __restrict__ col_of_elem,
-                               const int* __restrict__ xform, const T* __restrict__ shares, TU* __restrict__ u) {
-  const int N = g.N, N2 = N * N, N3 = N2 * N, ov = g.ov, ld = g.ld;
-  const int64_t ndof = (int64_t)g.E * N3;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ndof; t += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(t / N3);
-    const int p = (int)(t - (int64_t)q * N3);
-    const int ca0 = p % N, ca1 = (p / N) % N, ca2 = p / N2;
-    int nb[6], pattern = 0;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      nb[f] = nbr_elem(g, q, f);
-      pattern |= (nb[f] >= 0) << f;
-    }
-    const T* sh = shares + ((int64_t)pattern * N3 + p) * 7;
-    int c0, c1, c2;
-    to_canonical(Orient(xform[q]), N, ca0, ca1, ca2, c0, c1, c2);
-    T acc = sh[0] * duS[(int64_t)col_of_elem[q] * ld + (c2 * N + c1) * N + c0];
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      if (nb[f] < 0) continue;
-      const int d = f >> 1, side = f & 1;
-      // the neighbour e sees this element across its actual face (d, 1 - side)
-      const Orient o(xform[nb[f]]);
-      const int a = o.inv(d);
-      const int sc = o.flip(a) ? side : 1 - side;
-      to_canonical(o, N, ca0, ca1, ca2, c0, c1, c2);
-      const int along = pick3(a, c0, c1, c2);
-      const int depth = sc ? along : N - 1 - along;
-      if (depth >= ov) continue;
-      const int a1 = a == 0 ? c1 : c0;
-      const int a2 = a == 2 ? c1 : c2;
-      const int row = N3 + (2 * a + sc) * ov * N2 + (depth * N + a2) * N + a1;
-      acc += sh[1 + f] * duS[(int64_t)col_of_elem[nb[f]] * ld + row];
-    }
-    u[t] += (TU)acc;
-  }
-}
-
-template <typename T, typename TU>
-void launch_scatter_add(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* xform,
-                        const T* shares, TU* u, cudaStream_t s) {
-  const int64_t ndof = (int64_t)g.E * g.N * g.N * g.N;
-  if (ndof == 0) return;
-  const int blocks = (int)std::min<int64_t>((ndof + 255) / 256, 152 * 16);
-  scatter_kernel<T, TU><<<blocks, 256, 0, s>>>(g, duS, col_of_elem, xform, shares, u);
+void launch_scatter_tab(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* orient,
+                        const int* inv, const T* shares, TU* u, cudaStream_t s) {
+  if (g.E == 0) return;
+  const int N3 = g.N * g.N * g.N;
+  scatter_tab_kernel<T, TU><<<g.E, N3 > 512 ? 512 : (N3 < 32 ? 32 : N3), 0, s>>>(g, duS, col_of_elem, orient, inv,
+                                                                                 shares, u);
   DG_LAUNCHED(1);
 }
+
+template void launch_gather_tab<double>(const SubdomainGeom&, const double*, const int*, const int*, const int*,
+                                        double*, cudaStream_t);
+template void launch_gather_tab<float>(const SubdomainGeom&, const float*, const int*, const int*, const int*, float*,
+                                       cudaStream_t);
+template void launch_scatter_tab<double, double>(const SubdomainGeom&, const double*, const int*, const int*,
+                                                 const int*, const double*, double*, cudaStream_t);
+template void launch_scatter_tab<float, float>(const SubdomainGeom&, const float*, const int*, const int*, const int*,
+                                               const float*, float*, cudaStream_t);
 
 // ------------------------------------------------------------------ class GEMM (SIMT)
 
@@ -578,8 +547,11 @@ void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream
 template <typename T>
 void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* Z, T* H, cudaStream_t s) {
   const size_t smem = nS * sizeof(T);
-  if (smem > 48 * 1024)
+  static size_t attr_set = 48 * 1024;  // largest dynamic shared memory already enabled
+  if (smem > attr_set) {
     DG_CUDA(cudaFuncSetAttribute(sub_arnoldi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = smem;
+  }
   sub_arnoldi_kernel<T><<<E, 256, smem, s>>>(nS, (int64_t)E * nS, j, m, D, V, Z, H);
   DG_LAUNCHED(1);
 }
@@ -598,13 +570,7 @@ template void launch_sub_lsq_combine<double>(int, int, int, const double*, const
 template void launch_sub_lsq_combine<float>(int, int, int, const float*, const float*, const float*, float*,
                                             cudaStream_t);
 
-template void launch_gather<double>(const SubdomainGeom&, const double*, const int*, const int*, double*,
-                                   cudaStream_t);
-template void launch_gather<float>(const SubdomainGeom&, const float*, const int*, const int*, float*, cudaStream_t);
-template void launch_scatter_add<double, double>(const SubdomainGeom&, const double*, const int*, const int*,
-                                                 const double*, double*, cudaStream_t);
-template void launch_scatter_add<float, float>(const SubdomainGeom&, const float*, const int*, const int*,
-                                               const float*, float*, cudaStream_t);
+
 template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int,
                                               cudaStream_t);
 template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, cudaStream_t);

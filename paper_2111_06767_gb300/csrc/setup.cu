@@ -23,6 +23,8 @@ namespace dg {
 
 namespace {
 
+const int kPerms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
 double smoothstep(double x) {
   if (x >= 1.0) return 1.0;
   if (x <= -1.0) return -1.0;
@@ -112,14 +114,15 @@ void classify_schwarz(dg_domain* dom, Level& L) {
         const int a = perm[j], b = perm[j + 1];
         if (L.h[a] == L.h[b] && pair_key(a) > pair_key(b)) std::swap(perm[j], perm[j + 1]);
       }
-    int k = 0, code = 0;
+    int k = 0, fl = 0;
     for (int a = 0; a < 3; ++a) {
       k = k * 9 + pair_key(perm[a]);
-      code |= perm[a] << (2 * a);
-      code |= flip[perm[a]] << (6 + a);
+      fl |= flip[perm[a]] << a;
     }
+    int pi = 0;
+    while (!(kPerms[pi][0] == perm[0] && kPerms[pi][1] == perm[1] && kPerms[pi][2] == perm[2])) ++pi;
     key[e] = k;
-    xform[e] = code;
+    xform[e] = pi * 8 + fl;
   }
   std::map<int, int> cls_id;
   for (int e = 0; e < E; ++e) cls_id.emplace(key[e], 0);
@@ -189,6 +192,52 @@ void classify_schwarz(dg_domain* dom, Level& L) {
         tiles_tc.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles_tc = (int)tiles_tc.size();
   upload(sw.tiles_tc, tiles_tc, s);
+}
+
+// Point maps of the 48 subdomain orientations (orientation o = 8 perm + flips: canonical axis a is
+// actual axis kPerms[perm][a], reflected if bit a of flips): map[o][q] = (actual slot << 16) |
+// actual point of canonical subdomain row q; inv[o][slot][p] = canonical row of point p of that
+// actual slot, -1 outside the subdomain.
+void build_orientation_tables(dg_domain* dom) {
+  const int N = dom->N, N2 = N * N, N3 = N2 * N, ov = dom->desc.overlap;
+  const int nS = N3 + 6 * ov * N2;
+  std::vector<int> map((size_t)48 * nS), inv((size_t)48 * 7 * N3, -1);
+  for (int pi = 0; pi < 6; ++pi)
+    for (int fl = 0; fl < 8; ++fl) {
+      const int o = pi * 8 + fl;
+      const int* perm = kPerms[pi];
+      int invp[3];
+      for (int a = 0; a < 3; ++a) invp[perm[a]] = a;
+      for (int q = 0; q < nS; ++q) {
+        int cc[3], slot = 0;
+        if (q < N3) {
+          cc[0] = q % N;
+          cc[1] = (q / N) % N;
+          cc[2] = q / N2;
+        } else {
+          const int rr = q - N3, fc = rr / (ov * N2), k = rr - fc * ov * N2;
+          const int depth = k / N2, a2 = (k / N) % N, a1 = k % N;
+          const int a = fc >> 1, sc = fc & 1;
+          const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+          cc[a] = sc ? depth : N - 1 - depth;
+          cc[t1] = a1;
+          cc[t2] = a2;
+          const int d = perm[a];
+          const int sa = ((fl >> a) & 1) ? 1 - sc : sc;
+          slot = 1 + 2 * d + sa;
+        }
+        int ca[3];
+        for (int d = 0; d < 3; ++d) {
+          const int a = invp[d];
+          ca[d] = ((fl >> a) & 1) ? N - 1 - cc[a] : cc[a];
+        }
+        const int p = (ca[2] * N + ca[1]) * N + ca[0];
+        map[(size_t)o * nS + q] = (slot << 16) | p;
+        inv[((size_t)o * 7 + slot) * N3 + p] = q;
+      }
+    }
+  upload(dom->orient_map, map, dom->stream);
+  upload(dom->orient_inv, inv, dom->stream);
 }
 
 // Schwarz weight shares of every point for the 64 patterns of existing face neighbours.
@@ -294,6 +343,7 @@ void domain_setup(dg_domain* dom) {
   launch_mass_diag<double>(N, L0.g64, dom->w64.get(), L0.ndof, dom->mass.get(), s);
   for (auto& L : dom->levels) classify_schwarz(dom, L);
   build_shares(dom);
+  build_orientation_tables(dom);
   if (d.problem == DG_PROBLEM_PUNCTURE) {
     dom->alpha.alloc(L0.ndof);
     dom->beta.alloc(L0.ndof);
@@ -345,7 +395,8 @@ size_t domain_device_bytes(const dg_domain* dom) {
              dom->lin64.bytes() + dom->lin32.bytes() + dom->V.bytes() + dom->Zb.bytes() + dom->w.bytes() +
              dom->r.bytes() + dom->du.bytes() + dom->ut.bytes() + dom->rt.bytes() + dom->tmp.bytes() +
              dom->partial.bytes() + dom->dots.bytes() + dom->vin32.bytes() + dom->shares64.bytes() +
-             dom->shares32.bytes();
+             dom->shares32.bytes() + dom->orient_map.bytes() + dom->orient_inv.bytes() + dom->vin64.bytes() +
+             dom->vout64.bytes() + dom->err_flag.bytes();
   for (const auto& L : dom->levels) {
     const auto& sw = L.sw;
     b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.xform_of_elem.bytes() + sw.inv64.bytes() +

@@ -129,7 +129,8 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     const int ld = sw.ld;
     {
       PhaseScope ps(dom->prof, DG_PHASE_GATHER, s, L.ndof * sz + vec, 0.0);
-      launch_gather<T>(sw.geom, r, sw.elem_of_col.get(), sw.xform_of_elem.get(), W.rS.get(), s);
+      launch_gather_tab<T>(sw.geom, r, sw.elem_of_col.get(), sw.xform_of_elem.get(), dom->orient_map.get(), W.rS.get(),
+                           s);
     }
     const bool linearized = level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE &&
                             dom->subdomain_iterations > 0 && lin_diag<T>(dom) != nullptr;
@@ -151,7 +152,8 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
         W.gH.alloc((size_t)L.E * ((m + 1) * m + 1));
       }
       T* beta = W.gH.get() + (size_t)L.E * (m + 1) * m;
-      launch_gather<T>(sw.geom, lin_diag<T>(dom), sw.elem_of_col.get(), sw.xform_of_elem.get(), W.gD.get(), s);
+      launch_gather_tab<T>(sw.geom, lin_diag<T>(dom), sw.elem_of_col.get(), sw.xform_of_elem.get(),
+                           dom->orient_map.get(), W.gD.get(), s);
       PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, (double)blk * sz * (4.0 * m + 3.0), 6.0 * blk * m);
       launch_sub_normalize<T>(L.E, ld, W.rS.get(), W.gV.get(), beta, s);
       for (int j = 0; j < m; ++j) {
@@ -162,8 +164,8 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     }
     {
       PhaseScope ps(dom->prof, DG_PHASE_SCATTER, s, vec + 2.0 * L.ndof * sz, 0.0);
-      launch_scatter_add<T, T>(sw.geom, W.duS.get(), sw.col_of_elem.get(), sw.xform_of_elem.get(), shares<T>(dom), u,
-                               s);
+      launch_scatter_tab<T, T>(sw.geom, W.duS.get(), sw.col_of_elem.get(), sw.xform_of_elem.get(),
+                               dom->orient_inv.get(), shares<T>(dom), u, s);
     }
   }
 }
@@ -207,6 +209,71 @@ void vcycle(dg_domain* dom, const T* r, T* z, cudaStream_t s) {
 template void vcycle<double>(dg_domain*, const double*, double*, cudaStream_t);
 template void vcycle<float>(dg_domain*, const float*, float*, cudaStream_t);
 
+namespace {
+
+// Run the V-cycle on the domain's fixed buffers (FP32 vin32 -> vin32 + n in MIXED, vin64 -> vout64
+// in FP64), replaying a captured CUDA graph when possible: the ~100 launches of a V-cycle become
+// one graph launch. The graph is captured on the second call (the first one allocates lazily and
+// sets kernel attributes) and re-captured when the linearization state changes.
+void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
+  const int64_t n = dom->levels[0].ndof;
+  auto run = [&] {
+    if (dom->mixed) vcycle<float>(dom, dom->vin32.get(), dom->vin32.get() + n, s);
+    else vcycle<double>(dom, dom->vin64.get(), dom->vout64.get(), s);
+  };
+  const bool lin = dom->lin_set;
+  const int m = dom->subdomain_iterations;
+  const bool prof = dom->prof.on;
+  if (dom->vgraph && (dom->vgraph_lin != lin || dom->vgraph_m != m || dom->vgraph_prof != prof)) {
+    // different kernels: drop the graph and run once uncaptured (it may allocate) before re-capturing
+    cudaGraphExecDestroy(dom->vgraph);
+    dom->vgraph = nullptr;
+    dom->prof.drop_graph_records();
+    dom->vcycle_calls = 0;
+  }
+  const bool use_graph = dom->graphs && dom->vcycle_calls > 0;
+  dom->vcycle_calls++;
+  if (!use_graph) {
+    run();
+    return;
+  }
+  if (!dom->vgraph) {
+    cudaGraph_t g = nullptr;
+    // with profiling on, the phase events become event-record nodes of the graph
+    dom->prof.capturing = prof;
+    const int64_t k0 = launches_total();
+    DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      run();
+    } catch (...) {
+      dom->prof.capturing = false;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      throw;
+    }
+    dom->prof.capturing = false;
+    dom->vgraph_kernels = launches_total() - k0;
+    count_launches(-dom->vgraph_kernels);  // captured, not launched: counted at each replay
+    DG_CUDA(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&dom->vgraph, g, 0);
+    cudaGraphDestroy(g);
+    DG_CUDA(e);
+    dom->vgraph_lin = lin;
+    dom->vgraph_m = m;
+    dom->vgraph_prof = prof;
+  }
+  DG_CUDA(cudaGraphLaunch(dom->vgraph, s));
+  count_launches(dom->vgraph_kernels);
+  if (prof) {
+    // read this replay's event nodes before the next replay records them again
+    DG_CUDA(cudaStreamSynchronize(s));
+    dom->prof.add_graph_replay();
+  }
+}
+
+}  // namespace
+
 // z = M^-1 v in FP64 vectors; mode 0 identity, 1 Schwarz only, 2 V-cycle.
 void precondition(dg_domain* dom, int mode, const double* v, double* z, cudaStream_t s) {
   const int64_t n = dom->levels[0].ndof;
@@ -220,7 +287,13 @@ void precondition(dg_domain* dom, int mode, const double* v, double* z, cudaStre
       DG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
       schwarz_smooth<double>(dom, 0, v, z, steps, true, s);
     } else {
-      vcycle<double>(dom, v, z, s);
+      if (!dom->vin64.get()) {
+        dom->vin64.alloc(n);
+        dom->vout64.alloc(n);
+      }
+      DG_CUDA(cudaMemcpyAsync(dom->vin64.get(), v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      vcycle_fixed(dom, s);
+      DG_CUDA(cudaMemcpyAsync(z, dom->vout64.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
     return;
   }
@@ -233,7 +306,7 @@ void precondition(dg_domain* dom, int mode, const double* v, double* z, cudaStre
     DG_CUDA(cudaMemsetAsync(z32, 0, sizeof(float) * n, s));
     schwarz_smooth<float>(dom, 0, v32, z32, steps, true, s);
   } else {
-    vcycle<float>(dom, v32, z32, s);
+    vcycle_fixed(dom, s);
   }
   launch_convert_f2d(n, z32, z, s);
 }
@@ -483,20 +556,44 @@ void Profiler::clear() {
   for (auto& a : acc) a = dg_phase_stats{};
 }
 
-Profiler::~Profiler() {
-  for (auto& r : pending) {
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+void Profiler::drop_graph_records() {
+  for (auto& r : graph_recs) {
+    pool.push_back(r.a);
+    pool.push_back(r.b);
   }
+  graph_recs.clear();
+  for (auto& a : graph_acc) a = dg_phase_stats{};
+}
+
+void Profiler::add_graph_replay() {
+  for (auto& r : graph_recs) {
+    float ms = 0;
+    DG_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    acc[r.phase].milliseconds += ms;
+  }
+  for (int i = 0; i < DG_PHASE_COUNT; ++i) {
+    acc[i].launches += graph_acc[i].launches;
+    acc[i].bytes += graph_acc[i].bytes;
+    acc[i].flops += graph_acc[i].flops;
+  }
+}
+
+Profiler::~Profiler() {
+  for (auto* v : {&pending, &graph_recs})
+    for (auto& r : *v) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
   for (auto e : pool) cudaEventDestroy(e);
 }
 
 PhaseScope::PhaseScope(Profiler& p, int phase, cudaStream_t s, double bytes, double flops)
     : p_(p), phase_(phase), s_(s) {
   if (!p_.on) return;
-  p_.acc[phase].launches++;
-  p_.acc[phase].bytes += bytes;
-  p_.acc[phase].flops += flops;
+  dg_phase_stats& st = p_.capturing ? p_.graph_acc[phase] : p_.acc[phase];
+  st.launches++;
+  st.bytes += bytes;
+  st.flops += flops;
   a_ = p_.get();
   DG_CUDA(cudaEventRecord(a_, s_));
 }
@@ -513,7 +610,7 @@ PhaseScope::~PhaseScope() {
     return;
   }
   if (cudaEventRecord(b, s_) != cudaSuccess) (void)cudaGetLastError();
-  p_.pending.push_back({a_, b, phase_});
+  (p_.capturing ? p_.graph_recs : p_.pending).push_back({a_, b, phase_});
 }
 
 void profile_read(dg_domain* dom, dg_phase_stats* out) {
