@@ -154,13 +154,138 @@ __global__ void __launch_bounds__(NT) apply_kernel(const OpGeom<T> g, const T* _
   }
 }
 
+// Column variant: one thread per (i, j) column of N points along z, EPB elements per CTA. The
+// z-contractions run in registers (the column's u and g_z), the x- and y-contractions read shared
+// memory; each thread also owns the six face points with tangential indices (i, j), so the
+// z-faces never touch shared memory and the neighbour z-lines are read coalesced.
+template <int N, typename T>
+struct ColShape {
+  static constexpr int n2 = N * N;
+  static constexpr int bytes_per_elem = (3 * N * N * N + 6 * N * N) * (int)sizeof(T);
+  static constexpr int by_threads = n2 >= 256 ? 1 : 256 / n2;
+  static constexpr int by_smem = (44 * 1024) / bytes_per_elem;
+  static constexpr int epb = by_threads < by_smem ? by_threads : (by_smem < 1 ? 1 : by_smem);
+  static constexpr int threads = epb * n2;
+};
+
+template <int N, typename T, int EPB>
+__global__ void __launch_bounds__(EPB* N* N) apply_col_kernel(const OpGeom<T> g, const T* __restrict__ Dg,
+                                                             const T* __restrict__ wg, const T* __restrict__ u,
+                                                             const T* __restrict__ diag, const T* __restrict__ b,
+                                                             T* __restrict__ out, int E) {
+  constexpr int N2 = N * N, N3 = N * N * N, NT = EPB * N2;
+  __shared__ T sD[N2];
+  __shared__ T sw[N];
+  __shared__ T su[EPB][N3];
+  __shared__ T sv[EPB][2][N3];
+  __shared__ T sfb[EPB][6][N2];
+  const int tid = threadIdx.x;
+  const int el = tid / N2, col = tid - el * N2;
+  const int i = col % N, j = col / N;
+  const int e0 = blockIdx.x * EPB;
+  const int e = e0 + el;
+  const bool valid = e < E;
+  for (int t = tid; t < N2; t += NT) sD[t] = Dg[t];
+  for (int t = tid; t < N; t += NT) sw[t] = wg[t];
+  T uk[N], gz[N];
+  const T* ue = u + (int64_t)e * N3;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    uk[k] = valid ? ue[(k * N + j) * N + i] : T(0);
+    su[el][(k * N + j) * N + i] = uk[k];
+  }
+  __syncthreads();
+  // local gradient: x, y from shared memory, z in registers
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    T gx = 0, gy = 0, gzk = 0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      gx += sD[i * N + l] * su[el][(k * N + j) * N + l];
+      gy += sD[j * N + l] * su[el][(k * N + l) * N + i];
+      gzk += sD[k * N + l] * uk[l];
+    }
+    sv[el][0][(k * N + j) * N + i] = g.dxi[0] * gx;
+    sv[el][1][(k * N + j) * N + i] = g.dxi[1] * gy;
+    gz[k] = g.dxi[2] * gzk;
+  }
+  __syncthreads();
+  // the six face points with tangential indices (a1, a2) = (i, j)
+  if (valid) {
+    const int cx = e % g.nx, cy = (e / g.nx) % g.ny, cz = e / (g.nx * g.ny);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, side = f & 1;
+      const T s = side ? T(1) : T(-1);
+      const int idx = side ? N - 1 : 0, opp = side ? 0 : N - 1;
+      // face point and neighbour line offsets (x-faces: y = i, z = j; y-faces: x = i, z = j; z-faces: x = i, y = j)
+      int pf, base, stride;
+      if (d == 0) { pf = (j * N + i) * N + idx; base = (j * N + i) * N; stride = 1; }
+      else if (d == 1) { pf = (j * N + idx) * N + i; base = j * N2 + i; stride = N; }
+      else { pf = (idx * N + j) * N + i; base = j * N + i; stride = N2; }
+      const T dxi = d == 0 ? g.dxi[0] : (d == 1 ? g.dxi[1] : g.dxi[2]);
+      const T lift = d == 0 ? g.lift[0] : (d == 1 ? g.lift[1] : g.lift[2]);
+      const T sigma = d == 0 ? g.sigma[0] : (d == 1 ? g.sigma[1] : g.sigma[2]);
+      const T Jf = d == 0 ? g.Jf[0] : (d == 1 ? g.Jf[1] : g.Jf[2]);
+      const T u_int = d == 2 ? uk[idx] : su[el][pf];
+      const T g_int = d == 2 ? gz[idx] : sv[el][d][pf];
+      const int cd = d == 0 ? cx : (d == 1 ? cy : cz);
+      const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+      const int cn = cd + (side ? 1 : -1);
+      T u_ext, g_ext;
+      if (cn >= 0 && cn < nd) {
+        const int es = d == 0 ? 1 : (d == 1 ? g.nx : g.nx * g.ny);
+        const T* uq = u + (int64_t)(e + (side ? es : -es)) * N3 + base;
+        u_ext = __ldg(uq + opp * stride);
+        T acc = 0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) acc += sD[opp * N + l] * __ldg(uq + l * stride);
+        g_ext = dxi * acc;
+      } else {
+        u_ext = -u_int;  // Dirichlet ghost state of Eq. bc with u_b = 0
+        g_ext = g_int;
+      }
+      const T jump = u_ext - u_int;
+      const T v_face = g_int + s * jump * lift;
+      if (d == 2) gz[idx] = v_face;
+      else sv[el][d][pf] = v_face;
+      sfb[el][f][j * N + i] = Jf * sw[i] * sw[j] * (T(0.5) * s * (g_ext - g_int) + (sigma - lift) * jump);
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  // primal step: -M sum_d D_d v_d - ML [(n.v)^* - n.v]
+  T* oe = out + (int64_t)e * N3;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    T dx = 0, dy = 0, dz = 0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      dx += sD[i * N + l] * sv[el][0][(k * N + j) * N + l];
+      dy += sD[j * N + l] * sv[el][1][(k * N + l) * N + i];
+      dz += sD[k * N + l] * gz[l];
+    }
+    const T M = g.J * sw[i] * sw[j] * sw[k];
+    T res = -M * (g.dxi[0] * dx + g.dxi[1] * dy + g.dxi[2] * dz);
+    if (i == 0) res -= sfb[el][0][k * N + j];
+    if (i == N - 1) res -= sfb[el][1][k * N + j];
+    if (j == 0) res -= sfb[el][2][k * N + i];
+    if (j == N - 1) res -= sfb[el][3][k * N + i];
+    if (k == 0) res -= sfb[el][4][j * N + i];
+    if (k == N - 1) res -= sfb[el][5][j * N + i];
+    const int p = (k * N + j) * N + i;
+    if (diag) res += diag[(int64_t)e * N3 + p] * uk[k];
+    oe[p] = b ? b[(int64_t)e * N3 + p] - res : res;
+  }
+}
+
 template <int N, typename T>
 static void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
                            cudaStream_t s) {
-  using S = ApplyShape<N>;
   const int E = g.nx * g.ny * g.nz;
-  const int blocks = (E + S::epb - 1) / S::epb;
-  apply_kernel<N, T, S::epb, S::threads><<<blocks, S::threads, 0, s>>>(g, D, w, u, diag, b, out, E);
+  using C = ColShape<N, T>;
+  const int blocks = (E + C::epb - 1) / C::epb;
+  apply_col_kernel<N, T, C::epb><<<blocks, C::threads, 0, s>>>(g, D, w, u, diag, b, out, E);
 }
 
 template <typename T>

@@ -123,8 +123,13 @@ struct dg_domain {
   int64_t vgraph_kernels = 0;  // kernels in the captured graph (counted again at every replay)
   int vgraph_m = -1;
   dg::DevBuf<double> vin64, vout64;
+  cudaStream_t gstream = nullptr;  // private stream the graph is captured on and replayed in
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   ~dg_domain() {
     if (vgraph) cudaGraphExecDestroy(vgraph);
+    if (gev_in) cudaEventDestroy(gev_in);
+    if (gev_out) cudaEventDestroy(gev_out);
+    if (gstream) cudaStreamDestroy(gstream);
   }
 };
 

@@ -217,9 +217,9 @@ namespace {
 // sets kernel attributes) and re-captured when the linearization state changes.
 void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
   const int64_t n = dom->levels[0].ndof;
-  auto run = [&] {
-    if (dom->mixed) vcycle<float>(dom, dom->vin32.get(), dom->vin32.get() + n, s);
-    else vcycle<double>(dom, dom->vin64.get(), dom->vout64.get(), s);
+  auto run = [&](cudaStream_t st) {
+    if (dom->mixed) vcycle<float>(dom, dom->vin32.get(), dom->vin32.get() + n, st);
+    else vcycle<double>(dom, dom->vin64.get(), dom->vout64.get(), st);
   };
   const bool lin = dom->lin_set;
   const int m = dom->subdomain_iterations;
@@ -234,20 +234,30 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
   const bool use_graph = dom->graphs && dom->vcycle_calls > 0;
   dom->vcycle_calls++;
   if (!use_graph) {
-    run();
+    run(s);
     return;
   }
+  // capture and replay on a private stream (the caller's may be the legacy default stream, which
+  // cannot be captured), ordered after and before the caller's stream with events
+  if (!dom->gstream) {
+    DG_CUDA(cudaStreamCreateWithFlags(&dom->gstream, cudaStreamNonBlocking));
+    DG_CUDA(cudaEventCreateWithFlags(&dom->gev_in, cudaEventDisableTiming));
+    DG_CUDA(cudaEventCreateWithFlags(&dom->gev_out, cudaEventDisableTiming));
+  }
+  cudaStream_t gs = dom->gstream;
+  DG_CUDA(cudaEventRecord(dom->gev_in, s));
+  DG_CUDA(cudaStreamWaitEvent(gs, dom->gev_in, 0));
   if (!dom->vgraph) {
     cudaGraph_t g = nullptr;
     // with profiling on, the phase events become event-record nodes of the graph
     dom->prof.capturing = prof;
     const int64_t k0 = launches_total();
-    DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    DG_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
     try {
-      run();
+      run(gs);
     } catch (...) {
       dom->prof.capturing = false;
-      cudaStreamEndCapture(s, &g);
+      cudaStreamEndCapture(gs, &g);
       if (g) cudaGraphDestroy(g);
       (void)cudaGetLastError();
       throw;
@@ -255,7 +265,7 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
     dom->prof.capturing = false;
     dom->vgraph_kernels = launches_total() - k0;
     count_launches(-dom->vgraph_kernels);  // captured, not launched: counted at each replay
-    DG_CUDA(cudaStreamEndCapture(s, &g));
+    DG_CUDA(cudaStreamEndCapture(gs, &g));
     cudaError_t e = cudaGraphInstantiate(&dom->vgraph, g, 0);
     cudaGraphDestroy(g);
     DG_CUDA(e);
@@ -263,11 +273,13 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
     dom->vgraph_m = m;
     dom->vgraph_prof = prof;
   }
-  DG_CUDA(cudaGraphLaunch(dom->vgraph, s));
+  DG_CUDA(cudaGraphLaunch(dom->vgraph, gs));
   count_launches(dom->vgraph_kernels);
+  DG_CUDA(cudaEventRecord(dom->gev_out, gs));
+  DG_CUDA(cudaStreamWaitEvent(s, dom->gev_out, 0));
   if (prof) {
     // read this replay's event nodes before the next replay records them again
-    DG_CUDA(cudaStreamSynchronize(s));
+    DG_CUDA(cudaStreamSynchronize(gs));
     dom->prof.add_graph_replay();
   }
 }
@@ -595,7 +607,9 @@ PhaseScope::PhaseScope(Profiler& p, int phase, cudaStream_t s, double bytes, dou
   st.bytes += bytes;
   st.flops += flops;
   a_ = p_.get();
-  DG_CUDA(cudaEventRecord(a_, s_));
+  // inside stream capture only an "external" record becomes an event-record node of the graph
+  if (p_.capturing) DG_CUDA(cudaEventRecordWithFlags(a_, s_, cudaEventRecordExternal));
+  else DG_CUDA(cudaEventRecord(a_, s_));
 }
 
 PhaseScope::~PhaseScope() {
@@ -609,7 +623,9 @@ PhaseScope::~PhaseScope() {
     p_.pool.push_back(a_);  // drop this record rather than throw from a destructor
     return;
   }
-  if (cudaEventRecord(b, s_) != cudaSuccess) (void)cudaGetLastError();
+  const cudaError_t e =
+      p_.capturing ? cudaEventRecordWithFlags(b, s_, cudaEventRecordExternal) : cudaEventRecord(b, s_);
+  if (e != cudaSuccess) (void)cudaGetLastError();
   (p_.capturing ? p_.graph_recs : p_.pending).push_back({a_, b, phase_});
 }
 

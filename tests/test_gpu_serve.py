@@ -1,0 +1,97 @@
+"""Continuous-batching server (elliptic_serve_*): requests of different sizes, orders and problem
+kinds run concurrently; every result equals the same request solved alone (FP64 domains,
+deterministic kernels and reductions: agreement to 1e-12 relative), and the queue reports BUSY /
+NOT_FOUND / INVALID_ARG as documented."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import box, rel
+
+pytestmark = pytest.mark.gpu
+
+dgg = pytest.importorskip("paper_2111_06767_gb300")
+from paper_2111_06767_gb300 import _native  # noqa: E402
+
+
+def _request(kind, n, N, seed):
+    if kind == "poisson":
+        desc = dgg.make_desc((-1.0,) * 3, (1.0,) * 3, (n,) * 3, N, precision="fp64", overlap=2)
+        grid = box((n,) * 3, N)
+        x, y, z = grid.coordinates()
+        f = workloads.gaussian_source(seed)(x, y, z).ravel()
+    else:
+        desc = dgg.make_desc((-20.0,) * 3, (20.0,) * 3, (n,) * 3, N, precision="fp64", overlap=2, problem="puncture",
+                             punctures=workloads.BINARY_PUNCTURES)
+        f = None
+    return desc, f
+
+
+def _alone(desc, f, tol):
+    lo, hi, n = tuple(desc.lower), tuple(desc.upper), tuple(desc.n)
+    kind = "puncture" if desc.problem == 1 else "poisson"
+    d = dgg.Domain(lo, hi, n, desc.N, precision="fp64", overlap=2, problem=kind,
+                   punctures=workloads.BINARY_PUNCTURES if kind == "puncture" else ())
+    u = torch.zeros(d.n_dof, dtype=torch.float64, device="cuda")
+    if kind == "poisson":
+        b = d.rhs(torch.from_numpy(f).cuda())
+        d.solve(b, u, tol, opts=dgg.solve_opts(relative_to_b=True))
+    else:
+        d.solve(None, u, tol)
+    return u.cpu().numpy()
+
+
+def test_results_alone_equal_results_in_the_mix():
+    reqs = [("poisson", 4, 5, 11), ("puncture", 2, 4, 0), ("poisson", 2, 6, 12), ("poisson", 3, 4, 13),
+            ("puncture", 4, 5, 0), ("poisson", 6, 4, 14)]
+    srv = dgg.Server(max_active=3, n_streams=3)
+    tickets = []
+    for kind, n, N, seed in reqs:
+        desc, f = _request(kind, n, N, seed)
+        tickets.append((srv.submit(desc, f, tol=1e-10), desc, f))
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 300:
+        for t, desc, f in tickets:
+            if t in results:
+                continue
+            u = np.empty(desc.n[0] * desc.n[1] * desc.n[2] * desc.N**3)
+            st, res = srv.poll(t, u)
+            if st != _native.DG_PENDING:
+                results[t] = (st, res.report.relative_residual, u, res.submit_time, res.admit_time,
+                              res.finish_time)
+        time.sleep(0.01)
+    assert len(results) == len(tickets)
+    # requests overlapped on the device: some admission happened before an earlier finish
+    finishes = sorted(r[5] for r in results.values())
+    assert min(r[4] for r in results.values()) < finishes[-1]
+    for t, desc, f in tickets:
+        st, relres, u, *_ = results[t]
+        assert st == _native.DG_OK and relres <= 1e-10
+        assert rel(u, _alone(desc, f, 1e-10)) < 1e-12
+    assert srv.poll(tickets[0][0])[0] == -8  # a returned ticket is released
+    srv.close()
+
+
+def test_queue_errors():
+    srv = dgg.Server(max_active=1, queue_capacity=1, n_streams=1, memory_budget_bytes=512 << 20)
+    st, _ = srv.poll(12345)
+    assert st == -8  # DG_ERR_NOT_FOUND
+    big, _ = _request("poisson", 64, 8, 1)
+    with pytest.raises(dgg.NativeError) as e:
+        srv.submit(big, np.zeros(64**3 * 8**3), tol=1e-8)  # can never fit 512 MiB
+    assert e.value.status == -1
+    desc, f = _request("poisson", 6, 8, 2)
+    t1 = srv.submit(desc, f, tol=1e-10)
+    busy = 0
+    for _ in range(5):  # the single worker holds one request; the queue holds one more
+        try:
+            srv.submit(desc, f, tol=1e-10)
+        except dgg.NativeError as err:
+            assert err.status == -7  # DG_ERR_BUSY
+            busy += 1
+    assert busy >= 3
+    srv.close()
