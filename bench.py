@@ -154,6 +154,78 @@ def whole_job_rate(units_per_rank: int, world: int, max_seconds: float) -> float
     return world * units_per_rank / max_seconds
 
 
+def build_requests(dgg, workloads, items, precision="mixed"):
+    """(desc, f) for (kind, n, N, seed) items: Poisson on [-1,1]^3 with a seeded 16-Gaussian source,
+    puncture on [-20,20]^3 with the binary punctures; n is per dimension (int or 3-tuple)."""
+    out = []
+    for kind, n, N, seed in items:
+        nn = (n,) * 3 if isinstance(n, int) else tuple(n)
+        if kind == "poisson":
+            desc = dgg.make_desc((-1.0,) * 3, (1.0,) * 3, nn, N, precision=precision, overlap=2)
+            x, y, z = dgg.host_coordinates(desc)
+            f = workloads.gaussian_source(seed)(x, y, z)
+        else:
+            desc = dgg.make_desc((-20.0,) * 3, (20.0,) * 3, nn, N, precision=precision, overlap=2, problem="puncture",
+                                 punctures=workloads.BINARY_PUNCTURES)
+            f = None
+        out.append((desc, f))
+    return out
+
+
+def served_run(dgg, workloads, duration, rate=200.0, seed=5, max_active=4):
+    """Poisson-process arrivals of Poisson / puncture requests (n ~ U{2..12} cubic, N ~ U{4..8}) into the
+    continuous-batching server; latency = completion - scheduled arrival."""
+    import time as _t
+
+    arr = workloads.poisson_arrivals(seed, rate, duration)
+    reqs = build_requests(dgg, workloads, [(k, n, N, rs) for _, k, n, N, rs in arr])
+    srv = dgg.Server(max_active=max_active, n_streams=max_active, queue_capacity=1 << 20)
+    pending, done, i = {}, {}, 0
+    start = srv.clock()
+    while len(done) < len(reqs):
+        now = srv.clock() - start
+        while i < len(reqs) and arr[i][0] <= now:
+            tk = srv.submit(reqs[i][0], reqs[i][1], tol=1e-10)
+            pending[tk] = arr[i][0]
+            i += 1
+        for tk in list(pending):
+            st, res = srv.poll(tk)
+            if st != 1:
+                done[tk] = (st, res.finish_time - start - pending.pop(tk), res.report.relative_residual)
+        _t.sleep(0.0002)
+    total = srv.clock() - start
+    srv.close()
+    lat = sorted(v[1] for v in done.values())
+    pick = lambda q: 1e3 * lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "arrival_window_s": duration,
+            "solves_per_s": len(reqs) / total, "p50_latency_ms": pick(0.5), "p99_latency_ms": pick(0.99),
+            "ok": sum(1 for v in done.values() if v[0] == 0), "max_relative_residual": max(v[2] for v in done.values()),
+            "max_active": max_active, "precision": "mixed (TF32 subdomain GEMM, FP64 FGMRES)"}
+
+
+def batched_run(dgg, workloads, count=512, seed=4, max_active=8):
+    """`count` independent Poisson solves of uneven shapes (n_i ~ U{2..8}, N ~ U{4..9}), all submitted
+    at once; domains are built inside the run (explicit inverses come from the library cache after
+    the first of each shape)."""
+    shapes = workloads.batched_shapes(seed, count)
+    reqs = build_requests(dgg, workloads, [("poisson", n, N, seed + k) for k, (n, N) in enumerate(shapes)])
+    srv = dgg.Server(max_active=max_active, n_streams=max_active, queue_capacity=1 << 20)
+    start = srv.clock()
+    pending = {srv.submit(d, f, tol=1e-10): k for k, (d, f) in enumerate(reqs)}
+    res_ok, worst = 0, 0.0
+    while pending:
+        for tk in list(pending):
+            st, res = srv.poll(tk)
+            if st != 1:
+                pending.pop(tk)
+                res_ok += st == 0
+                worst = max(worst, res.report.relative_residual)
+    total = srv.clock() - start
+    srv.close()
+    return {"solves": count, "solves_per_s": count / total, "seconds": total, "ok": res_ok,
+            "max_relative_residual": worst, "max_active": max_active}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -339,6 +411,9 @@ def run_ours(args):
                   "share": round(v["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-12), 4),
                   "GB/s": round(v["bytes"] / max(v["ms"], 1e-12) / 1e6, 1)} for k, v in prof.items()}
 
+    served = served_run(dgg, workloads, args.served_seconds) if args.served_seconds > 0 and rank == 0 else None
+    batched = batched_run(dgg, workloads, args.batched) if args.batched > 0 and rank == 0 else None
+
     lat = sorted(times)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
@@ -361,6 +436,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roof,
         "phases": phases,
+        "served": served,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -376,6 +453,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--served-seconds", type=float, default=2.0, help="arrival window of the served stream (0: skip)")
+    ap.add_argument("--batched", type=int, default=0, help="also run this many batched uneven solves (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

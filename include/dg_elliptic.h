@@ -132,6 +132,10 @@ dg_status dg_domain_create(const dg_domain_desc* desc, void* cuda_stream, struct
 void dg_domain_destroy(struct dg_domain* dom);
 /* Sizes and the library-owned node coordinates, so that callers can fill f and b. */
 dg_status dg_domain_layout(const struct dg_domain* dom, dg_layout* out);
+/* Host-side node coordinates of the grid a descriptor defines (no domain, no GPU work): fills the
+ * caller's host arrays x, y, z of n_dof = n[0] n[1] n[2] N^3 doubles each in the element-major
+ * layout, so that a client can evaluate its source before submitting a served request. */
+dg_status dg_layout_coordinates_host(const dg_domain_desc* desc, double* x, double* y, double* z);
 /* Copy the node coordinates into caller-owned device buffers x, y, z (n_dof doubles each). */
 dg_status dg_copy_coordinates(const struct dg_domain* dom, double* x, double* y, double* z, void* stream);
 /* Message of the last failed call on this handle ("" if none). Thread-unsafe per handle. */

@@ -57,6 +57,17 @@ def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, ov
     return d
 
 
+def host_coordinates(desc):
+    """(x, y, z) numpy arrays of the node coordinates of the grid `desc` describes (host only)."""
+    import numpy as np
+
+    n = desc.n[0] * desc.n[1] * desc.n[2] * desc.N**3
+    out = [np.empty(n) for _ in range(3)]
+    ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in out]
+    check(_lib.dg_layout_coordinates_host(C.byref(desc), *ptrs))
+    return tuple(out)
+
+
 def solve_opts(max_iterations=200, precondition=2, linear_tol=1e-4, max_newton_steps=20, subdomain_iterations=3,
                relative_to_b=False):
     return nat.dg_solve_opts(max_iterations, precondition, linear_tol, max_newton_steps, subdomain_iterations,

@@ -92,6 +92,8 @@ SIGNATURES = {
     "dg_set_linearization": (C.c_int, [_vp, _vp, _vp]),
     "dg_puncture_fields": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_copy_coordinates": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "dg_layout_coordinates_host": (C.c_int, [C.POINTER(dg_domain_desc), C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "elliptic_solve": (C.c_int, [_vp, _vp, _vp, C.c_double, C.POINTER(dg_solve_opts), C.POINTER(dg_solve_report)]),
     "dg_kernel_launches": (C.c_int64, []),
     "dg_profile_enable": (C.c_int, [_vp, _i32]),

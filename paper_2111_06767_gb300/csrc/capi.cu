@@ -248,6 +248,31 @@ dg_status dg_puncture_fields(const dg_domain* dom, double* alpha, double* beta, 
   });
 }
 
+dg_status dg_layout_coordinates_host(const dg_domain_desc* d, double* x, double* y, double* z) {
+  if (!d || !x || !y || !z) return DG_ERR_INVALID_ARG;
+  if (d->N < 2 || d->N > DG_MAX_N || d->n[0] < 1 || d->n[1] < 1 || d->n[2] < 1) return DG_ERR_INVALID_ARG;
+  try {
+    const dg::LglTables t = dg::make_lgl(d->N);
+    const int N = d->N, N3 = N * N * N;
+    double h[3];
+    for (int i = 0; i < 3; ++i) h[i] = (d->upper[i] - d->lower[i]) / d->n[i];
+    const int64_t E = (int64_t)d->n[0] * d->n[1] * d->n[2];
+    for (int64_t e = 0; e < E; ++e) {
+      const int ex = (int)(e % d->n[0]), ey = (int)((e / d->n[0]) % d->n[1]), ez = (int)(e / ((int64_t)d->n[0] * d->n[1]));
+      for (int p = 0; p < N3; ++p) {
+        const int i = p % N, j = (p / N) % N, k = p / (N * N);
+        const int64_t q = e * N3 + p;
+        x[q] = d->lower[0] + h[0] * (ex + 0.5 * (t.x[i] + 1.0));
+        y[q] = d->lower[1] + h[1] * (ey + 0.5 * (t.x[j] + 1.0));
+        z[q] = d->lower[2] + h[2] * (ez + 0.5 * (t.x[k] + 1.0));
+      }
+    }
+  } catch (...) {
+    return DG_ERR_INVALID_ARG;
+  }
+  return DG_OK;
+}
+
 dg_status dg_copy_coordinates(const dg_domain* dom, double* x, double* y, double* z, void* stream) {
   if (!dom || !x || !y || !z) return DG_ERR_INVALID_ARG;
   dg_domain* d = const_cast<dg_domain*>(dom);

@@ -14,150 +14,18 @@
 // (n F_v)^b = n u_b, u_b = 0, and (n F_u)^b = (n F_u)^int is the ghost state u_ext = -u_int,
 // g_ext = g_int, which this kernel uses.
 //
-// GB300 mapping: EPB elements per CTA (EPB N^3 ~ 256 points), at most 512 threads striding over
-// the points; the element block, its gradient and the face brackets stay in shared memory; neighbour face
-// data (the neighbour's face value and normal derivative, which needs its whole normal line)
-// is read straight from global memory, which L2 serves for the element-ordered sweep.
+// GB300 mapping: EPB elements per CTA (EPB N^2 ~ 256 threads, one per (i, j) column); the element
+// block, its x/y gradients and the face brackets stay in shared memory; neighbour face data (the
+// neighbour's face value and normal derivative, which needs its whole normal line) is read straight
+// from global memory, which L2 serves for the element-ordered sweep.
 #include "internal.h"
 
 namespace dg {
 
-template <int N>
-struct ApplyShape {
-  static constexpr int n3 = N * N * N;
-  static constexpr int epb = n3 >= 256 ? 1 : (256 / n3);         // elements per CTA
-  static constexpr int threads = epb * n3 > 512 ? 512 : epb * n3;  // points per thread = ceil(epb n3 / threads)
-};
-
-template <typename T>
-__device__ __forceinline__ T sel3(int d, T a, T b, T c) {
-  return d == 0 ? a : (d == 1 ? b : c);
-}
-
-template <int N>
-__device__ __forceinline__ int face_node(int d, int idx_d, int a1, int a2) {
-  // node offset (k*N + j)*N + i of the point with index idx_d along d and tangential indices
-  // a1 (the lower tangential dimension) and a2 (the higher one)
-  if (d == 0) return (a2 * N + a1) * N + idx_d;
-  if (d == 1) return (a2 * N + idx_d) * N + a1;
-  return (idx_d * N + a2) * N + a1;
-}
-
-template <int N, typename T, int EPB, int NT>
-__global__ void __launch_bounds__(NT) apply_kernel(const OpGeom<T> g, const T* __restrict__ Dg,
-                                                   const T* __restrict__ wg, const T* __restrict__ u,
-                                                   const T* __restrict__ diag, const T* __restrict__ b,
-                                                   T* __restrict__ out, int E) {
-  constexpr int N2 = N * N, N3 = N * N * N;
-  __shared__ T sD[N2];
-  __shared__ T sw[N];
-  __shared__ T su[EPB][N3];
-  __shared__ T sv[EPB][3][N3];
-  __shared__ T sfb[EPB][6][N2];
-
-  const int tid = threadIdx.x;
-  const int e0 = blockIdx.x * EPB;
-  for (int t = tid; t < N2; t += NT) sD[t] = Dg[t];
-  for (int t = tid; t < N; t += NT) sw[t] = wg[t];
-  for (int t = tid; t < EPB * N3; t += NT) {
-    const int el = t / N3;
-    su[el][t - el * N3] = e0 + el < E ? u[(int64_t)e0 * N3 + t] : T(0);
-  }
-  __syncthreads();
-
-  // local gradient g_d = (2/h_d) Dhat_d u
-  for (int t = tid; t < EPB * N3; t += NT) {
-    const int el = t / N3, p = t - el * N3;
-    const int i = p % N, j = (p / N) % N, k = p / N2;
-    T gx = 0, gy = 0, gz = 0;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      gx += sD[i * N + l] * su[el][(k * N + j) * N + l];
-      gy += sD[j * N + l] * su[el][(k * N + l) * N + i];
-      gz += sD[k * N + l] * su[el][(l * N + j) * N + i];
-    }
-    sv[el][0][p] = g.dxi[0] * gx;
-    sv[el][1][p] = g.dxi[1] * gy;
-    sv[el][2][p] = g.dxi[2] * gz;
-  }
-  __syncthreads();
-
-  // face points: lift the auxiliary flux into v_d and form the primal flux bracket
-  for (int item = tid; item < EPB * 6 * N2; item += NT) {
-    const int el = item / (6 * N2);
-    const int rem = item - el * 6 * N2;
-    const int f = rem / N2;
-    const int ab = rem - f * N2;
-    const int a1 = ab % N, a2 = ab / N;
-    const int d = f >> 1, side = f & 1;
-    const int e = e0 + el;
-    if (e >= E) continue;
-    const T s = side ? T(1) : T(-1);
-    const T dxi = sel3(d, g.dxi[0], g.dxi[1], g.dxi[2]);
-    const T lift = sel3(d, g.lift[0], g.lift[1], g.lift[2]);
-    const T sigma = sel3(d, g.sigma[0], g.sigma[1], g.sigma[2]);
-    const T Jf = sel3(d, g.Jf[0], g.Jf[1], g.Jf[2]);
-    const int pf = face_node<N>(d, side ? N - 1 : 0, a1, a2);
-    const T u_int = su[el][pf];
-    const T g_int = sv[el][d][pf];
-    // neighbour across face f
-    const int cx = e % g.nx, cy = (e / g.nx) % g.ny, cz = e / (g.nx * g.ny);
-    const int cd = sel3(d, cx, cy, cz);
-    const int nd = sel3(d, g.nx, g.ny, g.nz);
-    const int cn = cd + (side ? 1 : -1);
-    T u_ext, g_ext;
-    if (cn >= 0 && cn < nd) {
-      const int stride = sel3(d, 1, g.nx, g.nx * g.ny);
-      const int q = e + (side ? stride : -stride);
-      const T* uq = u + (int64_t)q * N3;
-      const int opp = side ? 0 : N - 1;
-      u_ext = __ldg(uq + face_node<N>(d, opp, a1, a2));
-      T acc = 0;
-#pragma unroll
-      for (int l = 0; l < N; ++l) acc += sD[opp * N + l] * __ldg(uq + face_node<N>(d, l, a1, a2));
-      g_ext = dxi * acc;
-    } else {
-      u_ext = -u_int;  // Dirichlet ghost state of Eq. bc with u_b = 0
-      g_ext = g_int;
-    }
-    const T jump = u_ext - u_int;
-    sv[el][d][pf] = g_int + s * jump * lift;
-    const T Bf = Jf * sw[a1] * sw[a2];
-    sfb[el][f][ab] = Bf * (T(0.5) * s * (g_ext - g_int) + (sigma - lift) * jump);
-  }
-  __syncthreads();
-
-  // primal step: -M sum_d D_d v_d - ML [(n.v)^* - n.v]
-  for (int t = tid; t < EPB * N3; t += NT) {
-    const int el = t / N3, p = t - el * N3;
-    const int e = e0 + el;
-    if (e >= E) continue;
-    const int i = p % N, j = (p / N) % N, k = p / N2;
-    T dx = 0, dy = 0, dz = 0;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      dx += sD[i * N + l] * sv[el][0][(k * N + j) * N + l];
-      dy += sD[j * N + l] * sv[el][1][(k * N + l) * N + i];
-      dz += sD[k * N + l] * sv[el][2][(l * N + j) * N + i];
-    }
-    const T M = g.J * sw[i] * sw[j] * sw[k];
-    T res = -M * (g.dxi[0] * dx + g.dxi[1] * dy + g.dxi[2] * dz);
-    if (i == 0) res -= sfb[el][0][k * N + j];
-    if (i == N - 1) res -= sfb[el][1][k * N + j];
-    if (j == 0) res -= sfb[el][2][k * N + i];
-    if (j == N - 1) res -= sfb[el][3][k * N + i];
-    if (k == 0) res -= sfb[el][4][j * N + i];
-    if (k == N - 1) res -= sfb[el][5][j * N + i];
-    const int64_t gi = (int64_t)e * N3 + p;
-    if (diag) res += diag[gi] * su[el][p];
-    out[gi] = b ? b[gi] - res : res;
-  }
-}
-
-// Column variant: one thread per (i, j) column of N points along z, EPB elements per CTA. The
-// z-contractions run in registers (the column's u and g_z), the x- and y-contractions read shared
-// memory; each thread also owns the six face points with tangential indices (i, j), so the
-// z-faces never touch shared memory and the neighbour z-lines are read coalesced.
+// One thread per (i, j) column of N points along z, EPB elements per CTA. The z-contractions run
+// in registers (the column's u and g_z), the x- and y-contractions read shared memory; each thread
+// also owns the six face points with tangential indices (i, j), so the z-faces never touch shared
+// memory and the neighbour z-lines are read coalesced.
 template <int N, typename T>
 struct ColShape {
   static constexpr int n2 = N * N;
@@ -172,7 +40,7 @@ template <int N, typename T, int EPB>
 __global__ void __launch_bounds__(EPB* N* N) apply_col_kernel(const OpGeom<T> g, const T* __restrict__ Dg,
                                                              const T* __restrict__ wg, const T* __restrict__ u,
                                                              const T* __restrict__ diag, const T* __restrict__ b,
-                                                             T* __restrict__ out, int E) {
+                                                             T* __restrict__ out, int E, const SubdomainOut so) {
   constexpr int N2 = N * N, N3 = N * N * N, NT = EPB * N2;
   __shared__ T sD[N2];
   __shared__ T sw[N];
@@ -187,6 +55,30 @@ __global__ void __launch_bounds__(EPB* N* N) apply_col_kernel(const OpGeom<T> g,
   const bool valid = e < E;
   for (int t = tid; t < N2; t += NT) sD[t] = Dg[t];
   for (int t = tid; t < N; t += NT) sw[t] = wg[t];
+  // residual written straight into the subdomain vectors: column and point-map offset of this
+  // element's own subdomain (slot 0) and of each face neighbour's subdomain (slot 1 + (f ^ 1))
+  __shared__ int s_col[EPB][7], s_map[EPB][7];
+  for (int t = tid; so.rS && t < EPB * 7; t += NT) {
+    const int el2 = t / 7, sl = t - el2 * 7;
+    const int e2 = e0 + el2;
+    int c = -1, m = 0;
+    if (e2 < E) {
+      int q = e2;
+      if (sl > 0) {
+        const int f = sl - 1, d = f >> 1;
+        int c3[3] = {e2 % g.nx, (e2 / g.nx) % g.ny, e2 / (g.nx * g.ny)};
+        const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+        c3[d] += (f & 1) ? 1 : -1;
+        q = (c3[d] >= 0 && c3[d] < nd) ? c3[0] + g.nx * (c3[1] + g.ny * c3[2]) : -1;
+      }
+      if (q >= 0) {
+        c = so.col_of_elem[q];
+        m = (so.orient[q] * 7 + (sl == 0 ? 0 : 1 + ((sl - 1) ^ 1))) * N * N * N;
+      }
+    }
+    s_col[el2][sl] = c;
+    s_map[el2][sl] = m;
+  }
   T uk[N], gz[N];
   const T* ue = u + (int64_t)e * N3;
 #pragma unroll
@@ -210,46 +102,62 @@ __global__ void __launch_bounds__(EPB* N* N) apply_col_kernel(const OpGeom<T> g,
     gz[k] = g.dxi[2] * gzk;
   }
   __syncthreads();
-  // the six face points with tangential indices (a1, a2) = (i, j)
+  // the six face points with tangential indices (a1, a2) = (i, j). Branch-free: a face without a
+  // neighbour reads the thread's own element (in bounds) and discards it, so the loads of all six
+  // neighbour lines are independent and can be in flight together.
   if (valid) {
     const int cx = e % g.nx, cy = (e / g.nx) % g.ny, cz = e / (g.nx * g.ny);
+    T u_ext[6], g_ext[6];
+    unsigned external = 0;  // bit f: face f is on the domain boundary
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, side = f & 1;
+      const int opp = side ? 0 : N - 1;
+      int base, stride;
+      if (d == 0) { base = (j * N + i) * N; stride = 1; }
+      else if (d == 1) { base = j * N2 + i; stride = N; }
+      else { base = j * N + i; stride = N2; }
+      const int cd = d == 0 ? cx : (d == 1 ? cy : cz);
+      const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+      const int cn = cd + (side ? 1 : -1);
+      const bool has = cn >= 0 && cn < nd;
+      const int es = d == 0 ? 1 : (d == 1 ? g.nx : g.nx * g.ny);
+      const T* uq = u + (int64_t)(has ? e + (side ? es : -es) : e) * N3 + base;
+      T acc = 0, ue = 0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const T v = __ldg(uq + l * stride);
+        acc += sD[opp * N + l] * v;
+        if (l == opp) ue = v;
+      }
+      const T dxi = d == 0 ? g.dxi[0] : (d == 1 ? g.dxi[1] : g.dxi[2]);
+      u_ext[f] = ue;
+      g_ext[f] = dxi * acc;
+      external |= (has ? 0u : 1u) << f;
+    }
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, side = f & 1;
       const T s = side ? T(1) : T(-1);
-      const int idx = side ? N - 1 : 0, opp = side ? 0 : N - 1;
-      // face point and neighbour line offsets (x-faces: y = i, z = j; y-faces: x = i, z = j; z-faces: x = i, y = j)
-      int pf, base, stride;
-      if (d == 0) { pf = (j * N + i) * N + idx; base = (j * N + i) * N; stride = 1; }
-      else if (d == 1) { pf = (j * N + idx) * N + i; base = j * N2 + i; stride = N; }
-      else { pf = (idx * N + j) * N + i; base = j * N + i; stride = N2; }
-      const T dxi = d == 0 ? g.dxi[0] : (d == 1 ? g.dxi[1] : g.dxi[2]);
+      const int idx = side ? N - 1 : 0;
+      int pf;
+      if (d == 0) pf = (j * N + i) * N + idx;
+      else if (d == 1) pf = (j * N + idx) * N + i;
+      else pf = (idx * N + j) * N + i;
       const T lift = d == 0 ? g.lift[0] : (d == 1 ? g.lift[1] : g.lift[2]);
       const T sigma = d == 0 ? g.sigma[0] : (d == 1 ? g.sigma[1] : g.sigma[2]);
       const T Jf = d == 0 ? g.Jf[0] : (d == 1 ? g.Jf[1] : g.Jf[2]);
       const T u_int = d == 2 ? uk[idx] : su[el][pf];
       const T g_int = d == 2 ? gz[idx] : sv[el][d][pf];
-      const int cd = d == 0 ? cx : (d == 1 ? cy : cz);
-      const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
-      const int cn = cd + (side ? 1 : -1);
-      T u_ext, g_ext;
-      if (cn >= 0 && cn < nd) {
-        const int es = d == 0 ? 1 : (d == 1 ? g.nx : g.nx * g.ny);
-        const T* uq = u + (int64_t)(e + (side ? es : -es)) * N3 + base;
-        u_ext = __ldg(uq + opp * stride);
-        T acc = 0;
-#pragma unroll
-        for (int l = 0; l < N; ++l) acc += sD[opp * N + l] * __ldg(uq + l * stride);
-        g_ext = dxi * acc;
-      } else {
-        u_ext = -u_int;  // Dirichlet ghost state of Eq. bc with u_b = 0
-        g_ext = g_int;
-      }
-      const T jump = u_ext - u_int;
+      const bool ext = (external >> f) & 1u;
+      // Dirichlet ghost state of Eq. bc with u_b = 0 at external faces
+      const T ue = ext ? -u_int : u_ext[f];
+      const T ge = ext ? g_int : g_ext[f];
+      const T jump = ue - u_int;
       const T v_face = g_int + s * jump * lift;
       if (d == 2) gz[idx] = v_face;
       else sv[el][d][pf] = v_face;
-      sfb[el][f][j * N + i] = Jf * sw[i] * sw[j] * (T(0.5) * s * (g_ext - g_int) + (sigma - lift) * jump);
+      sfb[el][f][j * N + i] = Jf * sw[i] * sw[j] * (T(0.5) * s * (ge - g_int) + (sigma - lift) * jump);
     }
   }
   __syncthreads();
@@ -275,41 +183,68 @@ __global__ void __launch_bounds__(EPB* N* N) apply_col_kernel(const OpGeom<T> g,
     if (k == N - 1) res -= sfb[el][5][j * N + i];
     const int p = (k * N + j) * N + i;
     if (diag) res += diag[(int64_t)e * N3 + p] * uk[k];
-    oe[p] = b ? b[(int64_t)e * N3 + p] - res : res;
+    const T val = b ? b[(int64_t)e * N3 + p] - res : res;
+    if (!so.rS) {
+      oe[p] = val;
+    } else {
+      // every subdomain row holds exactly one point, so these stores never collide
+      const int cc[3] = {i, j, k};
+#pragma unroll
+      for (int sl = 0; sl < 7; ++sl) {
+        const int c = s_col[el][sl];
+        if (c < 0) continue;
+        if (sl > 0) {
+          // only points within N_overlap layers of a face belong to that neighbour's subdomain
+          const int f = sl - 1, dd = f >> 1;
+          const int depth = (f & 1) ? N - 1 - cc[dd] : cc[dd];
+          if (depth >= so.ov) continue;
+        }
+        const int row = __ldg(so.inv + s_map[el][sl] + p);
+        if (row >= 0) static_cast<T*>(so.rS)[(int64_t)c * so.ld + row] = val;
+      }
+    }
   }
 }
 
 template <int N, typename T>
 static void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                           cudaStream_t s) {
+                           const SubdomainOut& so, cudaStream_t s) {
   const int E = g.nx * g.ny * g.nz;
   using C = ColShape<N, T>;
-  const int blocks = (E + C::epb - 1) / C::epb;
-  apply_col_kernel<N, T, C::epb><<<blocks, C::threads, 0, s>>>(g, D, w, u, diag, b, out, E);
+  constexpr int kSmall = N * N >= 32 ? 1 : (32 + N * N - 1) / (N * N);  // at least one warp per CTA
+  if ((E + C::epb - 1) / C::epb >= 2 * 152 || C::epb <= kSmall) {
+    const int blocks = (E + C::epb - 1) / C::epb;
+    apply_col_kernel<N, T, C::epb><<<blocks, C::threads, 0, s>>>(g, D, w, u, diag, b, out, E, so);
+  } else {
+    // small grids: fewer elements per CTA so that every SM gets work
+    const int blocks = (E + kSmall - 1) / kSmall;
+    apply_col_kernel<N, T, kSmall><<<blocks, kSmall * N * N, 0, s>>>(g, D, w, u, diag, b, out, E, so);
+  }
 }
 
 template <typename T>
 void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                  cudaStream_t s) {
+                  cudaStream_t s, const SubdomainOut* so_ptr) {
+  const SubdomainOut so = so_ptr ? *so_ptr : SubdomainOut{};
   switch (N) {
-    case 2: launch_apply_n<2, T>(g, D, w, u, diag, b, out, s); break;
-    case 3: launch_apply_n<3, T>(g, D, w, u, diag, b, out, s); break;
-    case 4: launch_apply_n<4, T>(g, D, w, u, diag, b, out, s); break;
-    case 5: launch_apply_n<5, T>(g, D, w, u, diag, b, out, s); break;
-    case 6: launch_apply_n<6, T>(g, D, w, u, diag, b, out, s); break;
-    case 7: launch_apply_n<7, T>(g, D, w, u, diag, b, out, s); break;
-    case 8: launch_apply_n<8, T>(g, D, w, u, diag, b, out, s); break;
-    case 9: launch_apply_n<9, T>(g, D, w, u, diag, b, out, s); break;
-    case 10: launch_apply_n<10, T>(g, D, w, u, diag, b, out, s); break;
+    case 2: launch_apply_n<2, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 3: launch_apply_n<3, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 4: launch_apply_n<4, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 5: launch_apply_n<5, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 6: launch_apply_n<6, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 7: launch_apply_n<7, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 8: launch_apply_n<8, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 9: launch_apply_n<9, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 10: launch_apply_n<10, T>(g, D, w, u, diag, b, out, so, s); break;
     default: fail(DG_ERR_INVALID_ARG, "unsupported N");
   }
   DG_LAUNCHED(1);
 }
 
 template void launch_apply<double>(int, const OpGeom<double>&, const double*, const double*, const double*,
-                                   const double*, const double*, double*, cudaStream_t);
+                                   const double*, const double*, double*, cudaStream_t, const SubdomainOut*);
 template void launch_apply<float>(int, const OpGeom<float>&, const float*, const float*, const float*, const float*,
-                                  const float*, float*, cudaStream_t);
+                                  const float*, float*, cudaStream_t, const SubdomainOut*);
 
 // Diagonal of the LGL mass matrix, M = J w_i w_j w_k (Eq. massmat with collocation quadrature).
 template <typename T>

@@ -19,6 +19,8 @@ struct SchwarzLevel {
   std::vector<int> position;       // element -> subdomain column (class-sorted)
   std::vector<int> class_of;       // element -> class
   std::vector<int> patch;          // per class: 49 ints describing the representative's patch
+  std::vector<int> class_key;      // per class: canonical boundary-code key
+  double inv_scale = 1.0;          // stored inverses are built at unit element width: A_S^-1 = inv_scale x stored
   DevBuf<int> elem_of_col;         // subdomain column -> element
   DevBuf<int> col_of_elem;         // element -> subdomain column
   DevBuf<int> xform_of_elem;       // orientation index 8 perm + flips (canonical -> actual frame)
@@ -142,9 +144,9 @@ size_t domain_device_bytes(const dg_domain* dom);
 
 // level operators
 void apply_level(dg_domain* dom, int level, const double* u, double* out, const double* b, bool with_lin,
-                 cudaStream_t s);
+                 cudaStream_t s, const SubdomainOut* so = nullptr);
 void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, const float* b, bool with_lin,
-                     cudaStream_t s);
+                     cudaStream_t s, const SubdomainOut* so = nullptr);
 template <typename T>
 void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations, bool u_is_zero, cudaStream_t s);
 template <typename T>

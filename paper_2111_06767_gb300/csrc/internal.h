@@ -108,16 +108,30 @@ OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, co
 
 // ------------------------------------------------------------------ kernels (launchers)
 
+// Optional destination of the apply: instead of `out`, write every result point into the subdomain
+// vectors that contain it (rows from the orientation point maps), i.e. the Schwarz gather fused
+// into the residual computation.
+struct SubdomainOut {
+  void* rS = nullptr;            // T*: [columns][ld]
+  int ld = 0;
+  int ov = 0;                    // N_overlap
+  const int* col_of_elem = nullptr;
+  const int* orient = nullptr;   // orientation index per element
+  const int* inv = nullptr;      // [48][7][N^3] canonical row or -1
+};
+
 // out = A u (+ diag * u)  or, with b != nullptr, out = b - (A u + diag * u).
 template <typename T>
 void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                  cudaStream_t s);
+                  cudaStream_t s, const SubdomainOut* so = nullptr);
 
 // Build explicit subdomain matrices A_S for a set of classes (FP64, column-major == row-major by symmetry).
 void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<double>& g, const double* D, const double* w,
                                      const int* d_patch_info, int n_classes, int nS, double* A_out, cudaStream_t s);
 // In-place Gauss-Jordan inversion of n_classes SPD matrices of size n (no pivoting).
-void launch_invert_spd_batched(double* A, int n, int n_classes, cudaStream_t s);
+template <typename T>
+void launch_invert_spd_batched(T* A, int n, int n_classes, cudaStream_t s);
+void launch_d2f_compact(const double* src, int64_t total, float* dst, cudaStream_t s);
 
 // Schwarz data movement. Subdomain columns are class-sorted; rows follow the subdomain point order.
 struct SubdomainGeom {
@@ -131,13 +145,13 @@ void launch_gather_tab(const SubdomainGeom& g, const T* r, const int* elem_of_co
 template <typename T, typename TU>
 void launch_scatter_tab(const SubdomainGeom& g, const T* duS, const int* col_of_elem, const int* orient,
                         const int* inv, const T* shares, TU* u, cudaStream_t s);
-template <typename T>
-void launch_pad_convert(const double* src, int n, int ld, int n_classes, T* dst, cudaStream_t s);
+template <typename S, typename T>
+void launch_pad_convert(const S* src, int n, int ld, int n_classes, T* dst, cudaStream_t s);
 
 // Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
 bool tc_gemm_available();
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, cudaStream_t s);
+                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s);
 
 // Subdomain GMRES for linearized problems (columns of n_S values, E columns per basis vector).
 template <typename T>

@@ -192,52 +192,54 @@ void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<double>& g
 
 // ------------------------------------------------------------------ Gauss-Jordan inversion
 
-// Copy pivot row k and column k of every matrix into buffers.
-__global__ void gj_copy_kernel(const double* __restrict__ A, int n, int k, double* __restrict__ row,
-                               double* __restrict__ col) {
-  const int c = blockIdx.y;
-  const double* M = A + (size_t)c * n * n;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    row[(size_t)c * n + t] = M[(size_t)k * n + t];
-    col[(size_t)c * n + t] = M[(size_t)t * n + k];
-  }
-}
-
-// A[i][j] <- in-place Gauss-Jordan step k, from the saved pivot row and column.
-__global__ void gj_update_kernel(double* __restrict__ A, int n, int k, const double* __restrict__ row,
-                                 const double* __restrict__ col) {
+// One Gauss-Jordan step on pivot k, reading `in` and writing `out` (ping-pong, so no element is
+// overwritten while another thread still needs it):
+//   out[k][j] = in[k][j] / in[k][k] (j != k),   out[k][k] = 1 / in[k][k],
+//   out[i][j] = in[i][j] - in[i][k] out[k][j] (i != k, j != k),   out[i][k] = -in[i][k] / in[k][k].
+template <typename T>
+__global__ void gj_step_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int k) {
   const int c = blockIdx.z;
-  double* M = A + (size_t)c * n * n;
+  const T* A = in + (size_t)c * n * n;
+  T* B = out + (size_t)c * n * n;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || j >= n) return;
-  const double piv = col[(size_t)c * n + k];
-  const double rk = (j == k ? 1.0 : row[(size_t)c * n + j]) / piv;  // scaled pivot row
+  const T inv_piv = T(1) / A[(size_t)k * n + k];
+  const T rk = (j == k ? T(1) : A[(size_t)k * n + j]) * inv_piv;
   if (i == k) {
-    M[(size_t)k * n + j] = rk;
+    B[(size_t)k * n + j] = rk;
   } else {
-    const double f = col[(size_t)c * n + i];
-    M[(size_t)i * n + j] = (j == k ? 0.0 : M[(size_t)i * n + j]) - f * rk;
+    const T f = A[(size_t)i * n + k];
+    B[(size_t)i * n + j] = (j == k ? T(0) : A[(size_t)i * n + j]) - f * rk;
   }
 }
 
-void launch_invert_spd_batched(double* A, int n, int n_classes, cudaStream_t s) {
+// In-place inversion of n_classes SPD matrices (n x n, FP64 or FP32) by Gauss-Jordan without
+// pivoting: A_S is a principal submatrix of the SPD operator, and its condition number is small
+// (tens to hundreds for N = 4..8), so the FP32 variant loses only ~2 digits.
+template <typename T>
+void launch_invert_spd_batched(T* A, int n, int n_classes, cudaStream_t s) {
   if (n_classes == 0) return;
-  DevBuf<double> row((size_t)n * n_classes), col((size_t)n * n_classes);
-  dim3 cb(256), cg((n + 255) / 256, n_classes);
+  DevBuf<T> tmp((size_t)n * n * n_classes);
   dim3 ub(32, 8), ug((n + 31) / 32, (n + 7) / 8, n_classes);
-  for (int k = 0; k < n; ++k) {
-    gj_copy_kernel<<<cg, cb, 0, s>>>(A, n, k, row.get(), col.get());
-    gj_update_kernel<<<ug, ub, 0, s>>>(A, n, k, row.get(), col.get());
-  }
-  DG_LAUNCHED(2 * n);
-  DG_CUDA(cudaStreamSynchronize(s));  // row/col are freed on return
+  T* bufs[2] = {A, tmp.get()};
+  for (int k = 0; k < n; ++k) gj_step_kernel<T><<<ug, ub, 0, s>>>(bufs[k & 1], bufs[(k + 1) & 1], n, k);
+  DG_LAUNCHED(n);
+  if (n & 1) DG_CUDA(cudaMemcpyAsync(A, tmp.get(), sizeof(T) * (size_t)n * n * n_classes, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaStreamSynchronize(s));  // tmp is freed on return
+}
+template void launch_invert_spd_batched<double>(double*, int, int, cudaStream_t);
+template void launch_invert_spd_batched<float>(float*, int, int, cudaStream_t);
+
+__global__ void d2f_compact_kernel(const double* __restrict__ src, int64_t total, float* __restrict__ dst) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = (float)src[t];
 }
 
 // Copy compact [n_classes][n][n] FP64 inverses into [n_classes][ld][ld] storage of type T with
 // zero padding (ld = n rounded up to 32 so rows are 128-byte aligned for TMA and vector loads).
-template <typename T>
-__global__ void pad_convert_kernel(const double* __restrict__ src, int n, int ld, int64_t total, T* __restrict__ dst) {
+template <typename S, typename T>
+__global__ void pad_convert_kernel(const S* __restrict__ src, int n, int ld, int64_t total, T* __restrict__ dst) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cls = t / ((int64_t)ld * ld);
     const int64_t rem = t - cls * ld * ld;
@@ -246,15 +248,23 @@ __global__ void pad_convert_kernel(const double* __restrict__ src, int n, int ld
   }
 }
 
-template <typename T>
-void launch_pad_convert(const double* src, int n, int ld, int n_classes, T* dst, cudaStream_t s) {
+template <typename S, typename T>
+void launch_pad_convert(const S* src, int n, int ld, int n_classes, T* dst, cudaStream_t s) {
   const int64_t total = (int64_t)n_classes * ld * ld;
   if (total == 0) return;
-  pad_convert_kernel<T><<<(int)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(src, n, ld, total, dst);
+  pad_convert_kernel<S, T><<<(int)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(src, n, ld, total,
+                                                                                                dst);
   DG_LAUNCHED(1);
 }
-template void launch_pad_convert<double>(const double*, int, int, int, double*, cudaStream_t);
-template void launch_pad_convert<float>(const double*, int, int, int, float*, cudaStream_t);
+template void launch_pad_convert<double, double>(const double*, int, int, int, double*, cudaStream_t);
+template void launch_pad_convert<double, float>(const double*, int, int, int, float*, cudaStream_t);
+template void launch_pad_convert<float, float>(const float*, int, int, int, float*, cudaStream_t);
+
+void launch_d2f_compact(const double* src, int64_t total, float* dst, cudaStream_t s) {
+  if (total == 0) return;
+  d2f_compact_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(src, total, dst);
+  DG_LAUNCHED(1);
+}
 
 // ------------------------------------------------------------------ gather / scatter
 
@@ -374,7 +384,8 @@ template void launch_scatter_tab<float, float>(const SubdomainGeom&, const float
 // 64 x 64 output tiles, K chunks of 16 staged in shared memory, 4 x 4 outputs per thread.
 template <typename T>
 __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ inv, const T* __restrict__ X,
-                                                         T* __restrict__ Y, int nS, const int4* __restrict__ tiles) {
+                                                         T* __restrict__ Y, int nS, const int4* __restrict__ tiles,
+                                                         T alpha) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T sA[BK][BM + 1];
   __shared__ T sB[BK][BN + 1];
@@ -414,15 +425,16 @@ __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ i
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int c = tx + 16 * r;
-      if (c < ncol) Y[(size_t)(col0 + c) * nS + gr] = acc[q][r];
+      if (c < ncol) Y[(size_t)(col0 + c) * nS + gr] = alpha * acc[q][r];
     }
   }
 }
 
 template <typename T>
-void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, cudaStream_t s) {
+void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
+                             cudaStream_t s) {
   if (n_tiles == 0) return;
-  class_gemm_kernel<T><<<n_tiles, 256, 0, s>>>(inv, X, Y, nS, d_tiles);
+  class_gemm_kernel<T><<<n_tiles, 256, 0, s>>>(inv, X, Y, nS, d_tiles, alpha);
   DG_LAUNCHED(1);
 }
 
@@ -571,8 +583,9 @@ template void launch_sub_lsq_combine<float>(int, int, int, const float*, const f
                                             cudaStream_t);
 
 
-template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int,
+template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int, double,
                                               cudaStream_t);
-template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, cudaStream_t);
+template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, float,
+                                             cudaStream_t);
 
 }  // namespace dg

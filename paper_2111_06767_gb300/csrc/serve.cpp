@@ -41,25 +41,36 @@ namespace dg {
 size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations) {
   const int N = d.N, ov = d.overlap;
   const size_t nS = (size_t)N * N * N + 6 * (size_t)ov * N * N;
+  const size_t ld = (nS + 31) / 32 * 32;
   const bool mixed = d.precision == DG_PRECISION_MIXED;
   const size_t fb = mixed ? 4 : 8;
-  size_t total = 0;
+  size_t total = (size_t)48 * (nS + 7 * N * N * N) * 4 + (size_t)64 * N * N * N * 7 * fb;  // point maps, shares
   int n[3] = {d.n[0], d.n[1], d.n[2]};
+  size_t build_peak = 0;
   for (int l = 0; l < DG_MAX_LEVELS; ++l) {
     const size_t E = (size_t)n[0] * n[1] * n[2];
     const size_t ndof = E * N * N * N;
-    size_t classes = 1;
-    for (int i = 0; i < 3; ++i) classes *= (size_t)std::min(n[i], 5);
+    // classes up to symmetry: 1, 2 or 3 boundary categories per dimension (n = 1-2, 3-4, >= 5);
+    // dimensions of equal element width count as a multiset
+    const double hw[3] = {(d.upper[0] - d.lower[0]) / n[0], (d.upper[1] - d.lower[1]) / n[1],
+                          (d.upper[2] - d.lower[2]) / n[2]};
+    const int cats[3] = {n[0] <= 2 ? 1 : (n[0] <= 4 ? 2 : 3), n[1] <= 2 ? 1 : (n[1] <= 4 ? 2 : 3),
+                         n[2] <= 2 ? 1 : (n[2] <= 4 ? 2 : 3)};
+    size_t classes = (size_t)cats[0] * cats[1] * cats[2];
+    if (hw[0] == hw[1] && hw[1] == hw[2] && cats[0] == cats[1] && cats[1] == cats[2])
+      classes = (size_t)cats[0] * (cats[0] + 1) * (cats[0] + 2) / 6;
     classes = std::min(classes, E);
-    total += classes * nS * nS * (8 + (mixed ? 4 : 0));      // FP64 build (+ FP32 copy)
-    total += E * nS * (4 + 2 * fb) + ndof * 7 * (4 + fb) + 5 * ndof * fb;
+    build_peak = std::max(build_peak, classes * nS * nS * 8);  // FP64 build, freed after inversion
+    total += classes * ld * ld * fb;                            // stored inverses
+    total += 2 * E * ld * fb + 3 * ndof * fb + 4 * E * 4;       // r_S, du_S, b, u, r, tables
     if ((d.mg_levels && l + 1 == d.mg_levels) || (n[0] % 2 && n[1] % 2 && n[2] % 2)) break;
     for (int i = 0; i < 3; ++i)
       if (n[i] % 2 == 0) n[i] /= 2;
   }
   const size_t ndof0 = (size_t)d.n[0] * d.n[1] * d.n[2] * N * N * N;
-  total += ndof0 * 8 * (2 * (size_t)max_iterations + 16);
-  return total + (8u << 20);
+  // Krylov basis: grown on demand; admission counts up to 64 iterations
+  total += ndof0 * 8 * (2 * (size_t)std::min(max_iterations, 64) + 16);
+  return total + build_peak + (8u << 20);
 }
 
 }  // namespace dg

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
+#include <tuple>
 
 #include "domain.h"
 
@@ -127,7 +129,11 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   std::map<int, int> cls_id;
   for (int e = 0; e < E; ++e) cls_id.emplace(key[e], 0);
   int nc = 0;
-  for (auto& kv : cls_id) kv.second = nc++;
+  sw.class_key.clear();
+  for (auto& kv : cls_id) {
+    kv.second = nc++;
+    sw.class_key.push_back(kv.first);
+  }
   sw.n_classes = nc;
   sw.class_of.resize(E);
   sw.class_count.assign(nc, 0);
@@ -264,12 +270,15 @@ void build_shares(dg_domain* dom) {
 }
 
 template <typename T>
-void alloc_work(LevelWork<T>& w, const Level& L) {
+void alloc_work(LevelWork<T>& w, const Level& L, cudaStream_t s) {
   w.b.alloc(L.ndof);
   w.u.alloc(L.ndof);
   w.r.alloc(L.ndof);
   w.rS.alloc((size_t)L.E * L.sw.ld);
   w.duS.alloc((size_t)L.E * L.sw.ld);
+  // rows of r_S that no point maps to (missing neighbours, stride padding) stay zero for good: the
+  // fused residual writes only mapped rows
+  DG_CUDA(cudaMemsetAsync(w.rS.get(), 0, w.rS.bytes(), s));
 }
 
 }  // namespace
@@ -357,6 +366,31 @@ void domain_setup(dg_domain* dom) {
 
 // Explicit inverses and work vectors of one level, built on first use (Sec. III.E: construction
 // cost amortised over all later solves).
+namespace {
+
+// Library-wide store of built inverses. Every term of the affine Poisson DG operator scales with
+// the element size in 3-D (mass h^3 x derivatives h^-2, face mass h^2 x penalty and lifting h^-1),
+// so A_S(h) = h_x A_S(h / h_x) and one inverse built at h_x = 1 serves every grid with the same
+// aspect ratios, order, overlap, penalty and boundary pattern: A_S(h)^-1 = (1/h_x) A_S(h/h_x)^-1.
+// Entries live until the process exits (bounded by kCacheCap; beyond it new inverses are built
+// but not kept).
+struct InvKey {
+  int dev, N, ov, key, fp64;
+  double penalty, a1, a2;
+  bool operator<(const InvKey& o) const {
+    return std::tie(dev, N, ov, key, fp64, penalty, a1, a2) <
+           std::tie(o.dev, o.N, o.ov, o.key, o.fp64, o.penalty, o.a1, o.a2);
+  }
+};
+constexpr size_t kCacheCap = size_t(8) << 30;
+std::mutex g_inv_mu;
+std::map<InvKey, void*>* g_inv = new std::map<InvKey, void*>();  // device buffers of ld^2 entries
+size_t g_inv_bytes = 0;
+
+}  // namespace
+
+// Explicit inverses and work vectors of one level, built on first use (Sec. III.E: construction
+// cost amortised over all later solves).
 void ensure_schwarz(dg_domain* dom, int level) {
   Level& L = dom->levels[level];
   SchwarzLevel& sw = L.sw;
@@ -365,24 +399,82 @@ void ensure_schwarz(dg_domain* dom, int level) {
   cudaStream_t s = dom->stream;
   DG_CUDA(cudaStreamSynchronize(s));
   const int ld = sw.ld;
-  DevBuf<int> d_patch;
-  upload(d_patch, sw.patch, s);
+  const size_t esz = dom->mixed ? sizeof(float) : sizeof(double);
+  const size_t mat = (size_t)ld * ld * esz;
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  const double hx = L.h[0];
+  sw.inv_scale = 1.0 / hx;
+  if (dom->mixed) sw.inv32.alloc((size_t)nc * ld * ld);
+  else sw.inv64.alloc((size_t)nc * ld * ld);
+  char* dst = dom->mixed ? (char*)sw.inv32.get() : (char*)sw.inv64.get();
+  std::vector<int> missing;
+  std::vector<InvKey> keys(nc);
   {
-    DevBuf<double> compact((size_t)nc * nS * nS);
-    launch_build_subdomain_matrices(N, ov, L.g64, dom->D64.get(), dom->w64.get(), d_patch.get(), nc, nS, compact.get(),
-                                    s);
-    launch_invert_spd_batched(compact.get(), nS, nc, s);
+    // cached entries are never freed, so their copies may run after the lock is released
+    std::lock_guard<std::mutex> lk(g_inv_mu);
+    for (int c = 0; c < nc; ++c) {
+      keys[c] = InvKey{dev, N, ov, sw.class_key[c], dom->mixed ? 0 : 1, dom->desc.penalty, L.h[1] / hx, L.h[2] / hx};
+      auto it = g_inv->find(keys[c]);
+      if (it != g_inv->end())
+        DG_CUDA(cudaMemcpyAsync(dst + c * mat, it->second, mat, cudaMemcpyDeviceToDevice, s));
+      else
+        missing.push_back(c);
+    }
+  }
+  if (!missing.empty()) {
+    // build the missing classes at unit width: A_S column by column, then Gauss-Jordan in FP64
+    const int nm = (int)missing.size();
+    std::vector<int> patch((size_t)nm * 49);
+    for (int i = 0; i < nm; ++i)
+      std::copy(sw.patch.begin() + (size_t)missing[i] * 49, sw.patch.begin() + (size_t)(missing[i] + 1) * 49,
+                patch.begin() + (size_t)i * 49);
+    DevBuf<int> d_patch;
+    upload(d_patch, patch, s);
+    const double hu[3] = {1.0, L.h[1] / hx, L.h[2] / hx};
+    const OpGeom<double> gu = make_geom<double>(L.n, hu, N, dom->desc.penalty, dom->lgl);
+    DevBuf<double> compact((size_t)nm * nS * nS);
+    launch_build_subdomain_matrices(N, ov, gu, dom->D64.get(), dom->w64.get(), d_patch.get(), nm, nS, compact.get(), s);
+    DevBuf<char> built((size_t)nm * mat);
     if (dom->mixed) {
-      sw.inv32.alloc((size_t)nc * ld * ld);
-      launch_pad_convert<float>(compact.get(), nS, ld, nc, sw.inv32.get(), s);
+      // stored in FP32 for an FP32/TF32 smoother: invert in FP32 (A_S is well conditioned)
+      DevBuf<float> c32((size_t)nm * nS * nS);
+      launch_d2f_compact(compact.get(), (int64_t)nm * nS * nS, c32.get(), s);
+      compact.release();
+      launch_invert_spd_batched<float>(c32.get(), nS, nm, s);
+      launch_pad_convert<float, float>(c32.get(), nS, ld, nm, (float*)built.get(), s);
     } else {
-      sw.inv64.alloc((size_t)nc * ld * ld);
-      launch_pad_convert<double>(compact.get(), nS, ld, nc, sw.inv64.get(), s);
+      launch_invert_spd_batched<double>(compact.get(), nS, nm, s);
+      launch_pad_convert<double, double>(compact.get(), nS, ld, nm, (double*)built.get(), s);
+    }
+    for (int i = 0; i < nm; ++i)
+      DG_CUDA(cudaMemcpyAsync(dst + missing[i] * mat, built.get() + i * mat, mat, cudaMemcpyDeviceToDevice, s));
+    // keep a copy for later domains (built outside the lock; another thread may have won the race)
+    for (int i = 0; i < nm; ++i) {
+      {
+        std::lock_guard<std::mutex> lk(g_inv_mu);
+        if (g_inv->count(keys[missing[i]]) || g_inv_bytes + mat > kCacheCap) continue;
+        g_inv_bytes += mat;
+      }
+      void* keep = nullptr;
+      if (cudaMalloc(&keep, mat) != cudaSuccess) {
+        (void)cudaGetLastError();
+        std::lock_guard<std::mutex> lk(g_inv_mu);
+        g_inv_bytes -= mat;
+        continue;
+      }
+      DG_CUDA(cudaMemcpyAsync(keep, built.get() + i * mat, mat, cudaMemcpyDeviceToDevice, s));
+      DG_CUDA(cudaStreamSynchronize(s));
+      std::lock_guard<std::mutex> lk(g_inv_mu);
+      if (!g_inv->emplace(keys[missing[i]], keep).second) {
+        cudaFree(keep);
+        g_inv_bytes -= mat;
+      }
     }
     DG_CUDA(cudaStreamSynchronize(s));
   }
-  if (dom->mixed) alloc_work(L.w32, L);
-  else alloc_work(L.w64, L);
+  if (dom->mixed) alloc_work(L.w32, L, s);
+  else alloc_work(L.w64, L, s);
   DG_CUDA(cudaStreamSynchronize(s));
   sw.built = true;
   dom->bytes = domain_device_bytes(dom);

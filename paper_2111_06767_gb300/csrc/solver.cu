@@ -17,19 +17,19 @@ double apply_flops(int64_t ndof, int N) { return (double)ndof * (12.0 * N + 12.0
 }  // namespace
 
 void apply_level(dg_domain* dom, int level, const double* u, double* out, const double* b, bool with_lin,
-                 cudaStream_t s) {
+                 cudaStream_t s, const SubdomainOut* so) {
   Level& L = dom->levels[level];
   const double* diag = (with_lin && level == 0 && dom->lin_set) ? dom->lin64.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP64, s, apply_bytes(L.ndof, 8, b, diag), apply_flops(L.ndof, dom->N));
-  launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s);
+  launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s, so);
 }
 
 void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, const float* b, bool with_lin,
-                     cudaStream_t s) {
+                     cudaStream_t s, const SubdomainOut* so) {
   Level& L = dom->levels[level];
   const float* diag = (with_lin && level == 0 && dom->lin_set && dom->lin32.get()) ? dom->lin32.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP32, s, apply_bytes(L.ndof, 4, b, diag), apply_flops(L.ndof, dom->N));
-  launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s);
+  launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s, so);
 }
 
 namespace {
@@ -63,14 +63,17 @@ template <>
 const float* lin_diag<float>(const dg_domain* dom) { return dom->lin32.get(); }
 
 template <typename T>
-void apply_T(dg_domain* dom, int level, const T* u, T* out, const T* b, cudaStream_t s);
+void apply_T(dg_domain* dom, int level, const T* u, T* out, const T* b, cudaStream_t s,
+             const SubdomainOut* so = nullptr);
 template <>
-void apply_T<double>(dg_domain* dom, int level, const double* u, double* out, const double* b, cudaStream_t s) {
-  apply_level(dom, level, u, out, b, true, s);
+void apply_T<double>(dg_domain* dom, int level, const double* u, double* out, const double* b, cudaStream_t s,
+                     const SubdomainOut* so) {
+  apply_level(dom, level, u, out, b, true, s, so);
 }
 template <>
-void apply_T<float>(dg_domain* dom, int level, const float* u, float* out, const float* b, cudaStream_t s) {
-  apply_level_f32(dom, level, u, out, b, true, s);
+void apply_T<float>(dg_domain* dom, int level, const float* u, float* out, const float* b, cudaStream_t s,
+                    const SubdomainOut* so) {
+  apply_level_f32(dom, level, u, out, b, true, s, so);
 }
 
 template <typename T>
@@ -89,7 +92,8 @@ const float* Ihi<float>(dg_domain* dom) { return dom->Ihi32.get(); }
 }  // namespace
 
 template <typename T>
-void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, cudaStream_t s);
+void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
+                             cudaStream_t s);
 
 namespace {
 // du_S = A_S^-1 r_S for every subdomain of every class
@@ -98,16 +102,16 @@ void class_gemm(dg_domain* dom, const Level& L, const T* X, T* Y, cudaStream_t s
 template <>
 void class_gemm<double>(dg_domain* dom, const Level& L, const double* X, double* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
-  launch_class_gemm_tiles<double>(sw.inv64.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, s);
+  launch_class_gemm_tiles<double>(sw.inv64.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, sw.inv_scale, s);
 }
 template <>
 void class_gemm<float>(dg_domain* dom, const Level& L, const float* X, float* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
   if (dom->use_tc)
     launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, sw.tiles_tc.get(), sw.n_tiles_tc,
-                         dom->err_flag.get(), s);
+                         dom->err_flag.get(), (float)sw.inv_scale, s);
   else
-    launch_class_gemm_tiles<float>(sw.inv32.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, s);
+    launch_class_gemm_tiles<float>(sw.inv32.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, (float)sw.inv_scale, s);
 }
 }  // namespace
 
@@ -119,18 +123,23 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
   SchwarzLevel& sw = L.sw;
   DG_REQUIRE(inverses<T>(sw) != nullptr && shares<T>(dom) != nullptr,
              "Schwarz data of this precision are not built for this domain");
+  SubdomainOut so;
+  so.rS = W.rS.get();
+  so.ld = sw.ld;
+  so.ov = dom->desc.overlap;
+  so.col_of_elem = sw.col_of_elem.get();
+  so.orient = sw.xform_of_elem.get();
+  so.inv = dom->orient_inv.get();
   for (int it = 0; it < iterations; ++it) {
-    const T* r = b;  // with u = 0 the residual is b itself
-    if (!(it == 0 && u_is_zero)) {
-      apply_T<T>(dom, level, u, W.r.get(), b, s);  // r = b - A u
-      r = W.r.get();
-    }
     const double sz = sizeof(T), vec = (double)L.E * sw.nS * sz;
     const int ld = sw.ld;
-    {
+    if (it == 0 && u_is_zero) {
+      // with u = 0 the residual is b itself: gather it into the subdomain vectors
       PhaseScope ps(dom->prof, DG_PHASE_GATHER, s, L.ndof * sz + vec, 0.0);
-      launch_gather_tab<T>(sw.geom, r, sw.elem_of_col.get(), sw.xform_of_elem.get(), dom->orient_map.get(), W.rS.get(),
+      launch_gather_tab<T>(sw.geom, b, sw.elem_of_col.get(), sw.xform_of_elem.get(), dom->orient_map.get(), W.rS.get(),
                            s);
+    } else {
+      apply_T<T>(dom, level, u, nullptr, b, s, &so);  // r = b - A u, written straight into r_S
     }
     const bool linearized = level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE &&
                             dom->subdomain_iterations > 0 && lin_diag<T>(dom) != nullptr;
@@ -329,20 +338,31 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Krylov workspace for k iterations: V (k + 1 vectors) and Z (k vectors), grown on demand
+// (doubling, contents kept) so that short solves do not hold a basis sized for the iteration cap.
 void ensure_workspace(dg_domain* dom, int k) {
   const int64_t n = dom->levels[0].ndof;
+  if (!dom->w.get()) {
+    dom->w.alloc(n);
+    dom->r.alloc(n);
+    dom->du.alloc(n);
+    dom->ut.alloc(n);
+    dom->rt.alloc(n);
+    dom->tmp.alloc(n);
+  }
   if (dom->kcap >= k) return;
-  dom->V.alloc((size_t)(k + 1) * n);
-  dom->Zb.alloc((size_t)k * n);
-  dom->w.alloc(n);
-  dom->r.alloc(n);
-  dom->du.alloc(n);
-  dom->ut.alloc(n);
-  dom->rt.alloc(n);
-  dom->tmp.alloc(n);
-  dom->partial.alloc((size_t)multidot_partial_blocks() * (k + 2));
-  dom->dots.alloc(3 * (size_t)(k + 2));
-  dom->kcap = k;
+  const int cap = std::max(k, std::min(2 * std::max(dom->kcap, 8), 400));
+  DevBuf<double> V((size_t)(cap + 1) * n), Z((size_t)cap * n);
+  if (dom->kcap > 0) {
+    DG_CUDA(cudaMemcpyAsync(V.get(), dom->V.get(), dom->V.bytes(), cudaMemcpyDeviceToDevice, dom->stream));
+    DG_CUDA(cudaMemcpyAsync(Z.get(), dom->Zb.get(), dom->Zb.bytes(), cudaMemcpyDeviceToDevice, dom->stream));
+    DG_CUDA(cudaStreamSynchronize(dom->stream));
+  }
+  dom->V = std::move(V);
+  dom->Zb = std::move(Z);
+  dom->partial.alloc((size_t)multidot_partial_blocks() * (cap + 2));
+  dom->dots.alloc(3 * (size_t)(cap + 2));
+  dom->kcap = cap;
 }
 
 double norm2(dg_domain* dom, const double* x, cudaStream_t s) {
@@ -366,10 +386,8 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
                     bool rel_to_b) {
   cudaStream_t s = dom->stream;
   const int64_t n = dom->levels[0].ndof;
-  ensure_workspace(dom, max_it);
+  ensure_workspace(dom, std::min(max_it, 16));
   LinearResult R;
-  double* V = dom->V.get();
-  double* Z = dom->Zb.get();
   double* w = dom->w.get();
   apply_level(dom, 0, x, dom->r.get(), b, true, s);  // r = b - A x
   const double beta = norm2(dom, dom->r.get(), s);
@@ -377,13 +395,20 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
   const double ref = rel_to_b ? ref_b_norm : beta;
   if (!std::isfinite(beta)) { R.status = DG_ERR_BREAKDOWN; return R; }
   if (beta <= tol * ref || beta == 0.0) { R.final_res = beta; return R; }
-  launch_axpby<double>(n, 1.0 / beta, dom->r.get(), 0.0, V, s);
+  launch_axpby<double>(n, 1.0 / beta, dom->r.get(), 0.0, dom->V.get(), s);
   std::vector<double> H((size_t)(max_it + 1) * max_it, 0.0), cs(max_it), sn(max_it), g(max_it + 1, 0.0);
   g[0] = beta;
   int k = 0;
-  double* dh = dom->dots.get();  // [h1 (k+2) | h2 (k+2) | norm]
   std::vector<double> hh(2 * (max_it + 2) + 1);
   for (int j = 0; j < max_it; ++j) {
+    ensure_workspace(dom, j + 1);  // may move V and Z (contents kept)
+    double* V = dom->V.get();
+    double* Z = dom->Zb.get();
+    double* dh = dom->dots.get();  // [h1 (max_it+2) | h2 (max_it+2) | norm]
+    if ((int64_t)dom->dots.count < 2 * (max_it + 2) + 1) {
+      dom->dots.alloc(2 * (size_t)(max_it + 2) + 1);
+      dh = dom->dots.get();
+    }
     precondition(dom, pmode, V + (size_t)j * n, Z + (size_t)j * n, s);
     apply_level(dom, 0, Z + (size_t)j * n, w, nullptr, true, s);
     // classical Gram-Schmidt, twice
@@ -419,6 +444,8 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
     launch_axpby<double>(n, 1.0 / hn, w, 0.0, V + (size_t)(j + 1) * n, s);
   }
   if (k > 0) {
+    double* Z = dom->Zb.get();
+    double* dh = dom->dots.get();
     std::vector<double> y(k);
     for (int i = k - 1; i >= 0; --i) {
       double acc = g[i];
@@ -473,7 +500,7 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
   const int pmode = o.precondition;
   DG_REQUIRE(pmode >= 0 && pmode <= 2, "precondition must be 0, 1 or 2");
   DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
-  ensure_workspace(dom, max_it);
+  ensure_workspace(dom, std::min(max_it, 16));
   dg_solve_report R{};
   if (dom->desc.problem == DG_PROBLEM_POISSON) {
     const double bn = o.relative_to_b ? norm2(dom, b, s) : 0.0;

@@ -6,8 +6,10 @@
 // output tile: TMA streams 128 x 32 tiles of Inv_c and 64 x 32 tiles of X (128-byte swizzle) into a
 // 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
 // instruction) accumulating in tensor memory, and the four warps read the accumulator back with
-// tcgen05.ld and store it column-contiguously. Every wait is bounded: on timeout the CTA raises an
-// error flag, drains and frees its tensor memory.
+// tcgen05.ld and store it column-contiguously. When the tiles alone cannot fill the GPU, the K
+// range is split across a 4-CTA cluster and the partial tiles are summed through distributed
+// shared memory in a fixed order. Every wait is bounded: on timeout the CTA raises an error flag,
+// drains and frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -113,9 +115,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float ld_peer(uint32_t local_addr, uint32_t rank) {
+  uint32_t remote;
+  float v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+// SPLIT > 1: the K range of a tile is split across the SPLIT CTAs of a thread-block cluster; each
+// keeps its partial 128 x 64 tile in shared memory and, after a cluster barrier, every CTA sums a
+// quarter (1/SPLIT) of the tile's columns over all partials through distributed shared memory in
+// rank order, so the result does not depend on timing.
+template <int SPLIT>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   float* __restrict__ Y, int ld, const int4* __restrict__ tiles, int* __restrict__ err) {
+                   float* __restrict__ Y, int ld, const int4* __restrict__ tiles, int* __restrict__ err,
+                   float alpha) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
@@ -125,10 +151,13 @@ __global__ void __launch_bounds__(128, 1)
   int* s_issued = (int*)(tmem_slot + 1);    // TMA chunks issued by the producer
   int* s_consumed = (int*)(tmem_slot + 2);  // chunks the MMA thread saw arrive
 
-  const int4 tile = tiles[blockIdx.x];
+  const int split = SPLIT > 1 ? (int)cluster_rank() : 0;
+  const int4 tile = tiles[blockIdx.x / SPLIT];
   const int cls = tile.x, row0 = tile.y, col0 = tile.z, ncol = min(tile.w, BN);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = ld / BK;
+  const int nk_all = ld / BK;
+  const int kc0 = split * nk_all / SPLIT, kc1 = (split + 1) * nk_all / SPLIT;
+  const int nk = kc1 - kc0;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
 
   if (threadIdx.x == 0) {
@@ -158,8 +187,8 @@ __global__ void __launch_bounds__(128, 1)
       const int s = kc % STAGES;
       if (kc >= STAGES && !mbar_wait(empty0 + 8 * s, ((kc / STAGES) & 1) ^ 1, err)) break;
       mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-      tma_load_3d(smem_u32(sA + s * A_BYTES), &mapA, full0 + 8 * s, kc * BK, row0, cls);
-      tma_load_2d(smem_u32(sB + s * B_BYTES), &mapB, full0 + 8 * s, kc * BK, col0);
+      tma_load_3d(smem_u32(sA + s * A_BYTES), &mapA, full0 + 8 * s, (kc0 + kc) * BK, row0, cls);
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &mapB, full0 + 8 * s, (kc0 + kc) * BK, col0);
       *s_issued = kc + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -182,17 +211,41 @@ __global__ void __launch_bounds__(128, 1)
   // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
   const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0, err));
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = row0 + warp * 32 + lane;
+  const int r_local = warp * 32 + lane;
+  const int row = row0 + r_local;
+  if (SPLIT == 1) {
 #pragma unroll
-  for (int c0 = 0; c0 < BN; c0 += 16) {
-    if (!ok) break;
-    uint32_t v[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-    if (row < ld) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      if (!ok) break;
+      uint32_t v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (row < ld) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (c0 + j < ncol) Y[(size_t)(col0 + c0 + j) * ld + row] = __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < ncol) Y[(size_t)(col0 + c0 + j) * ld + row] = alpha * __uint_as_float(v[j]);
+      }
     }
+  } else {
+    // partial tile -> own shared memory (column-major, 128 rows per column; the ring is idle now)
+    float* part = reinterpret_cast<float*>(smem);
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) part[(c0 + j) * BM + r_local] = ok ? __uint_as_float(v[j]) : 0.0f;
+    }
+    cluster_sync();
+    constexpr int CPR = BN / SPLIT;  // columns reduced by this CTA
+    for (int j = 0; j < CPR; ++j) {
+      const int c = split * CPR + j;
+      const uint32_t a = smem_u32(part + c * BM + r_local);
+      float acc = 0.0f;
+#pragma unroll
+      for (int p = 0; p < SPLIT; ++p) acc += ld_peer(a, (uint32_t)p);
+      if (row < ld && c < ncol) Y[(size_t)(col0 + c) * ld + row] = alpha * acc;
+    }
+    cluster_sync();  // no CTA leaves while a peer still reads its partial tile
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -238,7 +291,7 @@ CUtensorMap make_map(const float* base, int rank, const cuuint64_t* dims, const 
 bool tc_gemm_available() { return encode_fn() != nullptr; }
 
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, cudaStream_t s) {
+                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s) {
   if (n_tiles == 0) return;
   DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
   const cuuint64_t dA[3] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)n_classes};
@@ -251,9 +304,28 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
   const CUtensorMap mB = make_map(X, 2, dB, sBr, bB);
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
-  tc_gemm_kernel<<<n_tiles, 128, SMEM_BYTES, s>>>(mA, mB, Y, ld, d_tiles, err);
+  // split K over 4-CTA clusters when the tiles alone would leave most SMs idle
+  const int nk = ld / BK;
+  if (n_tiles * 2 <= 152 * 3 && nk >= 8) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_tiles * 4);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 4;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4>, mA, mB, Y, ld, d_tiles, err, alpha));
+  } else {
+    tc_gemm_kernel<1><<<n_tiles, 128, SMEM_BYTES, s>>>(mA, mB, Y, ld, d_tiles, err, alpha);
+  }
   DG_LAUNCHED(1);
 }
 

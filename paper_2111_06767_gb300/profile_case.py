@@ -1,0 +1,49 @@
+"""Run one operation of the solver a few times on a seeded input, for kernel profiling.
+
+    python -m paper_2111_06767_gb300.profile_case --op smooth --n 8 --N 8 --reps 3
+    python -m paper_2111_06767_gb300.profile_case --op apply --n 80 --N 4 --precision mixed --reps 3
+
+--op smooth: Schwarz smoothing steps on the finest level (residual apply, gather, subdomain GEMM,
+scatter); --op apply: the DG operator alone (FP32 for --precision mixed, FP64 otherwise);
+--op vcycle: full V-cycles. The domain is [-1,1]^3 with n^3 elements and N points per dimension.
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+import paper_2111_06767_gb300 as dgg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["smooth", "apply", "vcycle"], default="smooth")
+    ap.add_argument("--n", type=int, default=8)
+    ap.add_argument("--N", type=int, default=8)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--gemm", choices=["default", "simt", "tf32"], default="default")
+    ap.add_argument("--levels", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    d = dgg.Domain(n=(a.n,) * 3, N=a.N, precision=a.precision, mg_levels=a.levels, overlap=2, gemm=a.gemm)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    dt = torch.float32 if (a.op == "apply" and a.precision == "mixed") else torch.float64
+    x = torch.empty(d.n_dof, dtype=dt, device="cuda").uniform_(-1, 1, generator=g)
+    y = torch.zeros_like(x)
+    for _ in range(a.reps):
+        if a.op == "apply":
+            if dt == torch.float32:
+                d.apply_f32(x, 0, y)
+            else:
+                d.apply(x, y)
+        elif a.op == "smooth":
+            d.schwarz_smooth(0, x, y, 1)
+        else:
+            d.vcycle(x, y)
+    torch.cuda.synchronize()
+    print(f"{a.op} done: n={a.n}^3 N={a.N} dof={d.n_dof}")
+
+
+if __name__ == "__main__":
+    main()

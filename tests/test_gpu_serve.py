@@ -77,12 +77,12 @@ def test_results_alone_equal_results_in_the_mix():
 
 
 def test_queue_errors():
-    srv = dgg.Server(max_active=1, queue_capacity=1, n_streams=1, memory_budget_bytes=512 << 20)
+    srv = dgg.Server(max_active=1, queue_capacity=1, n_streams=1, memory_budget_bytes=1 << 30)
     st, _ = srv.poll(12345)
     assert st == -8  # DG_ERR_NOT_FOUND
     big, _ = _request("poisson", 64, 8, 1)
     with pytest.raises(dgg.NativeError) as e:
-        srv.submit(big, np.zeros(64**3 * 8**3), tol=1e-8)  # can never fit 512 MiB
+        srv.submit(big, np.zeros(64**3 * 8**3), tol=1e-8)  # 134M points can never fit 1 GiB
     assert e.value.status == -1
     desc, f = _request("poisson", 6, 8, 2)
     t1 = srv.submit(desc, f, tol=1e-10)
