@@ -144,7 +144,10 @@ const char* dg_last_error(const struct dg_domain* dom);
 /* Au = A u on the finest level, FP64 (Sec. II, Eqs. dg_op_auxvars and dg_op_primal with the
  * internal-penalty flux Eq. numflux and the homogeneous Dirichlet fluxes of Eq. bc). For a
  * PUNCTURE domain with a linearization set (dg_set_linearization) this is the linearized
- * operator A + M diag(S'(u_lin)). u and Au must not alias. */
+ * operator A + M diag(S'(u_lin)). u and Au must not alias. The kernel moves whole lines of N
+ * values, so u and Au must be aligned to gcd(16, N sizeof(value)) bytes, as every cudaMalloc or
+ * PyTorch buffer and every whole-vector offset into one is; otherwise DG_ERR_INVALID_ARG. The same
+ * holds for dg_apply_f32 and dg_apply_level. */
 dg_status dg_apply(struct dg_domain* dom, const double* u, double* Au, void* stream);
 /* Same operator in FP32 on multigrid level `level` (0 = finest). */
 dg_status dg_apply_f32(struct dg_domain* dom, int32_t level, const float* u, float* Au, void* stream);

@@ -1,0 +1,74 @@
+// Launch-shape autotuning (element-batch and tile schedules): the first time a kernel shape is
+// seen in the process, every candidate launch configuration is timed with CUDA events on the
+// caller's stream (one warm-up launch, then three timed ones) and the fastest is kept for the rest
+// of the process. The paper has no counterpart; it replaces hand-picked launch heuristics.
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace dg {
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, int> g_tuned;
+
+bool tuning_enabled() {
+  const char* v = std::getenv("DG_AUTOTUNE");
+  return !(v && std::strcmp(v, "0") == 0);
+}
+}  // namespace
+
+int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates,
+             const std::function<void(int)>& run, cudaStream_t s) {
+  DG_REQUIRE(!candidates.empty(), "autotune needs candidates");
+  if (candidates.size() == 1 || !tuning_enabled()) return candidates[0];
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  std::vector<int64_t> k = key;
+  k.push_back(dev);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(k);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  DG_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return candidates[0];
+  cudaEvent_t a = nullptr, b = nullptr;
+  DG_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    fail(DG_ERR_CUDA, "cudaEventCreate failed");
+  }
+  int best = candidates[0];
+  float best_ms = std::numeric_limits<float>::infinity();
+  try {
+    for (int c : candidates) {
+      run(c);  // warm-up (first launch of a kernel pays for module loading)
+      DG_CUDA(cudaEventRecord(a, s));
+      for (int r = 0; r < 3; ++r) run(c);
+      DG_CUDA(cudaEventRecord(b, s));
+      DG_CUDA(cudaEventSynchronize(b));
+      float ms = 0.0f;
+      DG_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    throw;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tuned.emplace(k, best).first->second;
+}
+
+}  // namespace dg

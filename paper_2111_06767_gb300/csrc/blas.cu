@@ -15,8 +15,15 @@ inline int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64
 
 int multidot_partial_blocks() { return kDotBlocks; }
 
+// y = a x + b y; with b == 0 the old y is not read (it may be uninitialised memory whose bits
+// decode as NaN, and 0 * NaN would poison the result)
 template <typename T>
 __global__ void axpby_kernel(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  if (b == T(0)) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      y[i] = a * x[i];
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }

@@ -14,237 +14,420 @@
 // (n F_v)^b = n u_b, u_b = 0, and (n F_u)^b = (n F_u)^int is the ghost state u_ext = -u_int,
 // g_ext = g_int, which this kernel uses.
 //
-// GB300 mapping: EPB elements per CTA (EPB N^2 ~ 256 threads, one per (i, j) column); the element
-// block, its x/y gradients and the face brackets stay in shared memory; neighbour face data (the
-// neighbour's face value and normal derivative, which needs its whole normal line) is read straight
-// from global memory, which L2 serves for the element-ordered sweep.
+// GB300 mapping: one thread per x-line of N points (the N contiguous values of u[e][k][j][:]),
+// N^2 threads per element, EPB elements per CTA. Every global access is a coalesced vector access of
+// whole lines: the element itself, the two x-neighbour lines at the same (j, k) (kept in registers)
+// and the matching lines of the four y/z neighbours (staged in shared memory, which L2 serves for
+// the element-ordered sweep). The x-contractions run in registers with Dhat read from constant
+// memory; the y- and z-contractions read whole lines from shared memory, which the threads of one
+// plane (y) or one column of planes (z) share as broadcasts, with the planes padded so that the
+// lines of one access fall into distinct banks.
+#include <mutex>
+#include <set>
+
 #include "internal.h"
+#include "lines.cuh"
+#include "pdl.cuh"
 
 namespace dg {
 
-// One thread per (i, j) column of N points along z, EPB elements per CTA. The z-contractions run
-// in registers (the column's u and g_z), the x- and y-contractions read shared memory; each thread
-// also owns the six face points with tangential indices (i, j), so the z-faces never touch shared
-// memory and the neighbour z-lines are read coalesced.
-template <int N, typename T>
-struct ColShape {
-  static constexpr int n2 = N * N;
-  static constexpr int bytes_per_elem = (3 * N * N * N + 6 * N * N) * (int)sizeof(T);
-  static constexpr int by_threads = n2 >= 256 ? 1 : 256 / n2;
-  static constexpr int by_smem = (44 * 1024) / bytes_per_elem;
-  static constexpr int epb = by_threads < by_smem ? by_threads : (by_smem < 1 ? 1 : by_smem);
-  static constexpr int threads = epb * n2;
+namespace {
+
+// Dhat and the LGL weights of every supported N, concatenated in constant memory, so that the
+// x-contraction and the per-point quadrature weights with unrolled (compile-time) indices are
+// operands of the FMA instructions themselves.
+constexpr int dtab_off(int N) { return (N - 1) * N * (2 * N - 1) / 6 - 1; }  // sum_{m=2}^{N-1} m^2
+constexpr int wtab_off(int N) { return N * (N - 1) / 2 - 1; }                 // sum_{m=2}^{N-1} m
+constexpr int kDTab = dtab_off(DG_MAX_N + 1), kWTab = wtab_off(DG_MAX_N + 1);
+__constant__ double cD64[kDTab];
+__constant__ float cD32[kDTab];
+__constant__ double cW64[kWTab];
+__constant__ float cW32[kWTab];
+
+template <typename T>
+struct CTab;
+template <>
+struct CTab<double> {
+  static __device__ __forceinline__ double D(int o) { return cD64[o]; }
+  static __device__ __forceinline__ double w(int o) { return cW64[o]; }
+};
+template <>
+struct CTab<float> {
+  static __device__ __forceinline__ float D(int o) { return cD32[o]; }
+  static __device__ __forceinline__ float w(int o) { return cW32[o]; }
 };
 
+// Shared-memory shape. A block holds one element as N planes (k) of N lines (j) of N points (i).
+// The plane stride P is padded so that the lines one y-contraction reads at once (one per plane
+// of the warp's threads) fall into distinct banks: where a line is a power-of-two fraction of the
+// 128-byte bank sweep, P is an odd number of lines (consecutive planes, and with them consecutive
+// elements, then land on distinct line slots); otherwise consecutive planes shift by one line.
+// Per element: five blocks (u and the four y/z neighbours; the neighbour blocks are later reused
+// for v_y, v_z and the face fluxes) and, for each of the four y/z faces, the neighbour's value and
+// normal derivative at the face points (N^2 each).
+template <int N, typename T>
+struct LineShape {
+  static constexpr int s = (int)sizeof(T);
+  static constexpr int line = N * s;
+  static constexpr int P = (128 % line == 0) ? N * (N % 2 == 0 ? N + 1 : N)
+                                             : N * N + ((N - N * N) % (128 / s) + (128 / s)) % (128 / s);
+  static constexpr int R = N * P;
+  static constexpr int n2 = N * N;
+  static constexpr int per_elem = (5 * R + 8 * n2) * s + 14 * (int)sizeof(int);
+  static constexpr int by_threads = n2 >= 256 ? 1 : 256 / n2;
+  static constexpr int by_smem = (47 * 1024) / per_elem;
+  static constexpr int cap = by_threads < by_smem ? by_threads : (by_smem < 1 ? 1 : by_smem);
+  // largest count up to the cap that fills whole warps, if there is one
+  static constexpr int whole(int e) { return e < 1 ? cap : ((e * n2) % 32 == 0 ? e : whole(e - 1)); }
+  static constexpr int epb = whole(cap);
+};
+
+// Lifting and primal flux at one face point of normal s e_d: from the interior value ui and local
+// gradient component gi, the neighbour's value ue and normal derivative ge (has = the neighbour
+// exists; otherwise the Dirichlet ghost state of Eq. bc with u_b = 0), returns the lifted v_d and
+// adds the flux term of the point, weighted by the face quadrature weight Bf, to fl.
+template <typename T>
+__device__ __forceinline__ T face_point(T s, T ui, T gi, T ue, T ge, bool has, T lift, T sigma_minus_lift, T Bf,
+                                        T& fl) {
+  const T uE = has ? ue : -ui;
+  const T gE = has ? ge : gi;
+  const T jump = uE - ui;
+  fl -= Bf * (T(0.5) * s * (gE - gi) + sigma_minus_lift * jump);
+  return gi + s * jump * lift;
+}
+
 template <int N, typename T, int EPB>
-__global__ void __launch_bounds__(EPB* N* N) apply_col_kernel(const OpGeom<T> g, const T* __restrict__ Dg,
-                                                             const T* __restrict__ wg, const T* __restrict__ u,
-                                                             const T* __restrict__ diag, const T* __restrict__ b,
-                                                             T* __restrict__ out, int E, const SubdomainOut so) {
-  constexpr int N2 = N * N, N3 = N * N * N, NT = EPB * N2;
-  __shared__ T sD[N2];
-  __shared__ T sw[N];
-  __shared__ T su[EPB][N3];
-  __shared__ T sv[EPB][2][N3];
-  __shared__ T sfb[EPB][6][N2];
-  const int tid = threadIdx.x;
-  const int el = tid / N2, col = tid - el * N2;
-  const int i = col % N, j = col / N;
-  const int e0 = blockIdx.x * EPB;
-  const int e = e0 + el;
-  const bool valid = e < E;
-  for (int t = tid; t < N2; t += NT) sD[t] = Dg[t];
-  for (int t = tid; t < N; t += NT) sw[t] = wg[t];
+__global__ void __launch_bounds__(EPB* N* N)
+    apply_line_kernel(const OpGeom<T> g, const T* __restrict__ Dg, const T* __restrict__ wg, const T* __restrict__ u,
+                      const T* __restrict__ diag, const T* __restrict__ b, T* __restrict__ out, int E,
+                      T* __restrict__ rS, int ld, int ov, const int* __restrict__ col_of_elem,
+                      const int* __restrict__ orient, const int* __restrict__ inv) {
+  using S = LineShape<N, T>;
+  using C = CTab<T>;
+  constexpr int N2 = N * N, N3 = N2 * N, P = S::P, R = S::R, NT = EPB * N2;
+  constexpr int dO = dtab_off(N), wO = wtab_off(N);
+  __shared__ __align__(16) T sm[5][EPB][R];
+  // y/z face data per face (0..3 = -y, +y, -z, +z): [neighbour value, neighbour normal derivative]
+  // [element][tangential point: (k, i) on y faces, (j, i) on z faces]
+  __shared__ __align__(16) T sf[4][2][EPB][N2];
   // residual written straight into the subdomain vectors: column and point-map offset of this
   // element's own subdomain (slot 0) and of each face neighbour's subdomain (slot 1 + (f ^ 1))
   __shared__ int s_col[EPB][7], s_map[EPB][7];
-  for (int t = tid; so.rS && t < EPB * 7; t += NT) {
-    const int el2 = t / 7, sl = t - el2 * 7;
+  pdl_launch_dependents();
+  const int tid = threadIdx.x;
+  const int el = tid / N2, t = tid - el * N2;
+  const int j = t % N, k = t / N;
+  const int e0 = blockIdx.x * EPB;
+  const int e = e0 + el;
+  const bool valid = e < E;
+  const int ec = valid ? e : E - 1;  // threads past the end load a real element and store nothing
+  const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
+  const int cx = ec % nx, cy = (ec / nx) % ny, cz = ec / nxy;
+  const bool hxm = cx > 0, hxp = cx + 1 < nx, hym = cy > 0, hyp = cy + 1 < ny, hzm = cz > 0, hzp = cz + 1 < g.nz;
+  for (int q = tid; rS && q < EPB * 7; q += NT) {
+    const int el2 = q / 7, sl = q - el2 * 7;
     const int e2 = e0 + el2;
     int c = -1, m = 0;
     if (e2 < E) {
-      int q = e2;
+      int r = e2;
       if (sl > 0) {
         const int f = sl - 1, d = f >> 1;
-        int c3[3] = {e2 % g.nx, (e2 / g.nx) % g.ny, e2 / (g.nx * g.ny)};
-        const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+        int c3[3] = {e2 % nx, (e2 / nx) % ny, e2 / nxy};
+        const int nd = d == 0 ? nx : (d == 1 ? ny : g.nz);
         c3[d] += (f & 1) ? 1 : -1;
-        q = (c3[d] >= 0 && c3[d] < nd) ? c3[0] + g.nx * (c3[1] + g.ny * c3[2]) : -1;
+        r = (c3[d] >= 0 && c3[d] < nd) ? c3[0] + nx * (c3[1] + ny * c3[2]) : -1;
       }
-      if (q >= 0) {
-        c = so.col_of_elem[q];
-        m = (so.orient[q] * 7 + (sl == 0 ? 0 : 1 + ((sl - 1) ^ 1))) * N * N * N;
+      if (r >= 0) {
+        c = col_of_elem[r];
+        m = (orient[r] * 7 + (sl == 0 ? 0 : 1 + ((sl - 1) ^ 1))) * N3;
       }
     }
     s_col[el2][sl] = c;
     s_map[el2][sl] = m;
   }
-  T uk[N], gz[N];
-  const T* ue = u + (int64_t)e * N3;
+  // rows j and k of Dhat, scaled by 2/h_y and 2/h_z, and the weights (static data: read before
+  // waiting for the previous kernel)
+  T Dj[N], Dk[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    uk[k] = valid ? ue[(k * N + j) * N + i] : T(0);
-    su[el][(k * N + j) * N + i] = uk[k];
+  for (int l = 0; l < N; ++l) {
+    Dj[l] = g.dxi[1] * __ldg(Dg + j * N + l);
+    Dk[l] = g.dxi[2] * __ldg(Dg + k * N + l);
   }
-  __syncthreads();
-  // local gradient: x, y from shared memory, z in registers
+  const T wj = __ldg(wg + j), wk = __ldg(wg + k);
+  pdl_wait();
+  // all loads of the thread's seven lines first (a missing neighbour reads the element itself and
+  // is replaced by the ghost state), then the shared-memory stores
+  const int64_t line = (int64_t)t * N;
+  T ul[N], xm[N], xp[N], ym[N], yp[N], zm[N], zp[N];
+  gld_line<N>(u + (int64_t)ec * N3 + line, ul);
+  gld_line<N>(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + line, xm);
+  gld_line<N>(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + line, xp);
+  gld_line<N>(u + (int64_t)(hym ? ec - nx : ec) * N3 + line, ym);
+  gld_line<N>(u + (int64_t)(hyp ? ec + nx : ec) * N3 + line, yp);
+  gld_line<N>(u + (int64_t)(hzm ? ec - nxy : ec) * N3 + line, zm);
+  gld_line<N>(u + (int64_t)(hzp ? ec + nxy : ec) * N3 + line, zp);
+  const int so = k * P + j * N;  // this thread's line within a block
+  sst_line<N>(&sm[0][el][so], ul);
+  sst_line<N>(&sm[1][el][so], ym);
+  sst_line<N>(&sm[2][el][so], yp);
+  sst_line<N>(&sm[3][el][so], zm);
+  sst_line<N>(&sm[4][el][so], zp);
+  // x-neighbour traces: the value on the shared face and the neighbour's normal derivative there
+  const T uxm = xm[N - 1], uxp = xp[0];
+  T gxm = T(0), gxp = T(0);
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    T gx = 0, gy = 0, gzk = 0;
+  for (int l = 0; l < N; ++l) {
+    gxm += C::D(dO + (N - 1) * N + l) * xm[l];
+    gxp += C::D(dO + l) * xp[l];
+  }
+  gxm *= g.dxi[0];
+  gxp *= g.dxi[0];
+  __syncthreads();
+  // y/z face data, one face point per thread and face (all threads share the work): on the y faces
+  // the point (i, k) = (j, k), on the z faces the point (i, j) = (k, j)
+  {
+    T gmy = T(0), gpy = T(0), gmz = T(0), gpz = T(0);
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      gx += sD[i * N + l] * su[el][(k * N + j) * N + l];
-      gy += sD[j * N + l] * su[el][(k * N + l) * N + i];
-      gzk += sD[k * N + l] * uk[l];
+      gmy += C::D(dO + (N - 1) * N + l) * sm[1][el][k * P + l * N + j];
+      gpy += C::D(dO + l) * sm[2][el][k * P + l * N + j];
+      gmz += C::D(dO + (N - 1) * N + l) * sm[3][el][l * P + j * N + k];
+      gpz += C::D(dO + l) * sm[4][el][l * P + j * N + k];
     }
-    sv[el][0][(k * N + j) * N + i] = g.dxi[0] * gx;
-    sv[el][1][(k * N + j) * N + i] = g.dxi[1] * gy;
-    gz[k] = g.dxi[2] * gzk;
+    const int py = k * N + j, pz = j * N + k;
+    sf[0][0][el][py] = sm[1][el][k * P + (N - 1) * N + j];
+    sf[0][1][el][py] = g.dxi[1] * gmy;
+    sf[1][0][el][py] = sm[2][el][k * P + j];
+    sf[1][1][el][py] = g.dxi[1] * gpy;
+    sf[2][0][el][pz] = sm[3][el][(N - 1) * P + j * N + k];
+    sf[2][1][el][pz] = g.dxi[2] * gmz;
+    sf[3][0][el][pz] = sm[4][el][j * N + k];
+    sf[3][1][el][pz] = g.dxi[2] * gpz;
+  }
+  // local gradient: x in registers, y and z from the lines of the element block
+  T vx[N], vy[N], vz[N], tmp[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T a = T(0);
+#pragma unroll
+    for (int l = 0; l < N; ++l) a += C::D(dO + i * N + l) * ul[l];
+    vx[i] = g.dxi[0] * a;
+    vy[i] = T(0);
+    vz[i] = T(0);
+  }
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    sld_line<N>(&sm[0][el][k * P + l * N], tmp);
+#pragma unroll
+    for (int i = 0; i < N; ++i) vy[i] += Dj[l] * tmp[i];
+  }
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    sld_line<N>(&sm[0][el][l * P + j * N], tmp);
+#pragma unroll
+    for (int i = 0; i < N; ++i) vz[i] += Dk[l] * tmp[i];
+  }
+  // x faces in registers: lifting into v_x at i = 0 and N-1, primal flux into o
+  T o[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = T(0);
+  {
+    const T Bf = g.Jf[0] * wj * wk, sml = g.sigma[0] - g.lift[0];
+    vx[0] = face_point(T(-1), ul[0], vx[0], uxm, gxm, hxm, g.lift[0], sml, Bf, o[0]);
+    vx[N - 1] = face_point(T(1), ul[N - 1], vx[N - 1], uxp, gxp, hxp, g.lift[0], sml, Bf, o[N - 1]);
+  }
+  __syncthreads();  // face data written; every read of the neighbour blocks is done
+  sst_line<N>(&sm[1][el][so], vy);
+  sst_line<N>(&sm[2][el][so], vz);
+  __syncthreads();
+  // y/z faces, one point per thread and face: lift v_y (block 1) / v_z (block 2) in shared memory,
+  // fluxes into blocks 3 (y faces) and 4 (z faces) at offsets 0 (lower) and N^2 (upper)
+  {
+    const T Bf = wj * wk;  // w_i w_k on y faces (i = j), w_i w_j on z faces (i = k)
+    const int py = k * N + j, pz = j * N + k;
+    T fl = T(0);
+    T* v = &sm[1][el][k * P + j];
+    *v = face_point(T(-1), sm[0][el][k * P + j], *v, sf[0][0][el][py], sf[0][1][el][py], hym, g.lift[1],
+                    g.sigma[1] - g.lift[1], g.Jf[1] * Bf, fl);
+    sm[3][el][py] = fl;
+    fl = T(0);
+    v = &sm[1][el][k * P + (N - 1) * N + j];
+    *v = face_point(T(1), sm[0][el][k * P + (N - 1) * N + j], *v, sf[1][0][el][py], sf[1][1][el][py], hyp,
+                    g.lift[1], g.sigma[1] - g.lift[1], g.Jf[1] * Bf, fl);
+    sm[3][el][N2 + py] = fl;
+    fl = T(0);
+    v = &sm[2][el][j * N + k];
+    *v = face_point(T(-1), sm[0][el][j * N + k], *v, sf[2][0][el][pz], sf[2][1][el][pz], hzm, g.lift[2],
+                    g.sigma[2] - g.lift[2], g.Jf[2] * Bf, fl);
+    sm[4][el][pz] = fl;
+    fl = T(0);
+    v = &sm[2][el][(N - 1) * P + j * N + k];
+    *v = face_point(T(1), sm[0][el][(N - 1) * P + j * N + k], *v, sf[3][0][el][pz], sf[3][1][el][pz], hzp,
+                    g.lift[2], g.sigma[2] - g.lift[2], g.Jf[2] * Bf, fl);
+    sm[4][el][N2 + pz] = fl;
   }
   __syncthreads();
-  // the six face points with tangential indices (a1, a2) = (i, j). Branch-free: a face without a
-  // neighbour reads the thread's own element (in bounds) and discards it, so the loads of all six
-  // neighbour lines are independent and can be in flight together.
-  if (valid) {
-    const int cx = e % g.nx, cy = (e / g.nx) % g.ny, cz = e / (g.nx * g.ny);
-    T u_ext[6], g_ext[6];
-    unsigned external = 0;  // bit f: face f is on the domain boundary
+  // y/z face fluxes of the thread's own points
+  if (j == 0) {
+    sld_line<N>(&sm[3][el][k * N], tmp);
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const int d = f >> 1, side = f & 1;
-      const int opp = side ? 0 : N - 1;
-      int base, stride;
-      if (d == 0) { base = (j * N + i) * N; stride = 1; }
-      else if (d == 1) { base = j * N2 + i; stride = N; }
-      else { base = j * N + i; stride = N2; }
-      const int cd = d == 0 ? cx : (d == 1 ? cy : cz);
-      const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
-      const int cn = cd + (side ? 1 : -1);
-      const bool has = cn >= 0 && cn < nd;
-      const int es = d == 0 ? 1 : (d == 1 ? g.nx : g.nx * g.ny);
-      const T* uq = u + (int64_t)(has ? e + (side ? es : -es) : e) * N3 + base;
-      T acc = 0, ue = 0;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const T v = __ldg(uq + l * stride);
-        acc += sD[opp * N + l] * v;
-        if (l == opp) ue = v;
-      }
-      const T dxi = d == 0 ? g.dxi[0] : (d == 1 ? g.dxi[1] : g.dxi[2]);
-      u_ext[f] = ue;
-      g_ext[f] = dxi * acc;
-      external |= (has ? 0u : 1u) << f;
-    }
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const int d = f >> 1, side = f & 1;
-      const T s = side ? T(1) : T(-1);
-      const int idx = side ? N - 1 : 0;
-      int pf;
-      if (d == 0) pf = (j * N + i) * N + idx;
-      else if (d == 1) pf = (j * N + idx) * N + i;
-      else pf = (idx * N + j) * N + i;
-      const T lift = d == 0 ? g.lift[0] : (d == 1 ? g.lift[1] : g.lift[2]);
-      const T sigma = d == 0 ? g.sigma[0] : (d == 1 ? g.sigma[1] : g.sigma[2]);
-      const T Jf = d == 0 ? g.Jf[0] : (d == 1 ? g.Jf[1] : g.Jf[2]);
-      const T u_int = d == 2 ? uk[idx] : su[el][pf];
-      const T g_int = d == 2 ? gz[idx] : sv[el][d][pf];
-      const bool ext = (external >> f) & 1u;
-      // Dirichlet ghost state of Eq. bc with u_b = 0 at external faces
-      const T ue = ext ? -u_int : u_ext[f];
-      const T ge = ext ? g_int : g_ext[f];
-      const T jump = ue - u_int;
-      const T v_face = g_int + s * jump * lift;
-      if (d == 2) gz[idx] = v_face;
-      else sv[el][d][pf] = v_face;
-      sfb[el][f][j * N + i] = Jf * sw[i] * sw[j] * (T(0.5) * s * (ge - g_int) + (sigma - lift) * jump);
-    }
+    for (int i = 0; i < N; ++i) o[i] += tmp[i];
   }
-  __syncthreads();
-  if (!valid) return;
+  if (j == N - 1) {
+    sld_line<N>(&sm[3][el][N2 + k * N], tmp);
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] += tmp[i];
+  }
+  if (k == 0) {
+    sld_line<N>(&sm[4][el][j * N], tmp);
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] += tmp[i];
+  }
+  if (k == N - 1) {
+    sld_line<N>(&sm[4][el][N2 + j * N], tmp);
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] += tmp[i];
+  }
   // primal step: -M sum_d D_d v_d - ML [(n.v)^* - n.v]
-  T* oe = out + (int64_t)e * N3;
+  T dy[N], dz[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    T dx = 0, dy = 0, dz = 0;
+  for (int i = 0; i < N; ++i) {
+    dy[i] = T(0);
+    dz[i] = T(0);
+  }
 #pragma unroll
-    for (int l = 0; l < N; ++l) {
-      dx += sD[i * N + l] * sv[el][0][(k * N + j) * N + l];
-      dy += sD[j * N + l] * sv[el][1][(k * N + l) * N + i];
-      dz += sD[k * N + l] * gz[l];
-    }
-    const T M = g.J * sw[i] * sw[j] * sw[k];
-    T res = -M * (g.dxi[0] * dx + g.dxi[1] * dy + g.dxi[2] * dz);
-    if (i == 0) res -= sfb[el][0][k * N + j];
-    if (i == N - 1) res -= sfb[el][1][k * N + j];
-    if (j == 0) res -= sfb[el][2][k * N + i];
-    if (j == N - 1) res -= sfb[el][3][k * N + i];
-    if (k == 0) res -= sfb[el][4][j * N + i];
-    if (k == N - 1) res -= sfb[el][5][j * N + i];
-    const int p = (k * N + j) * N + i;
-    if (diag) res += diag[(int64_t)e * N3 + p] * uk[k];
-    const T val = b ? b[(int64_t)e * N3 + p] - res : res;
-    if (!so.rS) {
-      oe[p] = val;
-    } else {
-      // every subdomain row holds exactly one point, so these stores never collide
-      const int cc[3] = {i, j, k};
+  for (int l = 0; l < N; ++l) {
+    sld_line<N>(&sm[1][el][k * P + l * N], tmp);
 #pragma unroll
-      for (int sl = 0; sl < 7; ++sl) {
-        const int c = s_col[el][sl];
-        if (c < 0) continue;
-        if (sl > 0) {
-          // only points within N_overlap layers of a face belong to that neighbour's subdomain
-          const int f = sl - 1, dd = f >> 1;
-          const int depth = (f & 1) ? N - 1 - cc[dd] : cc[dd];
-          if (depth >= so.ov) continue;
-        }
-        const int row = __ldg(so.inv + s_map[el][sl] + p);
-        if (row >= 0) static_cast<T*>(so.rS)[(int64_t)c * so.ld + row] = val;
+    for (int i = 0; i < N; ++i) dy[i] += Dj[l] * tmp[i];
+  }
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    sld_line<N>(&sm[2][el][l * P + j * N], tmp);
+#pragma unroll
+    for (int i = 0; i < N; ++i) dz[i] += Dk[l] * tmp[i];
+  }
+  if (!valid) return;
+  const int64_t base = (int64_t)ec * N3 + line;
+  T dl[N], bl[N];
+  if (diag) gld_line<N>(diag + base, dl);
+  if (b) gld_line<N>(b + base, bl);
+  T val[N];
+  const T M0 = g.J * wj * wk;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T dx = T(0);
+#pragma unroll
+    for (int l = 0; l < N; ++l) dx += C::D(dO + i * N + l) * vx[l];
+    T res = -(M0 * C::w(wO + i)) * (g.dxi[0] * dx + dy[i] + dz[i]) + o[i];
+    if (diag) res += dl[i] * ul[i];
+    val[i] = b ? bl[i] - res : res;
+  }
+  if (!rS) {
+    gst_line<N>(out + base, val);
+    return;
+  }
+  // every subdomain row holds exactly one point, so these stores never collide; unrolled so that
+  // the seven row-table loads are in flight together
+#pragma unroll
+  for (int sl = 0; sl < 7; ++sl) {
+    const int c = s_col[el][sl];
+    if (c < 0) continue;
+    int lo = 0, hi = N;  // points of the line inside this slot's subdomain (N_overlap layers of a face)
+    if (sl > 0) {
+      const int f = sl - 1, dd = f >> 1, side = f & 1;
+      if (dd == 0) {
+        if (side) lo = N - ov;
+        else hi = ov;
+      } else {
+        const int cc = dd == 1 ? j : k;
+        if ((side ? N - 1 - cc : cc) >= ov) continue;
       }
     }
+    int rows[N];
+    gld_line<N>(inv + s_map[el][sl] + t * N, rows);
+    T* colp = rS + (int64_t)c * ld;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i >= lo && i < hi && rows[i] >= 0) colp[rows[i]] = val[i];
   }
 }
 
+template <int N, typename T, int EPB>
+void launch_apply_epb(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
+                      const SubdomainOut& so, int E, cudaStream_t s) {
+  launch_pdl(apply_line_kernel<N, T, EPB>, dim3((E + EPB - 1) / EPB), dim3(EPB * N * N), 0, s, g, D, w, u, diag, b,
+             out, E, static_cast<T*>(so.rS), so.ld, so.ov, so.col_of_elem, so.orient, so.inv);
+}
+
+// Launch shapes: elements per CTA from the shared-memory/thread budget (S::epb), the fewest that
+// fill a warp (kSmall) and one in between. Variant 0 picks by grid size; 1..3 force one of them
+// (the autotuner times them per level).
 template <int N, typename T>
-static void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                           const SubdomainOut& so, cudaStream_t s) {
+void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
+                    const SubdomainOut& so, int variant, cudaStream_t s) {
   const int E = g.nx * g.ny * g.nz;
-  using C = ColShape<N, T>;
+  if (E == 0) return;
+  constexpr unsigned a = LineVec<N, T>::w - 1;  // lines move in vectors of this many bytes
+  DG_REQUIRE(!(((uintptr_t)u | (uintptr_t)diag | (uintptr_t)b | (uintptr_t)out | (uintptr_t)so.rS) & a),
+             "DG apply vectors must be aligned to " + std::to_string(a + 1) + " bytes");
+  using S = LineShape<N, T>;
   constexpr int kSmall = N * N >= 32 ? 1 : (32 + N * N - 1) / (N * N);  // at least one warp per CTA
-  if ((E + C::epb - 1) / C::epb >= 2 * 152 || C::epb <= kSmall) {
-    const int blocks = (E + C::epb - 1) / C::epb;
-    apply_col_kernel<N, T, C::epb><<<blocks, C::threads, 0, s>>>(g, D, w, u, diag, b, out, E, so);
-  } else {
-    // small grids: fewer elements per CTA so that every SM gets work
-    const int blocks = (E + kSmall - 1) / kSmall;
-    apply_col_kernel<N, T, kSmall><<<blocks, kSmall * N * N, 0, s>>>(g, D, w, u, diag, b, out, E, so);
+  constexpr int kBig = S::epb > kSmall ? S::epb : kSmall;
+  constexpr int kMid = (kSmall + kBig) / 2;
+  if (variant == 0) variant = ((E + kBig - 1) / kBig >= 2 * 152) ? 3 : 1;
+  if (variant == 1) launch_apply_epb<N, T, kSmall>(g, D, w, u, diag, b, out, so, E, s);
+  else if (variant == 2) launch_apply_epb<N, T, kMid>(g, D, w, u, diag, b, out, so, E, s);
+  else launch_apply_epb<N, T, kBig>(g, D, w, u, diag, b, out, so, E, s);
+}
+
+}  // namespace
+
+void upload_operator_tables() {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(dev)) return;
+  std::vector<double> D(kDTab), W(kWTab);
+  for (int N = 2; N <= DG_MAX_N; ++N) {
+    const LglTables t = make_lgl(N);
+    std::copy(t.D, t.D + N * N, D.begin() + dtab_off(N));
+    std::copy(t.w, t.w + N, W.begin() + wtab_off(N));
   }
+  const std::vector<float> D32(D.begin(), D.end()), W32(W.begin(), W.end());
+  DG_CUDA(cudaMemcpyToSymbol(cD64, D.data(), sizeof(double) * kDTab));
+  DG_CUDA(cudaMemcpyToSymbol(cD32, D32.data(), sizeof(float) * kDTab));
+  DG_CUDA(cudaMemcpyToSymbol(cW64, W.data(), sizeof(double) * kWTab));
+  DG_CUDA(cudaMemcpyToSymbol(cW32, W32.data(), sizeof(float) * kWTab));
+  done.insert(dev);
 }
 
 template <typename T>
 void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                  cudaStream_t s, const SubdomainOut* so_ptr) {
+                  cudaStream_t s, const SubdomainOut* so_ptr, int variant) {
   const SubdomainOut so = so_ptr ? *so_ptr : SubdomainOut{};
   switch (N) {
-    case 2: launch_apply_n<2, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 3: launch_apply_n<3, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 4: launch_apply_n<4, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 5: launch_apply_n<5, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 6: launch_apply_n<6, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 7: launch_apply_n<7, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 8: launch_apply_n<8, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 9: launch_apply_n<9, T>(g, D, w, u, diag, b, out, so, s); break;
-    case 10: launch_apply_n<10, T>(g, D, w, u, diag, b, out, so, s); break;
+    case 2: launch_apply_n<2, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 3: launch_apply_n<3, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 4: launch_apply_n<4, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 5: launch_apply_n<5, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 6: launch_apply_n<6, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 7: launch_apply_n<7, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 8: launch_apply_n<8, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 9: launch_apply_n<9, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 10: launch_apply_n<10, T>(g, D, w, u, diag, b, out, so, variant, s); break;
     default: fail(DG_ERR_INVALID_ARG, "unsupported N");
   }
   DG_LAUNCHED(1);
 }
 
 template void launch_apply<double>(int, const OpGeom<double>&, const double*, const double*, const double*,
-                                   const double*, const double*, double*, cudaStream_t, const SubdomainOut*);
+                                   const double*, const double*, double*, cudaStream_t, const SubdomainOut*, int);
 template void launch_apply<float>(int, const OpGeom<float>&, const float*, const float*, const float*, const float*,
-                                  const float*, float*, cudaStream_t, const SubdomainOut*);
+                                  const float*, float*, cudaStream_t, const SubdomainOut*, int);
+
 
 // Diagonal of the LGL mass matrix, M = J w_i w_j w_k (Eq. massmat with collocation quadrature).
 template <typename T>

@@ -49,6 +49,10 @@ struct Level {
   SchwarzLevel sw;
   LevelWork<double> w64;
   LevelWork<float> w32;
+  // autotuned launch shapes (-1: not yet tuned): DG apply [FP64, FP32][plain, fused into r_S],
+  // tensor-core GEMM split
+  int apply_variant[2][2] = {{-1, -1}, {-1, -1}};
+  int gemm_split = -1;
 };
 
 // Event-based per-phase timing of launches (dg_profile_*).

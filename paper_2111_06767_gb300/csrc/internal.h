@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <memory>
 #include <string>
 #include <vector>
@@ -89,6 +90,8 @@ struct LglTables {
   double I_hi[DG_MAX_N * DG_MAX_N] = {};     // upper half: l_j((x_t + 1)/2)
 };
 LglTables make_lgl(int N);
+// Dhat and the LGL weights of every N in constant memory, uploaded once per device.
+void upload_operator_tables();
 
 // ------------------------------------------------------------------ operator geometry
 
@@ -120,10 +123,12 @@ struct SubdomainOut {
   const int* inv = nullptr;      // [48][7][N^3] canonical row or -1
 };
 
-// out = A u (+ diag * u)  or, with b != nullptr, out = b - (A u + diag * u).
+// out = A u (+ diag * u)  or, with b != nullptr, out = b - (A u + diag * u). variant: launch shape
+// (0 chosen by grid size, 1..3 few / middle / many elements per CTA).
 template <typename T>
 void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                  cudaStream_t s, const SubdomainOut* so = nullptr);
+                  cudaStream_t s, const SubdomainOut* so = nullptr, int variant = 0);
+constexpr int kApplyVariants = 3;
 
 // Build explicit subdomain matrices A_S for a set of classes (FP64, column-major == row-major by symmetry).
 void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<double>& g, const double* D, const double* w,
@@ -150,8 +155,18 @@ void launch_pad_convert(const S* src, int n, int ld, int n_classes, T* dst, cuda
 
 // Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
 bool tc_gemm_available();
+// split: K split across a cluster of 1, 2, 4 or 8 CTAs; 0 picks it from the tile count.
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s);
+                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split = 0);
+// Splits the tensor-core GEMM accepts for this shape (each CTA keeps >= 4 K chunks).
+std::vector<int> tc_gemm_splits(int ld);
+
+// Launch-shape autotuning: the first time a kernel shape (key) is seen in the process, time each
+// candidate (run(c) launches it once on stream s) and keep the fastest; later calls return the
+// kept choice. candidates[0] is the heuristic default, used alone when DG_AUTOTUNE=0 or while s is
+// being captured into a graph.
+int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates,
+             const std::function<void(int)>& run, cudaStream_t s);
 
 // Subdomain GMRES for linearized problems (columns of n_S values, E columns per basis vector).
 template <typename T>

@@ -7,6 +7,7 @@
 // N^4 work per element, one CTA per element (at most 512 threads), data staged in shared memory. The restriction
 // gathers its (up to 8) children in a fixed order: deterministic, no atomics.
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace dg {
 
@@ -49,6 +50,8 @@ __global__ void __launch_bounds__(XferShape<N>::threads) prolongate_kernel(XferG
   parent_of(cy, x.nf[1], x.nc[1], py, hy);
   parent_of(cz, x.nf[2], x.nc[2], pz, hz);
   const int ec = px + x.nc[0] * (py + x.nc[1] * pz);
+  pdl_launch_dependents();
+  pdl_wait();
   for (int t = tid; t < N3; t += NT) s0[t] = uc[(int64_t)ec * N3 + t];
   __syncthreads();
   for (int t = tid; t < N3; t += NT) {  // along x: s1[c][b][i] = sum_a Ix[i][a] uc[c][b][a]
@@ -90,6 +93,8 @@ __global__ void __launch_bounds__(XferShape<N>::threads) restrict_kernel(XferGeo
   for (int t = tid; t < N3; t += NT) sacc[t] = T(0);
   const int px = ec % x.nc[0], py = (ec / x.nc[0]) % x.nc[1], pz = ec / (x.nc[0] * x.nc[1]);
   const int rx = x.nf[0] == x.nc[0] ? 1 : 2, ry = x.nf[1] == x.nc[1] ? 1 : 2, rz = x.nf[2] == x.nc[2] ? 1 : 2;
+  pdl_launch_dependents();
+  pdl_wait();
   for (int dz = 0; dz < rz; ++dz)
     for (int dy = 0; dy < ry; ++dy)
       for (int dx = 0; dx < rx; ++dx) {
@@ -133,7 +138,8 @@ void launch_prolongate_add(int N, const int nf[3], const int nc[3], const T* Ilo
   XferGeom x{{nf[0], nf[1], nf[2]}, {nc[0], nc[1], nc[2]}};
   const int E = nf[0] * nf[1] * nf[2];
   switch (N) {
-#define DG_CASE(NN) case NN: prolongate_kernel<NN, T><<<E, XferShape<NN>::threads, 0, s>>>(x, Ilo, Ihi, uc, uf); break;
+#define DG_CASE(NN) \
+  case NN: launch_pdl(prolongate_kernel<NN, T>, dim3(E), dim3(XferShape<NN>::threads), 0, s, x, Ilo, Ihi, uc, uf); break;
     DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8) DG_CASE(9) DG_CASE(10)
 #undef DG_CASE
     default: fail(DG_ERR_INVALID_ARG, "unsupported N");
@@ -147,7 +153,8 @@ void launch_restrict(int N, const int nf[3], const int nc[3], const T* Ilo, cons
   XferGeom x{{nf[0], nf[1], nf[2]}, {nc[0], nc[1], nc[2]}};
   const int E = nc[0] * nc[1] * nc[2];
   switch (N) {
-#define DG_CASE(NN) case NN: restrict_kernel<NN, T><<<E, XferShape<NN>::threads, 0, s>>>(x, Ilo, Ihi, rf, bc); break;
+#define DG_CASE(NN) \
+  case NN: launch_pdl(restrict_kernel<NN, T>, dim3(E), dim3(XferShape<NN>::threads), 0, s, x, Ilo, Ihi, rf, bc); break;
     DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8) DG_CASE(9) DG_CASE(10)
 #undef DG_CASE
     default: fail(DG_ERR_INVALID_ARG, "unsupported N");

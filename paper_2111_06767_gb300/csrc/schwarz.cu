@@ -17,7 +17,12 @@
 // layers counted from the shared face, each layer in (a2, a1) order of the tangential indices.
 // Missing neighbours keep their slots as padding (identity rows and columns in A_S, zero data),
 // so every subdomain has n_S = N^3 + 6 N_ov N^2.
+#include <limits>
+#include <map>
+#include <mutex>
+
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace dg {
 
@@ -290,11 +295,13 @@ __device__ __forceinline__ int nbr_elem(const SubdomainGeom& g, int e, int f) {
 template <typename T>
 __global__ void gather_tab_kernel(SubdomainGeom g, const T* __restrict__ r, const int* __restrict__ elem_of_col,
                                   const int* __restrict__ orient, const int* __restrict__ map, T* __restrict__ rS) {
+  pdl_launch_dependents();
   __shared__ int nb[7];
   const int col = blockIdx.x;
   const int e = elem_of_col[col];
   if (threadIdx.x < 7) nb[threadIdx.x] = threadIdx.x == 0 ? e : nbr_elem(g, e, threadIdx.x - 1);
   __syncthreads();
+  pdl_wait();
   const int nS = g.nS, ld = g.ld, N3 = g.N * g.N * g.N;
   const int* m = map + (size_t)orient[e] * nS;
   T* out = rS + (size_t)col * ld;
@@ -313,6 +320,7 @@ template <typename T, typename TU>
 __global__ void scatter_tab_kernel(SubdomainGeom g, const T* __restrict__ duS, const int* __restrict__ col_of_elem,
                                    const int* __restrict__ orient, const int* __restrict__ inv,
                                    const T* __restrict__ shares, TU* __restrict__ u) {
+  pdl_launch_dependents();
   __shared__ int s_col[7], s_inv[7], s_pat;
   const int q = blockIdx.x;
   const int N3 = g.N * g.N * g.N, ld = g.ld;
@@ -338,6 +346,7 @@ __global__ void scatter_tab_kernel(SubdomainGeom g, const T* __restrict__ duS, c
   }
   __syncthreads();
   const T* sh0 = shares + (size_t)s_pat * N3 * 7;
+  pdl_wait();
   for (int p = threadIdx.x; p < N3; p += blockDim.x) {
     const T* sh = sh0 + (size_t)p * 7;
     T acc = sh[0] * duS[(int64_t)s_col[0] * ld + __ldg(inv + s_inv[0] + p)];
@@ -355,7 +364,7 @@ template <typename T>
 void launch_gather_tab(const SubdomainGeom& g, const T* r, const int* elem_of_col, const int* orient, const int* map,
                        T* rS, cudaStream_t s) {
   if (g.E == 0) return;
-  gather_tab_kernel<T><<<g.E, 256, 0, s>>>(g, r, elem_of_col, orient, map, rS);
+  launch_pdl(gather_tab_kernel<T>, dim3(g.E), dim3(256), 0, s, g, r, elem_of_col, orient, map, rS);
   DG_LAUNCHED(1);
 }
 
@@ -364,8 +373,8 @@ void launch_scatter_tab(const SubdomainGeom& g, const T* duS, const int* col_of_
                         const int* inv, const T* shares, TU* u, cudaStream_t s) {
   if (g.E == 0) return;
   const int N3 = g.N * g.N * g.N;
-  scatter_tab_kernel<T, TU><<<g.E, N3 > 512 ? 512 : (N3 < 32 ? 32 : N3), 0, s>>>(g, duS, col_of_elem, orient, inv,
-                                                                                 shares, u);
+  launch_pdl(scatter_tab_kernel<T, TU>, dim3(g.E), dim3(N3 > 512 ? 512 : (N3 < 32 ? 32 : N3)), 0, s, g, duS,
+             col_of_elem, orient, inv, shares, u);
   DG_LAUNCHED(1);
 }
 
@@ -394,6 +403,8 @@ __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ i
   const T* A = inv + (size_t)cls * nS * nS;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   T acc[4][4] = {};
+  pdl_launch_dependents();
+  pdl_wait();
   for (int k0 = 0; k0 < nS; k0 += BK) {
     for (int t = threadIdx.x; t < BM * BK; t += 256) {
       const int r = t / BK, kk = t % BK;
@@ -434,7 +445,7 @@ template <typename T>
 void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
                              cudaStream_t s) {
   if (n_tiles == 0) return;
-  class_gemm_kernel<T><<<n_tiles, 256, 0, s>>>(inv, X, Y, nS, d_tiles, alpha);
+  launch_pdl(class_gemm_kernel<T>, dim3(n_tiles), dim3(256), 0, s, inv, X, Y, nS, d_tiles, alpha);
   DG_LAUNCHED(1);
 }
 
@@ -484,8 +495,12 @@ __global__ void sub_arnoldi_kernel(int nS, int64_t stride, int j, int m, const T
   const size_t off = (size_t)col * nS;
   const T* vj = V + (size_t)j * stride + off;
   const T* zj = Z + (size_t)j * stride + off;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) w[i] = vj[i] + D[off + i] * zj[i];
-  __syncthreads();
+  T acc0 = 0;
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) {
+    w[i] = vj[i] + D[off + i] * zj[i];
+    acc0 += w[i] * w[i];
+  }
+  const T w0 = sqrt(block_sum(acc0, red));  // ||w|| before orthogonalisation
   T* h = H + (size_t)col * (m + 1) * m;
   for (int i = 0; i <= j; ++i) {
     const T* vi = V + (size_t)i * stride + off;
@@ -498,7 +513,10 @@ __global__ void sub_arnoldi_kernel(int nS, int64_t stride, int j, int m, const T
   }
   T acc = 0;
   for (int t = threadIdx.x; t < nS; t += blockDim.x) acc += w[t] * w[t];
-  const T hn = sqrt(block_sum(acc, red));
+  T hn = sqrt(block_sum(acc, red));
+  // what is left after orthogonalisation at the level of the cancellation error is rounding noise,
+  // not a new direction: treat it as a (happy) breakdown so that the least-squares step ignores it
+  if (hn <= T(64) * std::numeric_limits<T>::epsilon() * w0) hn = T(0);
   if (threadIdx.x == 0) h[(j + 1) * m + j] = hn;
   const T inv = hn > T(0) ? T(1) / hn : T(0);
   T* vn = V + (size_t)(j + 1) * stride + off;
@@ -559,10 +577,17 @@ void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream
 template <typename T>
 void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* Z, T* H, cudaStream_t s) {
   const size_t smem = nS * sizeof(T);
-  static size_t attr_set = 48 * 1024;  // largest dynamic shared memory already enabled
-  if (smem > attr_set) {
-    DG_CUDA(cudaFuncSetAttribute(sub_arnoldi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = smem;
+  if (smem > 48 * 1024) {
+    // the attribute is per device and may be raised by several serving threads at once
+    static std::mutex mu;
+    static std::map<int, size_t> attr_set;  // largest dynamic shared memory enabled per device
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > attr_set[dev]) {
+      DG_CUDA(cudaFuncSetAttribute(sub_arnoldi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_set[dev] = smem;
+    }
   }
   sub_arnoldi_kernel<T><<<E, 256, smem, s>>>(nS, (int64_t)E * nS, j, m, D, V, Z, H);
   DG_LAUNCHED(1);

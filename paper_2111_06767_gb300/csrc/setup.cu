@@ -313,6 +313,7 @@ void domain_setup(dg_domain* dom) {
   dom->err_flag.alloc(1);
   DG_CUDA(cudaMemsetAsync(dom->err_flag.get(), 0, sizeof(int), dom->stream));
   dom->lgl = make_lgl(d.N);
+  upload_operator_tables();
   cudaStream_t s = dom->stream;
   const LglTables& t = dom->lgl;
   const int N = d.N;

@@ -16,12 +16,32 @@ double apply_bytes(int64_t ndof, size_t sz, bool b, bool diag) { return (double)
 double apply_flops(int64_t ndof, int N) { return (double)ndof * (12.0 * N + 12.0); }
 }  // namespace
 
+namespace {
+// Launch shape of the DG apply for this level, precision and output: tuned on the first call (the
+// timed launches compute the same result into the same output, so the call stays correct).
+template <typename T>
+int apply_variant(dg_domain* dom, Level& L, bool fused, const std::function<void(int)>& run, cudaStream_t s) {
+  int& v = L.apply_variant[sizeof(T) == 4][fused];
+  if (v < 0) {
+    const int pick = autotune({1, dom->N, (int64_t)sizeof(T), L.n[0], L.n[1], L.n[2], fused}, {0, 1, 2, 3}, run, s);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DG_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return pick;  // not tuned while capturing: ask again later
+    v = pick;
+  }
+  return v;
+}
+}  // namespace
+
 void apply_level(dg_domain* dom, int level, const double* u, double* out, const double* b, bool with_lin,
                  cudaStream_t s, const SubdomainOut* so) {
   Level& L = dom->levels[level];
   const double* diag = (with_lin && level == 0 && dom->lin_set) ? dom->lin64.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP64, s, apply_bytes(L.ndof, 8, b, diag), apply_flops(L.ndof, dom->N));
-  launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s, so);
+  auto run = [&](int v) {
+    launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s, so, v);
+  };
+  run(apply_variant<double>(dom, L, so != nullptr, run, s));
 }
 
 void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, const float* b, bool with_lin,
@@ -29,7 +49,10 @@ void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, cons
   Level& L = dom->levels[level];
   const float* diag = (with_lin && level == 0 && dom->lin_set && dom->lin32.get()) ? dom->lin32.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP32, s, apply_bytes(L.ndof, 4, b, diag), apply_flops(L.ndof, dom->N));
-  launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s, so);
+  auto run = [&](int v) {
+    launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s, so, v);
+  };
+  run(apply_variant<float>(dom, L, so != nullptr, run, s));
 }
 
 namespace {
@@ -98,19 +121,35 @@ void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4*
 namespace {
 // du_S = A_S^-1 r_S for every subdomain of every class
 template <typename T>
-void class_gemm(dg_domain* dom, const Level& L, const T* X, T* Y, cudaStream_t s);
+void class_gemm(dg_domain* dom, Level& L, const T* X, T* Y, cudaStream_t s);
 template <>
-void class_gemm<double>(dg_domain* dom, const Level& L, const double* X, double* Y, cudaStream_t s) {
+void class_gemm<double>(dg_domain* dom, Level& L, const double* X, double* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
   launch_class_gemm_tiles<double>(sw.inv64.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, sw.inv_scale, s);
 }
 template <>
-void class_gemm<float>(dg_domain* dom, const Level& L, const float* X, float* Y, cudaStream_t s) {
+void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
-  if (dom->use_tc)
-    launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, sw.tiles_tc.get(), sw.n_tiles_tc,
-                         dom->err_flag.get(), (float)sw.inv_scale, s);
-  else
+  if (dom->use_tc) {
+    auto run = [&](int split) {
+      launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, sw.tiles_tc.get(), sw.n_tiles_tc,
+                           dom->err_flag.get(), (float)sw.inv_scale, s, split);
+    };
+    if (L.gemm_split < 0) {
+      // split-K factor: the default (0) first, then every split the shape allows
+      std::vector<int> cand{0};
+      for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(sp);
+      const int pick = autotune({2, sw.n_classes, sw.ld, sw.n_tiles_tc, L.E}, cand, run, s);
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      DG_CUDA(cudaStreamIsCapturing(s, &cap));
+      if (cap != cudaStreamCaptureStatusNone) {
+        run(pick);
+        return;
+      }
+      L.gemm_split = pick;
+    }
+    run(L.gemm_split);
+  } else
     launch_class_gemm_tiles<float>(sw.inv32.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, (float)sw.inv_scale, s);
 }
 }  // namespace

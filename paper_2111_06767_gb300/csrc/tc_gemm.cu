@@ -4,24 +4,26 @@
 // dense contraction of the method: Y[:, cols] = Inv_c (ld x ld, row-major) * X[:, cols] with every
 // subdomain column of X contiguous. Both operands are K-major, so each CTA computes a 128 x 64
 // output tile: TMA streams 128 x 32 tiles of Inv_c and 64 x 32 tiles of X (128-byte swizzle) into a
-// 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
+// 8-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
 // instruction) accumulating in tensor memory, and the four warps read the accumulator back with
 // tcgen05.ld and store it column-contiguously. When the tiles alone cannot fill the GPU, the K
-// range is split across a 4-CTA cluster and the partial tiles are summed through distributed
-// shared memory in a fixed order. Every wait is bounded: on timeout the CTA raises an error flag,
-// drains and frees its tensor memory.
+// range is split across a cluster of 2, 4 or 8 CTAs and the partial tiles are summed through
+// distributed shared memory in a fixed order. Every wait is bounded: on timeout the CTA raises an
+// error flag, drains and frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <set>
 
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace dg {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32, STAGES = 4;
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 8;
 constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
 constexpr int B_BYTES = BN * BK * 4;  // 8 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -29,6 +31,7 @@ constexpr int TMEM_COLS = 128;  // >= BN: the accumulator uses BN columns
 constexpr int SLACK = 8 * 1024;  // spare shared memory after the ring
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 256;
 constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls before a wait gives up (far above any real wait)
+constexpr int kSlots = 152;                 // co-resident CTAs: one per SM (the ring takes 192 KiB)
 
 // instruction descriptor: F32 accumulate, TF32 A and B, both K-major, N = BN, M = BM
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -125,17 +128,24 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ float ld_peer(uint32_t local_addr, uint32_t rank) {
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_peer(uint32_t local_addr, uint32_t rank) {
   uint32_t remote;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  return remote;
+}
+
+// Plain (reorderable) load from a peer's shared memory; callers order it after the writes with a
+// cluster barrier, which carries the memory clobber.
+__device__ __forceinline__ float ld_cluster(uint32_t addr) {
   float v;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+  asm("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
   return v;
 }
 
 // SPLIT > 1: the K range of a tile is split across the SPLIT CTAs of a thread-block cluster; each
 // keeps its partial 128 x 64 tile in shared memory and, after a cluster barrier, every CTA sums a
-// quarter (1/SPLIT) of the tile's columns over all partials through distributed shared memory in
+// 1/SPLIT of the tile's columns over all partials through distributed shared memory in
 // rank order, so the result does not depend on timing.
 template <int SPLIT>
 __global__ void __launch_bounds__(128, 1)
@@ -180,6 +190,9 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // set-up above overlaps the previous kernel; X (and Y) belong to the stream order from here on
+  pdl_launch_dependents();
+  pdl_wait();
 
   if (warp == 0 && lane == 0) {
     // producer: TMA loads into the ring
@@ -237,13 +250,28 @@ __global__ void __launch_bounds__(128, 1)
     }
     cluster_sync();
     constexpr int CPR = BN / SPLIT;  // columns reduced by this CTA
-    for (int j = 0; j < CPR; ++j) {
-      const int c = split * CPR + j;
-      const uint32_t a = smem_u32(part + c * BM + r_local);
-      float acc = 0.0f;
+    uint32_t peer[SPLIT];
+    const uint32_t mine = smem_u32(part + split * CPR * BM + r_local);
 #pragma unroll
-      for (int p = 0; p < SPLIT; ++p) acc += ld_peer(a, (uint32_t)p);
-      if (row < ld && c < ncol) Y[(size_t)(col0 + c) * ld + row] = alpha * acc;
+    for (int p = 0; p < SPLIT; ++p) peer[p] = map_peer(mine, (uint32_t)p);
+    // remote loads in groups of 32 issued back to back (they are independent), then each column is
+    // summed over the partials in rank order
+    constexpr int JG = 32 / SPLIT;  // columns per group
+#pragma unroll
+    for (int j0 = 0; j0 < CPR; j0 += JG) {
+      float v[JG][SPLIT];
+#pragma unroll
+      for (int j = 0; j < JG; ++j)
+#pragma unroll
+        for (int p = 0; p < SPLIT; ++p) v[j][p] = ld_cluster(peer[p] + (uint32_t)((j0 + j) * BM * 4));
+#pragma unroll
+      for (int j = 0; j < JG; ++j) {
+        const int c = split * CPR + j0 + j;
+        float acc = 0.0f;
+#pragma unroll
+        for (int p = 0; p < SPLIT; ++p) acc += v[j][p];
+        if (row < ld && c < ncol) Y[(size_t)(col0 + c) * ld + row] = alpha * acc;
+      }
     }
     cluster_sync();  // no CTA leaves while a peer still reads its partial tile
   }
@@ -290,8 +318,15 @@ CUtensorMap make_map(const float* base, int rank, const cuuint64_t* dims, const 
 
 bool tc_gemm_available() { return encode_fn() != nullptr; }
 
+std::vector<int> tc_gemm_splits(int ld) {
+  std::vector<int> out;
+  for (int split = 1; split <= 8; split *= 2)
+    if (split == 1 || (ld / BK) / split >= 4) out.push_back(split);
+  return out;
+}
+
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s) {
+                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split) {
   if (n_tiles == 0) return;
   DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
   const cuuint64_t dA[3] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)n_classes};
@@ -302,29 +337,50 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
   const cuuint32_t bB[2] = {BK, BN};
   const CUtensorMap mA = make_map(inv, 3, dA, sAr, bA);
   const CUtensorMap mB = make_map(X, 2, dB, sBr, bB);
-  static std::once_flag attr;
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
-  // split K over 4-CTA clusters when the tiles alone would leave most SMs idle
+  {
+    // kernel attributes are per device
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
+      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      done.insert(dev);
+    }
+  }
+  // Default: split K over a cluster of `split` CTAs so that the launch fills one wave of one CTA per
+  // SM, keeping >= 4 K chunks each.
   const int nk = ld / BK;
-  if (n_tiles * 2 <= 152 * 3 && nk >= 8) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_tiles * 4);
-    cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 4;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4>, mA, mB, Y, ld, d_tiles, err, alpha));
+  if (split == 0) {
+    split = 1;
+    while (split < 8 && n_tiles * split * 2 <= kSlots && nk / (split * 2) >= 4) split *= 2;
+  }
+  DG_REQUIRE(split == 1 || split == 2 || split == 4 || split == 8, "GEMM split must be 1, 2, 4 or 8");
+  DG_REQUIRE(split == 1 || nk / split >= 1, "GEMM split larger than the K chunks");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_tiles * split);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = split;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = split == 1 ? 1 : 2;
+  if (split == 1) {
+    DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1>, mA, mB, Y, ld, d_tiles, err, alpha));
   } else {
-    tc_gemm_kernel<1><<<n_tiles, 128, SMEM_BYTES, s>>>(mA, mB, Y, ld, d_tiles, err, alpha);
+    if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<2>, mA, mB, Y, ld, d_tiles, err, alpha));
+    else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4>, mA, mB, Y, ld, d_tiles, err, alpha));
+    else DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8>, mA, mB, Y, ld, d_tiles, err, alpha));
   }
   DG_LAUNCHED(1);
 }

@@ -1,0 +1,68 @@
+"""Parity at the full sizes of the benchmark workloads, in the configuration bench.py times.
+
+The oracle cannot run the full multigrid solves at these sizes within a test, so the GPU
+solutions are checked through properties that hold at any size: the oracle's own FP64 operator
+(Sec. II) applied to the GPU solution must leave a residual at the solver's tolerance, the mixed
+and FP64 solvers must agree with each other, and the Newton path must take the same steps."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import box, rel
+from oracle import dg, puncture
+
+pytestmark = pytest.mark.gpu
+
+dgg = pytest.importorskip("paper_2111_06767_gb300")
+
+
+def test_gaussian_8x8x8_N8_three_levels():
+    """16 Gaussians, 8^3 elements, N = 8, 3-level V-cycle, N_overlap = 2 (262,144 DOF)."""
+    n, N = (8, 8, 8), 8
+    grid = box(n, N)
+    x, y, z = grid.coordinates()
+    f = workloads.gaussian_source(2)(x, y, z)
+    graph = grid.graph()
+    b_ref = dg.rhs(graph, f).ravel()
+    sols = {}
+    for precision in ("fp64", "mixed"):
+        d = dgg.Domain(n=n, N=N, precision=precision, mg_levels=3, overlap=2)
+        b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-10)
+        assert rep.status == 0 and rep.relative_residual <= 1e-10
+        assert rel(b.cpu().numpy(), b_ref) < 1e-14
+        uh = u.cpu().numpy()
+        r = b_ref - dg.apply(graph, uh.reshape(-1, N, N, N)).ravel()
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b_ref)
+        sols[precision] = (uh, rep.iterations)
+    assert rel(sols["mixed"][0], sols["fp64"][0]) < 1e-9
+    assert abs(sols["mixed"][1] - sols["fp64"][1]) <= 1
+
+
+def test_puncture_16x16x16_N6_newton():
+    """Binary punctures on [-20,20]^3, 16^3 elements, N = 6 (884,736 DOF), Newton-Krylov with the
+    FP32 Schwarz smoother under FP64 FGMRES."""
+    n, N = (16, 16, 16), 6
+    grid = box(n, N, lower=(-20.0,) * 3, upper=(20.0,) * 3)
+    graph = grid.graph()
+    x, y, z = grid.coordinates()
+    alpha, beta = puncture.alpha_beta(x, y, z, workloads.BINARY_PUNCTURES)
+    mass = dg.mass_diag(graph)
+    sols = {}
+    for precision in ("fp64", "mixed"):
+        d = dgg.Domain((-20.0,) * 3, (20.0,) * 3, n, N, precision=precision, overlap=2, problem="puncture",
+                       punctures=workloads.BINARY_PUNCTURES)
+        u = torch.zeros(d.n_dof, dtype=torch.float64, device="cuda")
+        rep = d.solve(None, u, tol=1e-10, opts=dgg.solve_opts(linear_tol=1e-4))
+        assert rep.status == 0 and rep.relative_residual <= 1e-10
+        uh = u.cpu().numpy().reshape(-1, N, N, N)
+        r0 = -(mass * puncture.source(np.zeros_like(uh), alpha, beta))
+        r = -(dg.apply(graph, uh) + mass * puncture.source(uh, alpha, beta))
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(r0)
+        sols[precision] = (uh, rep)
+    (u64, r64), (u32, r32) = sols["fp64"], sols["mixed"]
+    assert r32.newton_steps == r64.newton_steps
+    assert r32.iterations <= 1.5 * r64.iterations + 3
+    assert rel(u32, u64) < 1e-9

@@ -78,3 +78,42 @@ def test_zero_rhs_returns_immediately():
     u = torch.zeros_like(b)
     rep = d.solve(b, u, tol=1e-10)
     assert rep.iterations == 0 and float(u.abs().max()) == 0.0
+
+
+def _poison_free_device_memory(gib=2.0):
+    """Fill a large block of device memory with NaN bit patterns and hand it back to the driver, so
+    that the library's next cudaMalloc calls are likely to receive pages holding NaNs."""
+    t = torch.full((int(gib * (1 << 30)) // 8,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    del t
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solves_do_not_read_uninitialised_memory(precision):
+    """Every mode and a second domain alive beside the first: the Krylov basis, subdomain vectors and
+    work buffers start as fresh allocations, so a kernel that multiplies an unset value by zero
+    (y = a x + 0 y) would turn NaN bits left in freed memory into a breakdown. Results must match a
+    run on a fresh domain bitwise."""
+    n, N = (4, 4, 4), 4
+    x, y, z = box(n, N).coordinates()
+    f = torch.from_numpy(workloads.gaussian_source(2)(x, y, z).ravel()).cuda()
+    ref = {}
+    for mode in (0, 1, 2):
+        d = dgg.Domain(n=n, N=N, precision=precision)
+        b = d.rhs(f)
+        u = torch.zeros_like(b)
+        d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(precondition=mode))
+        ref[mode] = u.clone()
+        del d
+    keep = dgg.Domain(n=n, N=N, precision=precision)  # stays alive, as a second tenant of the device
+    for mode in (0, 1, 2):
+        _poison_free_device_memory()
+        d = dgg.Domain(n=n, N=N, precision=precision)
+        b = d.rhs(f)
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(precondition=mode))
+        assert rep.status == 0 and rep.relative_residual <= 1e-10
+        assert torch.equal(u, ref[mode])
+        del d
+    del keep

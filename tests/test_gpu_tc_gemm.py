@@ -43,3 +43,39 @@ def test_tensor_core_solve_meets_tolerance():
         sols[prec] = (u.cpu().numpy(), rep.iterations)
     assert rel(sols["mixed"][0], sols["fp64"][0]) < 1e-9
     assert sols["mixed"][1] <= sols["fp64"][1] + 2
+
+
+_SOLVE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[2]); sys.path.insert(0, sys.argv[2] + "/tests")
+import workloads, paper_2111_06767_gb300 as dgg
+from gpu_util import box
+n, N = (6, 6, 6), 6
+x, y, z = box(n, N).coordinates()
+d = dgg.Domain(n=n, N=N, precision="mixed", mg_levels=2, overlap=2)
+b = d.rhs(torch.from_numpy(workloads.gaussian_source(2)(x, y, z).ravel()).cuda())
+u = torch.zeros_like(b)
+rep = d.solve(b, u, tol=1e-10)
+assert rep.relative_residual <= 1e-10
+np.save(sys.argv[1], u.cpu().numpy())
+"""
+
+
+def test_autotuned_launch_shapes_match_fixed_ones(tmp_path):
+    """The launch shapes of the DG apply and the split-K factor of the tensor-core GEMM are timed
+    and chosen per process; with DG_AUTOTUNE=0 the grid-size heuristics are used instead. Both
+    must reach the same solution (the split changes only the FP32 summation order)."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "solve.py"
+    script.write_text(_SOLVE_SCRIPT)
+    out = {}
+    for tune in ("1", "0"):
+        f = tmp_path / f"u{tune}.npy"
+        env = dict(os.environ, DG_AUTOTUNE=tune)
+        subprocess.run([sys.executable, str(script), str(f), root], env=env, check=True, timeout=600)
+        out[tune] = np.load(f)
+    assert rel(out["1"], out["0"]) < 1e-9
