@@ -4,7 +4,7 @@
 // dense contraction of the method: Y[:, cols] = Inv_c (ld x ld, row-major) * X[:, cols] with every
 // subdomain column of X contiguous. Both operands are K-major, so each CTA computes a 128 x 64
 // output tile: TMA streams 128 x 32 tiles of Inv_c and 64 x 32 tiles of X (128-byte swizzle) into a
-// 8-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
+// 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
 // instruction) accumulating in tensor memory, and the four warps read the accumulator back with
 // tcgen05.ld and store it column-contiguously. When the tiles alone cannot fill the GPU, the K
 // range is split across a cluster of 2, 4 or 8 CTAs and the partial tiles are summed through
@@ -23,7 +23,7 @@ namespace dg {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32, STAGES = 8;
+constexpr int BM = 128, BN = 64, BK = 32, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
 constexpr int B_BYTES = BN * BK * 4;  // 8 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -31,7 +31,7 @@ constexpr int TMEM_COLS = 128;  // >= BN: the accumulator uses BN columns
 constexpr int SLACK = 8 * 1024;  // spare shared memory after the ring
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 256;
 constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls before a wait gives up (far above any real wait)
-constexpr int kSlots = 152;                 // co-resident CTAs: one per SM (the ring takes 192 KiB)
+constexpr int kSlots = 2 * 152;             // co-resident CTAs: two per SM
 
 // instruction descriptor: F32 accumulate, TF32 A and B, both K-major, N = BN, M = BM
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -148,7 +148,7 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
 // 1/SPLIT of the tile's columns over all partials through distributed shared memory in
 // rank order, so the result does not depend on timing.
 template <int SPLIT>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    float* __restrict__ Y, int ld, const int4* __restrict__ tiles, int* __restrict__ err,
                    float alpha) {
@@ -352,8 +352,9 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
       done.insert(dev);
     }
   }
-  // Default: split K over a cluster of `split` CTAs so that the launch fills one wave of one CTA per
-  // SM, keeping >= 4 K chunks each.
+  // Default: split K over a cluster of `split` CTAs so that the launch fills one wave of two CTAs
+  // per SM (the ring and the partial tile fit twice in an SM's shared memory), keeping >= 4 K
+  // chunks each.
   const int nk = ld / BK;
   if (split == 0) {
     split = 1;
