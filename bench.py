@@ -172,13 +172,13 @@ def build_requests(dgg, workloads, items, precision="mixed"):
     return out
 
 
-def served_run(dgg, workloads, duration, rate=200.0, seed=5, max_active=4):
+def served_run(dgg, workloads, duration, rate=200.0, seed=5, max_active=4, precision="mixed"):
     """Poisson-process arrivals of Poisson / puncture requests (n ~ U{2..12} cubic, N ~ U{4..8}) into the
     continuous-batching server; latency = completion - scheduled arrival."""
     import time as _t
 
     arr = workloads.poisson_arrivals(seed, rate, duration)
-    reqs = build_requests(dgg, workloads, [(k, n, N, rs) for _, k, n, N, rs in arr])
+    reqs = build_requests(dgg, workloads, [(k, n, N, rs) for _, k, n, N, rs in arr], precision=precision)
     srv = dgg.Server(max_active=max_active, n_streams=max_active, queue_capacity=1 << 20)
     pending, done, i = {}, {}, 0
     start = srv.clock()
@@ -200,15 +200,29 @@ def served_run(dgg, workloads, duration, rate=200.0, seed=5, max_active=4):
     return {"requests": len(reqs), "arrival_rate_per_s": rate, "arrival_window_s": duration,
             "solves_per_s": len(reqs) / total, "p50_latency_ms": pick(0.5), "p99_latency_ms": pick(0.99),
             "ok": sum(1 for v in done.values() if v[0] == 0), "max_relative_residual": max(v[2] for v in done.values()),
-            "max_active": max_active, "precision": "mixed (TF32 subdomain GEMM, FP64 FGMRES)"}
+            "max_active": max_active,
+            "precision": "mixed (TF32 subdomain GEMM, FP64 FGMRES)" if precision == "mixed" else "fp64"}
 
 
-def batched_run(dgg, workloads, count=512, seed=4, max_active=8):
+def served_compare(dgg, workloads, duration, prefix):
+    """The served stream in MIXED precision, and the first `prefix` seconds of arrivals in both
+    precisions (the plain FP64 solver on the same requests, for the mixed/FP64 throughput ratio)."""
+    out = served_run(dgg, workloads, duration)
+    if prefix > 0:
+        m = served_run(dgg, workloads, prefix)
+        f = served_run(dgg, workloads, prefix, precision="fp64")
+        out["prefix"] = {"window_s": prefix, "mixed": m, "fp64": f,
+                         "mixed_over_fp64_solves_per_s": m["solves_per_s"] / f["solves_per_s"]}
+    return out
+
+
+def batched_run(dgg, workloads, count=512, seed=4, max_active=8, precision="mixed"):
     """`count` independent Poisson solves of uneven shapes (n_i ~ U{2..8}, N ~ U{4..9}), all submitted
     at once; domains are built inside the run (explicit inverses come from the library cache after
     the first of each shape)."""
     shapes = workloads.batched_shapes(seed, count)
-    reqs = build_requests(dgg, workloads, [("poisson", n, N, seed + k) for k, (n, N) in enumerate(shapes)])
+    reqs = build_requests(dgg, workloads, [("poisson", n, N, seed + k) for k, (n, N) in enumerate(shapes)],
+                          precision=precision)
     srv = dgg.Server(max_active=max_active, n_streams=max_active, queue_capacity=1 << 20)
     start = srv.clock()
     pending = {srv.submit(d, f, tol=1e-10): k for k, (d, f) in enumerate(reqs)}
@@ -222,8 +236,72 @@ def batched_run(dgg, workloads, count=512, seed=4, max_active=8):
                 worst = max(worst, res.report.relative_residual)
     total = srv.clock() - start
     srv.close()
-    return {"solves": count, "solves_per_s": count / total, "seconds": total, "ok": res_ok,
+    return {"solves": count, "precision": precision, "solves_per_s": count / total, "seconds": total, "ok": res_ok,
             "max_relative_residual": worst, "max_active": max_active}
+
+
+def batched_compare(dgg, workloads, count, fp64_count):
+    """The batched stream in MIXED precision, and its first `fp64_count` solves in both precisions
+    (plain FP64 on the GPU is ~50x slower, so it runs on a prefix of the same stream)."""
+    out = {"mixed": batched_run(dgg, workloads, count)}
+    if fp64_count > 0:
+        out["prefix_mixed"] = batched_run(dgg, workloads, fp64_count)
+        out["prefix_fp64"] = batched_run(dgg, workloads, fp64_count, precision="fp64")
+        out["prefix_mixed_over_fp64"] = out["prefix_mixed"]["solves_per_s"] / out["prefix_fp64"]["solves_per_s"]
+    return out
+
+
+def concurrent_run(dgg, workloads, torch, n_streams=8, rounds=4):
+    """The Gaussian solve of the headline workload on n_streams domains at once (one host thread
+    and one CUDA stream each, independent right-hand sides of the same problem): the throughput of
+    the GPU when independent solves share it, with the latency of each solve."""
+    import threading
+    import time as _t
+
+    src = workloads.gaussian_source(2)
+    doms, bs, us, streams = [], [], [], []
+    for _ in range(n_streams):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            d = dgg.Domain(n=n_CFG, N=N_CFG, penalty=1.5, precision="mixed", mg_levels=LEVELS, overlap=2, stream=s)
+            x, y, z = d.coordinates()
+            b = d.rhs(src(x, y, z).contiguous(), stream=s)
+            u = torch.zeros_like(b)
+        doms.append(d)
+        bs.append(b)
+        us.append(u)
+        streams.append(s)
+    torch.cuda.synchronize()
+    lat = [[] for _ in range(n_streams)]
+    worst = [0.0] * n_streams
+
+    def worker(i, n, record):
+        with torch.cuda.stream(streams[i]):
+            for _ in range(n):
+                us[i].zero_()
+                t = _t.perf_counter()
+                rep = doms[i].solve(bs[i], us[i], TOL)  # returns after the final FP64 residual check
+                if record:
+                    lat[i].append(_t.perf_counter() - t)
+                    worst[i] = max(worst[i], rep.relative_residual)
+
+    def run(n, record):
+        ths = [threading.Thread(target=worker, args=(i, n, record)) for i in range(n_streams)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+
+    run(2, False)  # graphs captured, launch shapes tuned
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    run(rounds, True)
+    total = _t.perf_counter() - t0
+    flat = sorted(x for l in lat for x in l)
+    pick = lambda q: 1e3 * flat[min(len(flat) - 1, int(math.ceil(q * len(flat))) - 1)]
+    return {"streams": n_streams, "solves": n_streams * rounds, "solves_per_s": n_streams * rounds / total,
+            "p50_latency_ms": pick(0.5), "p99_latency_ms": pick(0.99), "max_relative_residual": max(worst),
+            "timing": "host wall clock over all threads (each solve ends with a host read of its residual)"}
 
 
 def measured_peaks():
@@ -411,8 +489,11 @@ def run_ours(args):
                   "share": round(v["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-12), 4),
                   "GB/s": round(v["bytes"] / max(v["ms"], 1e-12) / 1e6, 1)} for k, v in prof.items()}
 
-    served = served_run(dgg, workloads, args.served_seconds) if args.served_seconds > 0 and rank == 0 else None
-    batched = batched_run(dgg, workloads, args.batched) if args.batched > 0 and rank == 0 else None
+    concurrent = concurrent_run(dgg, workloads, torch, args.concurrent) if args.concurrent > 0 and rank == 0 else None
+    served = (served_compare(dgg, workloads, args.served_seconds, args.served_fp64_seconds)
+              if args.served_seconds > 0 and rank == 0 else None)
+    batched = (batched_compare(dgg, workloads, args.batched, args.batched_fp64)
+               if args.batched > 0 and rank == 0 else None)
 
     lat = sorted(times)
     p50 = lat[len(lat) // 2]
@@ -438,6 +519,7 @@ def run_ours(args):
         "phases": phases,
         "served": served,
         "batched": batched,
+        "concurrent": concurrent,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -454,7 +536,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="arrival window of the served stream (0: skip)")
-    ap.add_argument("--batched", type=int, default=0, help="also run this many batched uneven solves (0: skip)")
+    ap.add_argument("--served-fp64-seconds", type=float, default=0.25,
+                    help="arrival window replayed in both precisions for the mixed/FP64 ratio (0: skip)")
+    ap.add_argument("--batched", type=int, default=512, help="also run this many batched uneven solves (0: skip)")
+    ap.add_argument("--concurrent", type=int, default=8,
+                    help="also solve the headline problem on this many streams at once (0: skip)")
+    ap.add_argument("--batched-fp64", type=int, default=32,
+                    help="prefix of the batched stream also solved in plain FP64 for the mixed/FP64 ratio")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

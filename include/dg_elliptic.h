@@ -224,7 +224,9 @@ enum dg_phase {
   DG_PHASE_SCATTER = 4,     /* u += sum_S R_S^T w_S du_S */
   DG_PHASE_TRANSFER = 5,    /* restriction and prolongation */
   DG_PHASE_KRYLOV = 6,      /* FGMRES vector kernels and precision conversions */
-  DG_PHASE_COUNT = 7
+  DG_PHASE_COARSE_SMOOTH = 7, /* fused Schwarz smoothing on a coarse level (residual, subdomain
+                                 solves and scatter of all steps in one launch) */
+  DG_PHASE_COUNT = 8
 };
 
 typedef struct dg_phase_stats {

@@ -48,7 +48,7 @@ class dg_solve_report(C.Structure):
                 ("final_residual", C.c_double), ("relative_residual", C.c_double), ("seconds", C.c_double)]
 
 
-PHASES = ("apply_fp64", "apply_fp32", "gather", "subdomain_gemm", "scatter", "transfer", "krylov")
+PHASES = ("apply_fp64", "apply_fp32", "gather", "subdomain_gemm", "scatter", "transfer", "krylov", "coarse_smooth")
 
 
 class dg_phase_stats(C.Structure):

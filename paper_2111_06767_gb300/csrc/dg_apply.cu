@@ -22,12 +22,14 @@
 // memory; the y- and z-contractions read whole lines from shared memory, which the threads of one
 // plane (y) or one column of planes (z) share as broadcasts, with the planes padded so that the
 // lines of one access fall into distinct banks.
+#include <algorithm>
 #include <mutex>
 #include <set>
 
 #include "internal.h"
 #include "lines.cuh"
 #include "pdl.cuh"
+#include "schwarz_dev.cuh"
 
 namespace dg {
 
@@ -96,12 +98,24 @@ __device__ __forceinline__ T face_point(T s, T ui, T gi, T ue, T ge, bool has, T
   return gi + s * jump * lift;
 }
 
-template <int N, typename T, int EPB>
-__global__ void __launch_bounds__(EPB* N* N)
-    apply_line_kernel(const OpGeom<T> g, const T* __restrict__ Dg, const T* __restrict__ wg, const T* __restrict__ u,
-                      const T* __restrict__ diag, const T* __restrict__ b, T* __restrict__ out, int E,
-                      T* __restrict__ rS, int ld, int ov, const int* __restrict__ col_of_elem,
-                      const int* __restrict__ orient, const int* __restrict__ inv) {
+// One group of EPB elements (block index blk) of the DG apply, for the kernel below and for the
+// fused coarse-level smoother; with PDL the set-up before the first read of u overlaps the
+// previous kernel on the stream.
+template <int N, typename T, int EPB, bool PDL, bool L2ONLY = false>
+__device__ __forceinline__ void apply_line_block(const ApplyArgs<T>& A, int blk) {
+  const OpGeom<T>& g = A.g;
+  const T* __restrict__ Dg = A.D;
+  const T* __restrict__ wg = A.w;
+  const T* __restrict__ u = A.u;
+  const T* __restrict__ diag = A.diag;
+  const T* __restrict__ b = A.b;
+  T* __restrict__ out = A.out;
+  const int E = A.E;
+  T* __restrict__ rS = A.rS;
+  const int ld = A.ld, ov = A.ov;
+  const int* __restrict__ col_of_elem = A.col_of_elem;
+  const int* __restrict__ orient = A.orient;
+  const int* __restrict__ inv = A.inv;
   using S = LineShape<N, T>;
   using C = CTab<T>;
   constexpr int N2 = N * N, N3 = N2 * N, P = S::P, R = S::R, NT = EPB * N2;
@@ -113,11 +127,11 @@ __global__ void __launch_bounds__(EPB* N* N)
   // residual written straight into the subdomain vectors: column and point-map offset of this
   // element's own subdomain (slot 0) and of each face neighbour's subdomain (slot 1 + (f ^ 1))
   __shared__ int s_col[EPB][7], s_map[EPB][7];
-  pdl_launch_dependents();
+  if constexpr (PDL) pdl_launch_dependents();
   const int tid = threadIdx.x;
   const int el = tid / N2, t = tid - el * N2;
   const int j = t % N, k = t / N;
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = blk * EPB;
   const int e = e0 + el;
   const bool valid = e < E;
   const int ec = valid ? e : E - 1;  // threads past the end load a real element and store nothing
@@ -154,18 +168,18 @@ __global__ void __launch_bounds__(EPB* N* N)
     Dk[l] = g.dxi[2] * __ldg(Dg + k * N + l);
   }
   const T wj = __ldg(wg + j), wk = __ldg(wg + k);
-  pdl_wait();
+  if constexpr (PDL) pdl_wait();
   // all loads of the thread's seven lines first (a missing neighbour reads the element itself and
   // is replaced by the ghost state), then the shared-memory stores
   const int64_t line = (int64_t)t * N;
   T ul[N], xm[N], xp[N], ym[N], yp[N], zm[N], zp[N];
-  gld_line<N>(u + (int64_t)ec * N3 + line, ul);
-  gld_line<N>(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + line, xm);
-  gld_line<N>(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + line, xp);
-  gld_line<N>(u + (int64_t)(hym ? ec - nx : ec) * N3 + line, ym);
-  gld_line<N>(u + (int64_t)(hyp ? ec + nx : ec) * N3 + line, yp);
-  gld_line<N>(u + (int64_t)(hzm ? ec - nxy : ec) * N3 + line, zm);
-  gld_line<N>(u + (int64_t)(hzp ? ec + nxy : ec) * N3 + line, zp);
+  gld_line<N, T, L2ONLY>(u + (int64_t)ec * N3 + line, ul);
+  gld_line<N, T, L2ONLY>(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + line, xm);
+  gld_line<N, T, L2ONLY>(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + line, xp);
+  gld_line<N, T, L2ONLY>(u + (int64_t)(hym ? ec - nx : ec) * N3 + line, ym);
+  gld_line<N, T, L2ONLY>(u + (int64_t)(hyp ? ec + nx : ec) * N3 + line, yp);
+  gld_line<N, T, L2ONLY>(u + (int64_t)(hzm ? ec - nxy : ec) * N3 + line, zm);
+  gld_line<N, T, L2ONLY>(u + (int64_t)(hzp ? ec + nxy : ec) * N3 + line, zp);
   const int so = k * P + j * N;  // this thread's line within a block
   sst_line<N>(&sm[0][el][so], ul);
   sst_line<N>(&sm[1][el][so], ym);
@@ -354,10 +368,16 @@ __global__ void __launch_bounds__(EPB* N* N)
 }
 
 template <int N, typename T, int EPB>
+__global__ void __launch_bounds__(EPB* N* N) apply_line_kernel(const ApplyArgs<T> A) {
+  apply_line_block<N, T, EPB, true>(A, blockIdx.x);
+}
+
+template <int N, typename T, int EPB>
 void launch_apply_epb(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
                       const SubdomainOut& so, int E, cudaStream_t s) {
-  launch_pdl(apply_line_kernel<N, T, EPB>, dim3((E + EPB - 1) / EPB), dim3(EPB * N * N), 0, s, g, D, w, u, diag, b,
-             out, E, static_cast<T*>(so.rS), so.ld, so.ov, so.col_of_elem, so.orient, so.inv);
+  const ApplyArgs<T> A{g, D, w, u, diag, b, out, E, static_cast<T*>(so.rS), so.ld, so.ov, so.col_of_elem, so.orient,
+                       so.inv};
+  launch_pdl(apply_line_kernel<N, T, EPB>, dim3((E + EPB - 1) / EPB), dim3(EPB * N * N), 0, s, A);
 }
 
 // Launch shapes: elements per CTA from the shared-memory/thread budget (S::epb), the fewest that
@@ -379,6 +399,163 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
   if (variant == 1) launch_apply_epb<N, T, kSmall>(g, D, w, u, diag, b, out, so, E, s);
   else if (variant == 2) launch_apply_epb<N, T, kMid>(g, D, w, u, diag, b, out, so, E, s);
   else launch_apply_epb<N, T, kBig>(g, D, w, u, diag, b, out, so, E, s);
+}
+
+// ------------------------------------------------------------------ fused coarse-level smoother
+//
+// On coarse levels (tens of elements) each of the three kernels of a Schwarz step is limited by its
+// own latency, not by work. This kernel runs all steps of one smoothing call in a single
+// cooperative launch: residual into r_S (or the gather of b when u = 0), the subdomain solves as a
+// CUDA-core GEMM over (class, 16-row) units, the weighted scatter into u, each phase separated by a
+// grid-wide barrier. Data written by other CTAs inside the kernel are read through L2 only.
+
+constexpr uint32_t kBarrierPolls = 1u << 22;  // polls before a barrier wait gives up
+
+// Grid-wide barrier over a cooperative launch (all CTAs co-resident). Returns false, with the error
+// flag set, if the wait gave up; the caller then leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned n_blocks, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == n_blocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint32_t polls = 0;
+      while (*gen == g) {
+        if (++polls > kBarrierPolls) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Rows row0 .. row0 + 15 of du_S for every column of one class: 128 threads = 16 rows x 8 K-groups
+// of 16; the class's columns are staged in shared memory 8 at a time in 128-wide K tiles; the 8
+// partial sums of each output are added in a fixed order.
+__device__ __forceinline__ void coarse_gemm_unit(const float* __restrict__ invm, int ld, const float* X, float* Y,
+                                                 int4 unit, float alpha) {
+  __shared__ __align__(16) float sx[8][136];  // 128 K values per column, one pad word per 16
+  __shared__ float red[8][16][9];
+  const int tid = threadIdx.x;
+  const int kg = tid & 7, r = tid >> 3;  // r < 16 for the first 128 threads
+  const int cls = unit.x, row0 = unit.y, col0 = unit.z, ncols = unit.w;
+  const float* arow = invm + ((size_t)cls * ld + row0 + r) * ld;
+  for (int c0 = 0; c0 < ncols; c0 += 8) {
+    const int nc = min(8, ncols - c0);
+    float acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+    for (int kt = 0; kt < ld; kt += 128) {
+      __syncthreads();  // sx and red of the previous round are consumed
+      for (int q = tid; q < 8 * 128; q += blockDim.x) {
+        const int c = q >> 7, kk = q & 127;
+        sx[c][kk + (kk >> 4)] = (c < nc && kt + kk < ld) ? __ldcg(X + (size_t)(col0 + c0 + c) * ld + kt + kk) : 0.0f;
+      }
+      __syncthreads();
+      const int kb = kt + kg * 16;
+      if (tid < 128 && kb < ld) {
+        float a[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(arow + kb) + q);
+          a[4 * q] = v.x;
+          a[4 * q + 1] = v.y;
+          a[4 * q + 2] = v.z;
+          a[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[c] += a[i] * sx[c][kg * 17 + i];
+      }
+    }
+    if (tid < 128) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) red[kg][r][c] = acc[c];
+    }
+    __syncthreads();
+    if (tid < 128) {
+      const int rr = tid >> 3, cc = tid & 7;
+      if (cc < nc) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) sum += red[g][rr][cc];
+        Y[(size_t)(col0 + c0 + cc) * ld + row0 + rr] = alpha * sum;
+      }
+    }
+  }
+}
+
+template <int N, int EPB>
+__global__ void __launch_bounds__(EPB* N* N) coarse_smooth_kernel(const CoarseArgs a) {
+  const unsigned G = gridDim.x;
+  const int E = a.ap.E;
+  const int nblk = (E + EPB - 1) / EPB;
+  for (int it = 0; it < a.iterations; ++it) {
+    if (it == 0 && a.u_zero) {
+      for (int col = blockIdx.x; col < E; col += G)
+        gather_column<float, false>(a.sg, a.ap.b, a.elem_of_col, a.ap.orient, a.map, a.ap.rS, col);
+    } else {
+      for (int blk = blockIdx.x; blk < nblk; blk += G) {
+        __syncthreads();  // the previous group is done with the shared blocks
+        apply_line_block<N, float, EPB, false, true>(a.ap, blk);
+      }
+    }
+    if (!grid_barrier(a.bar, G, a.err)) return;
+    for (int un = blockIdx.x; un < a.n_units; un += G)
+      coarse_gemm_unit(a.invm, a.sg.ld, a.ap.rS, a.duS, a.units[un], a.alpha);
+    if (!grid_barrier(a.bar, G, a.err)) return;
+    for (int e = blockIdx.x; e < E; e += G)
+      scatter_element<float, float, false, true>(a.sg, a.duS, a.ap.col_of_elem, a.ap.orient, a.ap.inv, a.shares,
+                                                 const_cast<float*>(a.ap.u), e);
+    if (it + 1 < a.iterations && !grid_barrier(a.bar, G, a.err)) return;
+  }
+}
+
+// threads per CTA: whole elements, at least the 128 the GEMM units use
+template <int N>
+struct CoarseShape {
+  static constexpr int epb = (128 + N * N - 1) / (N * N);
+  static constexpr int threads = epb * N * N;
+};
+
+template <int N>
+void launch_coarse_n(const CoarseArgs& a, cudaStream_t s) {
+  using CS = CoarseShape<N>;
+  static_assert(CS::threads >= 128, "GEMM units need 128 threads");
+  int dev = 0, sms = 0, per_sm = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_smooth_kernel<N, CS::epb>, CS::threads, 0));
+  DG_REQUIRE(per_sm >= 1, "fused coarse smoother does not fit on an SM");
+  const int E = a.ap.E;
+  const int work = std::max(std::max((E + CS::epb - 1) / CS::epb, E), a.n_units);
+  const int G = std::min(work, per_sm * sms);
+  DG_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(CS::threads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  DG_CUDA(cudaLaunchKernelEx(&cfg, coarse_smooth_kernel<N, CS::epb>, a));
 }
 
 }  // namespace
@@ -427,6 +604,24 @@ template void launch_apply<double>(int, const OpGeom<double>&, const double*, co
                                    const double*, const double*, double*, cudaStream_t, const SubdomainOut*, int);
 template void launch_apply<float>(int, const OpGeom<float>&, const float*, const float*, const float*, const float*,
                                   const float*, float*, cudaStream_t, const SubdomainOut*, int);
+
+// static shared memory of the fused kernel stays within 48 KiB up to N = 8
+bool coarse_smooth_available(int N) { return N >= 2 && N <= 8; }
+
+void launch_coarse_smooth(int N, const CoarseArgs& a, cudaStream_t s) {
+  DG_REQUIRE(a.sg.ld % 16 == 0, "fused coarse smoother needs a 16-aligned subdomain stride");
+  switch (N) {
+    case 2: launch_coarse_n<2>(a, s); break;
+    case 3: launch_coarse_n<3>(a, s); break;
+    case 4: launch_coarse_n<4>(a, s); break;
+    case 5: launch_coarse_n<5>(a, s); break;
+    case 6: launch_coarse_n<6>(a, s); break;
+    case 7: launch_coarse_n<7>(a, s); break;
+    case 8: launch_coarse_n<8>(a, s); break;
+    default: fail(DG_ERR_INVALID_ARG, "fused coarse smoother supports N <= 8");
+  }
+  DG_LAUNCHED(1);
+}
 
 
 // Diagonal of the LGL mass matrix, M = J w_i w_j w_k (Eq. massmat with collocation quadrature).

@@ -30,6 +30,9 @@ struct SchwarzLevel {
   int n_tiles = 0;
   DevBuf<int4> tiles_tc;           // tensor-core GEMM tiles: 128 rows x 64 columns
   int n_tiles_tc = 0;
+  DevBuf<int4> units;              // fused coarse smoother GEMM units: 16 rows x all columns of a class
+  int n_units = 0;
+  DevBuf<unsigned> bar;            // fused coarse smoother barrier state
 };
 
 template <typename T>
@@ -118,7 +121,8 @@ struct dg_domain {
   size_t bytes = 0;
   int subdomain_iterations = 3;
   dg::Profiler prof;
-  bool use_tc = false;            // subdomain GEMM on tcgen05 tensor cores (MIXED)
+  bool use_tc = false;
+  bool coarse_fused = false;  // fused cooperative smoother on coarse levels (DG_COARSE_FUSED=1 turns it on)            // subdomain GEMM on tcgen05 tensor cores (MIXED)
   dg::DevBuf<int> err_flag;       // set by device code whose bounded wait gave up
   // the V-cycle replayed as one CUDA graph (fixed input/output buffers; captured on the second use)
   bool graphs = true;

@@ -123,6 +123,24 @@ struct SubdomainOut {
   const int* inv = nullptr;      // [48][7][N^3] canonical row or -1
 };
 
+// Everything one DG apply reads and writes (rS != nullptr: write into the subdomain vectors).
+template <typename T>
+struct ApplyArgs {
+  OpGeom<T> g;
+  const T* D;
+  const T* w;
+  const T* u;
+  const T* diag;
+  const T* b;
+  T* out;
+  int E;
+  T* rS;
+  int ld, ov;
+  const int* col_of_elem;
+  const int* orient;
+  const int* inv;
+};
+
 // out = A u (+ diag * u)  or, with b != nullptr, out = b - (A u + diag * u). variant: launch shape
 // (0 chosen by grid size, 1..3 few / middle / many elements per CTA).
 template <typename T>
@@ -152,6 +170,28 @@ void launch_scatter_tab(const SubdomainGeom& g, const T* duS, const int* col_of_
                         const int* inv, const T* shares, TU* u, cudaStream_t s);
 template <typename S, typename T>
 void launch_pad_convert(const S* src, int n, int ld, int n_classes, T* dst, cudaStream_t s);
+
+// Fused coarse-level smoother (FP32): `iterations` Schwarz steps on one level in a single
+// cooperative launch, the phases (residual into r_S, subdomain solves, weighted scatter) separated
+// by grid-wide barriers.
+struct CoarseArgs {
+  ApplyArgs<float> ap;       // residual r = b - A u written into r_S (ap.rS)
+  SubdomainGeom sg;
+  const int* elem_of_col;    // gather of the first step when u = 0
+  const int* map;
+  const float* shares;       // scatter weights
+  float* duS;
+  const float* invm;         // class inverses [class][ld][ld] (unit width)
+  float alpha;               // 1 / h_x
+  const int4* units;         // (class, first of 16 rows, first column, columns) per GEMM work unit
+  int n_units;
+  unsigned* bar;             // barrier state (arrivals, generation), zeroed before the launch
+  int* err;                  // set if a barrier wait gave up
+  int iterations;
+  int u_zero;                // first step gathers b (u = 0)
+};
+bool coarse_smooth_available(int N);
+void launch_coarse_smooth(int N, const CoarseArgs& a, cudaStream_t s);
 
 // Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
 bool tc_gemm_available();

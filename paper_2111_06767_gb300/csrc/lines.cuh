@@ -37,12 +37,15 @@ struct LineVec {
   using V = typename VT<T, w>::type;
 };
 
-template <int N, typename T>
+// L2ONLY: load through L2 only (ld.global.cg), for data that other CTAs of the same kernel wrote
+// after a grid-wide barrier; otherwise the read-only path (data constant during the kernel).
+template <int N, typename T, bool L2ONLY = false>
 __device__ __forceinline__ void gld_line(const T* __restrict__ p, T (&v)[N]) {
   using L = LineVec<N, T>;
 #pragma unroll
   for (int q = 0; q < L::n; ++q) {
-    const typename L::V x = __ldg(reinterpret_cast<const typename L::V*>(p) + q);
+    const typename L::V* vp = reinterpret_cast<const typename L::V*>(p) + q;
+    const typename L::V x = L2ONLY ? __ldcg(vp) : __ldg(vp);
     const T* xs = reinterpret_cast<const T*>(&x);
 #pragma unroll
     for (int r = 0; r < L::per; ++r) v[q * L::per + r] = xs[r];

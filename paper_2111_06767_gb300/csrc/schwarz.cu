@@ -23,6 +23,7 @@
 
 #include "internal.h"
 #include "pdl.cuh"
+#include "schwarz_dev.cuh"
 
 namespace dg {
 
@@ -273,15 +274,6 @@ void launch_d2f_compact(const double* src, int64_t total, float* dst, cudaStream
 
 // ------------------------------------------------------------------ gather / scatter
 
-// Face neighbour of element e across face f (-1 at the domain boundary).
-__device__ __forceinline__ int nbr_elem(const SubdomainGeom& g, int e, int f) {
-  const int c0 = e % g.n[0], c1 = (e / g.n[0]) % g.n[1], c2 = e / (g.n[0] * g.n[1]);
-  int c[3] = {c0, c1, c2};
-  const int d = f >> 1;
-  c[d] += (f & 1) ? 1 : -1;
-  if (c[d] < 0 || c[d] >= g.n[d]) return -1;
-  return c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
-}
 
 // ------------------------------------------------------------------ table-driven gather / scatter
 //
@@ -296,24 +288,7 @@ template <typename T>
 __global__ void gather_tab_kernel(SubdomainGeom g, const T* __restrict__ r, const int* __restrict__ elem_of_col,
                                   const int* __restrict__ orient, const int* __restrict__ map, T* __restrict__ rS) {
   pdl_launch_dependents();
-  __shared__ int nb[7];
-  const int col = blockIdx.x;
-  const int e = elem_of_col[col];
-  if (threadIdx.x < 7) nb[threadIdx.x] = threadIdx.x == 0 ? e : nbr_elem(g, e, threadIdx.x - 1);
-  __syncthreads();
-  pdl_wait();
-  const int nS = g.nS, ld = g.ld, N3 = g.N * g.N * g.N;
-  const int* m = map + (size_t)orient[e] * nS;
-  T* out = rS + (size_t)col * ld;
-  for (int q = threadIdx.x; q < ld; q += blockDim.x) {
-    T v = 0;
-    if (q < nS) {
-      const int code = __ldg(m + q);
-      const int src = nb[code >> 16];
-      if (src >= 0) v = r[(int64_t)src * N3 + (code & 0xFFFF)];
-    }
-    out[q] = v;
-  }
+  gather_column<T, true>(g, r, elem_of_col, orient, map, rS, blockIdx.x);
 }
 
 template <typename T, typename TU>
@@ -321,43 +296,7 @@ __global__ void scatter_tab_kernel(SubdomainGeom g, const T* __restrict__ duS, c
                                    const int* __restrict__ orient, const int* __restrict__ inv,
                                    const T* __restrict__ shares, TU* __restrict__ u) {
   pdl_launch_dependents();
-  __shared__ int s_col[7], s_inv[7], s_pat;
-  const int q = blockIdx.x;
-  const int N3 = g.N * g.N * g.N, ld = g.ld;
-  if (threadIdx.x < 7) {
-    const int f = threadIdx.x - 1;
-    const int e = threadIdx.x == 0 ? q : nbr_elem(g, q, f);
-    if (e >= 0) {
-      s_col[threadIdx.x] = col_of_elem[e];
-      // own subdomain: slot 0 of q's orientation; neighbour e sees q across its actual face
-      // opposite to f, i.e. in slot 1 + (f ^ 1) of e's orientation
-      const int slot = threadIdx.x == 0 ? 0 : 1 + (f ^ 1);
-      s_inv[threadIdx.x] = (orient[e] * 7 + slot) * N3;
-    } else {
-      s_col[threadIdx.x] = -1;
-      s_inv[threadIdx.x] = 0;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int pat = 0;
-    for (int f = 0; f < 6; ++f) pat |= (s_col[1 + f] >= 0) << f;
-    s_pat = pat;
-  }
-  __syncthreads();
-  const T* sh0 = shares + (size_t)s_pat * N3 * 7;
-  pdl_wait();
-  for (int p = threadIdx.x; p < N3; p += blockDim.x) {
-    const T* sh = sh0 + (size_t)p * 7;
-    T acc = sh[0] * duS[(int64_t)s_col[0] * ld + __ldg(inv + s_inv[0] + p)];
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      if (s_col[1 + f] < 0) continue;
-      const int row = __ldg(inv + s_inv[1 + f] + p);
-      if (row >= 0) acc += sh[1 + f] * duS[(int64_t)s_col[1 + f] * ld + row];
-    }
-    u[(int64_t)q * N3 + p] += (TU)acc;
-  }
+  scatter_element<T, TU, true>(g, duS, col_of_elem, orient, inv, shares, u, blockIdx.x);
 }
 
 template <typename T>

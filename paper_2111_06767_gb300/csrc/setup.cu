@@ -19,6 +19,9 @@
 #include <mutex>
 #include <tuple>
 
+#include <cstdlib>
+#include <cstring>
+
 #include "domain.h"
 
 namespace dg {
@@ -198,6 +201,13 @@ void classify_schwarz(dg_domain* dom, Level& L) {
         tiles_tc.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles_tc = (int)tiles_tc.size();
   upload(sw.tiles_tc, tiles_tc, s);
+  std::vector<int4> units;
+  for (int c = 0; c < nc; ++c)
+    for (int r0 = 0; r0 < sw.ld; r0 += 16) units.push_back(make_int4(c, r0, sw.class_first[c], sw.class_count[c]));
+  sw.n_units = (int)units.size();
+  upload(sw.units, units, s);
+  sw.bar.alloc(2);
+  DG_CUDA(cudaMemsetAsync(sw.bar.get(), 0, sw.bar.bytes(), s));
 }
 
 // Point maps of the 48 subdomain orientations (orientation o = 8 perm + flips: canonical axis a is
@@ -306,6 +316,10 @@ void domain_setup(dg_domain* dom) {
   dom->N = d.N;
   dom->mixed = d.precision == DG_PRECISION_MIXED;
   dom->use_tc = dom->mixed && d.subdomain_gemm != DG_GEMM_SIMT;
+  {
+    const char* v = std::getenv("DG_COARSE_FUSED");
+    dom->coarse_fused = v && std::strcmp(v, "1") == 0;
+  }
   if (dom->use_tc && !tc_gemm_available()) {
     DG_REQUIRE(d.subdomain_gemm != DG_GEMM_TENSOR_TF32, "tensor-core GEMM requested but TMA encoding is unavailable");
     dom->use_tc = false;
@@ -493,7 +507,7 @@ size_t domain_device_bytes(const dg_domain* dom) {
   for (const auto& L : dom->levels) {
     const auto& sw = L.sw;
     b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.xform_of_elem.bytes() + sw.inv64.bytes() +
-         sw.inv32.bytes() + sw.tiles.bytes();
+         sw.inv32.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() + sw.units.bytes() + sw.bar.bytes();
     for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
                     &L.w64.gH})
       b += p->bytes();

@@ -4,6 +4,7 @@
 // (k+1) x k Hessenberg matrix and its Givens rotations, read back once per Krylov iteration.
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 
 #include "domain.h"
 
@@ -154,6 +155,9 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
 }
 }  // namespace
 
+// Levels with at most this many elements are smoothed by the fused cooperative kernel (MIXED).
+constexpr int kCoarseFusedElems = 64;
+
 template <typename T>
 void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations, bool u_is_zero, cudaStream_t s) {
   ensure_schwarz(dom, level);
@@ -162,6 +166,37 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
   SchwarzLevel& sw = L.sw;
   DG_REQUIRE(inverses<T>(sw) != nullptr && shares<T>(dom) != nullptr,
              "Schwarz data of this precision are not built for this domain");
+  if (iterations <= 0) return;
+  const bool linearized_level = level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE &&
+                                dom->subdomain_iterations > 0 && lin_diag<T>(dom) != nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    if (dom->coarse_fused && L.E <= kCoarseFusedElems && !linearized_level && coarse_smooth_available(dom->N)) {
+      // all steps of this call in one cooperative launch
+      CoarseArgs a{};
+      const float* diag = (level == 0 && dom->lin_set && dom->lin32.get()) ? dom->lin32.get() : nullptr;
+      a.ap = ApplyArgs<float>{L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, nullptr, L.E, W.rS.get(), sw.ld,
+                              dom->desc.overlap, sw.col_of_elem.get(), sw.xform_of_elem.get(), dom->orient_inv.get()};
+      a.sg = sw.geom;
+      a.elem_of_col = sw.elem_of_col.get();
+      a.map = dom->orient_map.get();
+      a.shares = dom->shares32.get();
+      a.duS = W.duS.get();
+      a.invm = sw.inv32.get();
+      a.alpha = (float)sw.inv_scale;
+      a.units = sw.units.get();
+      a.n_units = sw.n_units;
+      a.bar = sw.bar.get();
+      a.err = dom->err_flag.get();
+      a.iterations = iterations;
+      a.u_zero = u_is_zero ? 1 : 0;
+      const double vec = (double)L.E * sw.nS * 4.0, nS = sw.nS;
+      PhaseScope ps(dom->prof, DG_PHASE_COARSE_SMOOTH, s,
+                    iterations * ((double)sw.n_classes * nS * nS * 4.0 + 2 * vec + 4.0 * 4.0 * L.ndof),
+                    iterations * (2.0 * nS * nS * L.E + (12.0 * dom->N + 12.0) * L.ndof));
+      launch_coarse_smooth(dom->N, a, s);
+      return;
+    }
+  }
   SubdomainOut so;
   so.rS = W.rS.get();
   so.ld = sw.ld;

@@ -61,3 +61,27 @@ def test_vcycle_matches_oracle(n, N, levels):
             assert rel(out32, ref) < tol, gemm
     for _ in range(2):
         assert rel(d.vcycle(torch.from_numpy(r.ravel()).cuda()).cpu().numpy(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("n,N,levels", [((4, 4, 4), 6, 2), ((2, 2, 2), 8, 1), ((3, 4, 2), 5, 1)])
+def test_fused_coarse_smoother_matches_step_kernels(n, N, levels, monkeypatch):
+    """With DG_COARSE_FUSED=1, coarse levels (at most 64 elements) of a MIXED domain are smoothed by
+    one cooperative launch per smoothing call (residual, subdomain solves and scatter of every step,
+    separated by grid barriers). It must agree with the per-step kernels (the default) to FP32
+    rounding, for the V-cycle (first step a gather, u = 0), captured and replayed, and for
+    smoothing with u != 0."""
+    grid = box(n, N)
+    r = torch.from_numpy(rand(91, (grid.n_elements * N**3,))).cuda()
+    u0 = torch.from_numpy(rand(92, (grid.n_elements * N**3,))).cuda()
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("DG_COARSE_FUSED", fused)
+        d = dgg.Domain(n=n, N=N, mg_levels=levels, overlap=2, precision="mixed", gemm="simt")
+        vs = [d.vcycle(r).cpu().numpy() for _ in range(3)]  # uncaptured, captured, replayed
+        sm = d.schwarz_smooth(0, r, u0.clone(), 3).cpu().numpy() - u0.cpu().numpy()
+        out[fused] = (vs, sm)
+    (v1, s1), (v0, s0) = out["1"], out["0"]
+    assert np.array_equal(v1[1], v1[2])
+    for a, b in zip(v1, v0):
+        assert rel(a, b) < 1e-5
+    assert rel(s1, s0) < 1e-5
