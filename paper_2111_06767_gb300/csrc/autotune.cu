@@ -22,6 +22,17 @@ bool tuning_enabled() {
 }
 }  // namespace
 
+// Off by default: measured on the 8^3, N = 8 workload it slowed the FP64 solve from 339 to 630 ms
+// (dependent CTAs parked on the SMs during the long FP64 GEMMs) and the mixed one from 5.55 to
+// 5.78 ms. DG_PDL=1 turns it on.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("DG_PDL");
+    return v && std::strcmp(v, "1") == 0;
+  }();
+  return on;
+}
+
 int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates,
              const std::function<void(int)>& run, cudaStream_t s) {
   DG_REQUIRE(!candidates.empty(), "autotune needs candidates");

@@ -374,8 +374,9 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
   at[1].val.clusterDim.x = split;
   at[1].val.clusterDim.y = 1;
   at[1].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = split == 1 ? 1 : 2;
+  const bool pdl = pdl_enabled();
+  cfg.attrs = pdl ? at : at + 1;
+  cfg.numAttrs = (pdl ? 1 : 0) + (split == 1 ? 0 : 1);
   if (split == 1) {
     DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1>, mA, mB, Y, ld, d_tiles, err, alpha));
   } else {
