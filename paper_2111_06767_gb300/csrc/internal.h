@@ -148,13 +148,13 @@ void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u,
                   cudaStream_t s, const SubdomainOut* so = nullptr, int variant = 0);
 constexpr int kApplyVariants = 3;
 
-// Build explicit subdomain matrices A_S for a set of classes (FP64, column-major == row-major by symmetry).
-void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<double>& g, const double* D, const double* w,
-                                     const int* d_patch_info, int n_classes, int nS, double* A_out, cudaStream_t s);
+// Build explicit subdomain matrices A_S for a set of classes (column-major == row-major by symmetry).
+template <typename T>
+void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<T>& g, const T* D, const T* w,
+                                     const int* d_patch_info, int n_classes, int nS, T* A_out, cudaStream_t s);
 // In-place Gauss-Jordan inversion of n_classes SPD matrices of size n (no pivoting).
 template <typename T>
 void launch_invert_spd_batched(T* A, int n, int n_classes, cudaStream_t s);
-void launch_d2f_compact(const double* src, int64_t total, float* dst, cudaStream_t s);
 
 // Schwarz data movement. Subdomain columns are class-sorted; rows follow the subdomain point order.
 struct SubdomainGeom {

@@ -62,22 +62,22 @@ struct ColumnShape {
   static constexpr int threads = n3 > 512 ? 512 : n3;
 };
 
-template <int N>
+template <int N, typename T>
 __global__ void __launch_bounds__(ColumnShape<N>::threads) subdomain_column_kernel(
-    const OpGeom<double> g, const double* __restrict__ Dg, const double* __restrict__ wg,
-    const int* __restrict__ patch_info, int ov, int nS, double* __restrict__ A_out) {
+    const OpGeom<T> g, const T* __restrict__ Dg, const T* __restrict__ wg,
+    const int* __restrict__ patch_info, int ov, int nS, T* __restrict__ A_out) {
   constexpr int N2 = N * N, N3 = N * N * N, NT = ColumnShape<N>::threads;
-  __shared__ double sD[N2];
-  __shared__ double sw[N];
-  __shared__ double su[N3];
-  __shared__ double sv[3][N3];
-  __shared__ double sfb[6][N2];
+  __shared__ T sD[N2];
+  __shared__ T sw[N];
+  __shared__ T su[N3];
+  __shared__ T sv[3][N3];
+  __shared__ T sfb[6][N2];
   __shared__ int sinfo[kPatchInts];
 
   const int q = blockIdx.x;  // column
   const int cls = blockIdx.y;
   const int tid = threadIdx.x;
-  double* A = A_out + (size_t)cls * nS * nS + (size_t)q * nS;  // column q, contiguous
+  T* A = A_out + (size_t)cls * nS * nS + (size_t)q * nS;  // column q, contiguous
   for (int t = tid; t < N2; t += NT) sD[t] = Dg[t];
   for (int t = tid; t < N; t += NT) sw[t] = wg[t];
   for (int t = tid; t < kPatchInts; t += NT) sinfo[t] = patch_info[cls * kPatchInts + t];
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(ColumnShape<N>::threads) subdomain_column_kern
     __syncthreads();
     for (int p = tid; p < N3; p += NT) {
       const int i = p % N, j = (p / N) % N, k = p / N2;
-      double gx = 0, gy = 0, gz = 0;
+      T gx = 0, gy = 0, gz = 0;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
         gx += sD[i * N + l] * su[(k * N + j) * N + l];
@@ -126,16 +126,16 @@ __global__ void __launch_bounds__(ColumnShape<N>::threads) subdomain_column_kern
       const int f = item / N2, ab = item - f * N2;
       const int a1 = ab % N, a2 = ab / N;
       const int d = f >> 1, side = f & 1;
-      const double s = side ? 1.0 : -1.0;
-      const double dxi = d == 0 ? g.dxi[0] : (d == 1 ? g.dxi[1] : g.dxi[2]);
-      const double lift = d == 0 ? g.lift[0] : (d == 1 ? g.lift[1] : g.lift[2]);
-      const double sigma = d == 0 ? g.sigma[0] : (d == 1 ? g.sigma[1] : g.sigma[2]);
-      const double Jf = d == 0 ? g.Jf[0] : (d == 1 ? g.Jf[1] : g.Jf[2]);
+      const T s = side ? 1.0 : -1.0;
+      const T dxi = d == 0 ? g.dxi[0] : (d == 1 ? g.dxi[1] : g.dxi[2]);
+      const T lift = d == 0 ? g.lift[0] : (d == 1 ? g.lift[1] : g.lift[2]);
+      const T sigma = d == 0 ? g.sigma[0] : (d == 1 ? g.sigma[1] : g.sigma[2]);
+      const T Jf = d == 0 ? g.Jf[0] : (d == 1 ? g.Jf[1] : g.Jf[2]);
       const int pf = node_of<N>(d, side ? N - 1 : 0, a1, a2);
-      const double u_int = su[pf];
-      const double g_int = sv[d][pf];
+      const T u_int = su[pf];
+      const T g_int = sv[d][pf];
       const int t = sinfo[X * 6 + f];
-      double u_ext, g_ext;
+      T u_ext, g_ext;
       if (t == -1) {
         u_ext = -u_int;
         g_ext = g_int;
@@ -146,30 +146,30 @@ __global__ void __launch_bounds__(ColumnShape<N>::threads) subdomain_column_kern
         // neighbour data is the unit vector restricted to slot t
         const int opp = side ? 0 : N - 1;
         u_ext = (t == P && node_of<N>(d, opp, a1, a2) == pP) ? 1.0 : 0.0;
-        double acc = 0.0;
+        T acc = 0.0;
         if (t == P) {
           for (int l = 0; l < N; ++l)
             if (node_of<N>(d, l, a1, a2) == pP) acc += sD[opp * N + l];
         }
         g_ext = dxi * acc;
       }
-      const double jump = u_ext - u_int;
+      const T jump = u_ext - u_int;
       sv[d][pf] = g_int + s * jump * lift;
-      const double Bf = Jf * sw[a1] * sw[a2];
+      const T Bf = Jf * sw[a1] * sw[a2];
       sfb[f][ab] = Bf * (0.5 * s * (g_ext - g_int) + (sigma - lift) * jump);
     }
     __syncthreads();
     for (int p = tid; p < N3; p += NT) {
       const int i = p % N, j = (p / N) % N, k = p / N2;
-      double dx = 0, dy = 0, dz = 0;
+      T dx = 0, dy = 0, dz = 0;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
         dx += sD[i * N + l] * sv[0][(k * N + j) * N + l];
         dy += sD[j * N + l] * sv[1][(k * N + l) * N + i];
         dz += sD[k * N + l] * sv[2][(l * N + j) * N + i];
       }
-      const double M = g.J * sw[i] * sw[j] * sw[k];
-      double res = -M * (g.dxi[0] * dx + g.dxi[1] * dy + g.dxi[2] * dz);
+      const T M = g.J * sw[i] * sw[j] * sw[k];
+      T res = -M * (g.dxi[0] * dx + g.dxi[1] * dy + g.dxi[2] * dz);
       if (i == 0) res -= sfb[0][k * N + j];
       if (i == N - 1) res -= sfb[1][k * N + j];
       if (j == 0) res -= sfb[2][k * N + i];
@@ -183,18 +183,23 @@ __global__ void __launch_bounds__(ColumnShape<N>::threads) subdomain_column_kern
   }
 }
 
-void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<double>& g, const double* D, const double* w,
-                                     const int* d_patch_info, int n_classes, int nS, double* A_out, cudaStream_t s) {
+template <typename T>
+void launch_build_subdomain_matrices(int N, int overlap, const OpGeom<T>& g, const T* D, const T* w,
+                                     const int* d_patch_info, int n_classes, int nS, T* A_out, cudaStream_t s) {
   dim3 grid(nS, n_classes);
   switch (N) {
 #define DG_CASE(NN) \
-  case NN: subdomain_column_kernel<NN><<<grid, ColumnShape<NN>::threads, 0, s>>>(g, D, w, d_patch_info, overlap, nS, A_out); break;
+  case NN: subdomain_column_kernel<NN, T><<<grid, ColumnShape<NN>::threads, 0, s>>>(g, D, w, d_patch_info, overlap, nS, A_out); break;
     DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8) DG_CASE(9) DG_CASE(10)
 #undef DG_CASE
     default: fail(DG_ERR_INVALID_ARG, "unsupported N");
   }
   DG_LAUNCHED(1);
 }
+template void launch_build_subdomain_matrices<double>(int, int, const OpGeom<double>&, const double*, const double*,
+                                                      const int*, int, int, double*, cudaStream_t);
+template void launch_build_subdomain_matrices<float>(int, int, const OpGeom<float>&, const float*, const float*,
+                                                     const int*, int, int, float*, cudaStream_t);
 
 // ------------------------------------------------------------------ Gauss-Jordan inversion
 
@@ -363,13 +368,8 @@ void launch_invert_spd_batched(T* A, int n, int n_classes, cudaStream_t s) {
 template void launch_invert_spd_batched<double>(double*, int, int, cudaStream_t);
 template void launch_invert_spd_batched<float>(float*, int, int, cudaStream_t);
 
-__global__ void d2f_compact_kernel(const double* __restrict__ src, int64_t total, float* __restrict__ dst) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-    dst[t] = (float)src[t];
-}
-
-// Copy compact [n_classes][n][n] FP64 inverses into [n_classes][ld][ld] storage of type T with
-// zero padding (ld = n rounded up to 32 so rows are 128-byte aligned for TMA and vector loads).
+// Copy compact [n_classes][n][n] inverses into [n_classes][ld][ld] storage of type T with zero
+// padding (ld = n rounded up to 32 so rows are 128-byte aligned for TMA and vector loads).
 template <typename S, typename T>
 __global__ void pad_convert_kernel(const S* __restrict__ src, int n, int ld, int64_t total, T* __restrict__ dst) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -392,11 +392,6 @@ template void launch_pad_convert<double, double>(const double*, int, int, int, d
 template void launch_pad_convert<double, float>(const double*, int, int, int, float*, cudaStream_t);
 template void launch_pad_convert<float, float>(const float*, int, int, int, float*, cudaStream_t);
 
-void launch_d2f_compact(const double* src, int64_t total, float* dst, cudaStream_t s) {
-  if (total == 0) return;
-  d2f_compact_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, s>>>(src, total, dst);
-  DG_LAUNCHED(1);
-}
 
 // ------------------------------------------------------------------ gather / scatter
 

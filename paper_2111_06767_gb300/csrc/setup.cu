@@ -447,18 +447,21 @@ void ensure_schwarz(dg_domain* dom, int level) {
     DevBuf<int> d_patch;
     upload(d_patch, patch, s);
     const double hu[3] = {1.0, L.h[1] / hx, L.h[2] / hx};
-    const OpGeom<double> gu = make_geom<double>(L.n, hu, N, dom->desc.penalty, dom->lgl);
-    DevBuf<double> compact((size_t)nm * nS * nS);
-    launch_build_subdomain_matrices(N, ov, gu, dom->D64.get(), dom->w64.get(), d_patch.get(), nm, nS, compact.get(), s);
     DevBuf<char> built((size_t)nm * mat);
     if (dom->mixed) {
-      // stored in FP32 for an FP32/TF32 smoother: invert in FP32 (A_S is well conditioned)
+      // stored in FP32 for an FP32/TF32 smoother: built and inverted in FP32 (A_S is well
+      // conditioned; GB300's FP32 rate is ~60x its FP64 rate)
+      const OpGeom<float> gu = make_geom<float>(L.n, hu, N, dom->desc.penalty, dom->lgl);
       DevBuf<float> c32((size_t)nm * nS * nS);
-      launch_d2f_compact(compact.get(), (int64_t)nm * nS * nS, c32.get(), s);
-      compact.release();
+      launch_build_subdomain_matrices<float>(N, ov, gu, dom->D32.get(), dom->w32.get(), d_patch.get(), nm, nS,
+                                             c32.get(), s);
       launch_invert_spd_batched<float>(c32.get(), nS, nm, s);
       launch_pad_convert<float, float>(c32.get(), nS, ld, nm, (float*)built.get(), s);
     } else {
+      const OpGeom<double> gu = make_geom<double>(L.n, hu, N, dom->desc.penalty, dom->lgl);
+      DevBuf<double> compact((size_t)nm * nS * nS);
+      launch_build_subdomain_matrices<double>(N, ov, gu, dom->D64.get(), dom->w64.get(), d_patch.get(), nm, nS,
+                                              compact.get(), s);
       launch_invert_spd_batched<double>(compact.get(), nS, nm, s);
       launch_pad_convert<double, double>(compact.get(), nS, ld, nm, (double*)built.get(), s);
     }
