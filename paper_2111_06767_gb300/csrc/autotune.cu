@@ -1,12 +1,15 @@
-// Launch-shape autotuning (element-batch and tile schedules): the first time a kernel shape is
-// seen in the process, every candidate launch configuration is timed with CUDA events on the
-// caller's stream (one warm-up launch, then three timed ones) and the fastest is kept for the rest
-// of the process. The paper has no counterpart; it replaces hand-picked launch heuristics.
+// Process-wide runtime settings of the library: launch-shape autotuning (element-batch and tile
+// schedules: the first time a kernel shape is seen in the process, every candidate launch
+// configuration is timed with CUDA events on the caller's stream, one warm-up launch and three
+// timed ones, and the fastest is kept; it replaces hand-picked launch heuristics and has no
+// counterpart in the paper), the stream of this thread's allocations, and the switch for
+// programmatic dependent launch.
 #include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <map>
 #include <mutex>
+#include <set>
 
 #include "internal.h"
 
@@ -16,11 +19,33 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::vector<int64_t>, int> g_tuned;
 
+thread_local cudaStream_t tl_alloc_stream = nullptr;
+
 bool tuning_enabled() {
   const char* v = std::getenv("DG_AUTOTUNE");
   return !(v && std::strcmp(v, "0") == 0);
 }
 }  // namespace
+
+cudaStream_t alloc_stream() { return tl_alloc_stream; }
+
+void keep_pool_memory() {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(dev)) return;
+  // memory released to the device's default pool stays there for the next domain instead of
+  // being returned at every synchronisation (this process's pool only)
+  cudaMemPool_t pool;
+  DG_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t keep = UINT64_MAX;
+  DG_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  done.insert(dev);
+}
+AllocStreamScope::AllocStreamScope(cudaStream_t s) : prev(tl_alloc_stream) { tl_alloc_stream = s; }
+AllocStreamScope::~AllocStreamScope() { tl_alloc_stream = prev; }
 
 // Off by default: measured on the 8^3, N = 8 workload it slowed the FP64 solve from 339 to 630 ms
 // (dependent CTAs parked on the SMs during the long FP64 GEMMs) and the mixed one from 5.55 to

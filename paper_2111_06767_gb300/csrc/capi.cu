@@ -35,6 +35,7 @@ thread_local std::string g_create_error;
 template <typename F>
 dg_status guarded(dg_domain* dom, F&& f) {
   try {
+    dg::AllocStreamScope scope(dom ? dom->stream : nullptr);
     f();
     if (dom) dom->err.clear();
     return DG_OK;
@@ -70,9 +71,9 @@ dg_status dg_domain_create(const dg_domain_desc* desc, void* cuda_stream, dg_dom
     return DG_ERR_OOM;
   }
   dom->desc = *desc;
+  // NULL selects the legacy default stream (the one torch and most callers use by default)
+  dom->stream = (cudaStream_t)cuda_stream;
   dg_status st = guarded(dom, [&] {
-    // NULL selects the legacy default stream (the one torch and most callers use by default)
-    dom->stream = (cudaStream_t)cuda_stream;
     dg::domain_setup(dom);
     dom->bytes = dg::domain_device_bytes(dom);
   });
@@ -87,7 +88,10 @@ dg_status dg_domain_create(const dg_domain_desc* desc, void* cuda_stream, dg_dom
 
 void dg_domain_destroy(dg_domain* dom) {
   if (!dom) return;
-  if (dom->stream) cudaStreamSynchronize(dom->stream);
+  // buffers are released in the order of the domain's stream, after its work and that of its
+  // private graph stream
+  if (dom->gstream) cudaStreamSynchronize(dom->gstream);
+  cudaStreamSynchronize(dom->stream);
   cudaStream_t s = dom->own_stream ? dom->stream : nullptr;
   delete dom;
   if (s) cudaStreamDestroy(s);

@@ -41,24 +41,41 @@ int64_t launches_total();
 
 // ------------------------------------------------------------------ device memory
 
-// Owning device buffer (cudaMalloc/cudaFree), move-only.
+// Stream on which this thread's library allocations are made: the domain's stream while an entry
+// point runs (set by AllocStreamScope), else the legacy default stream. Allocation and release are
+// stream-ordered (cudaMallocAsync / cudaFreeAsync), so one domain's set-up or teardown does not
+// wait for the work of domains on other streams, as cudaMalloc / cudaFree would.
+cudaStream_t alloc_stream();
+struct AllocStreamScope {
+  cudaStream_t prev;
+  explicit AllocStreamScope(cudaStream_t s);
+  ~AllocStreamScope();
+};
+// Keep freed memory in this process's default pool of the current device (once per device).
+void keep_pool_memory();
+
+// Owning device buffer, move-only. alloc() returns once the memory is usable from any stream
+// (it synchronises the allocation stream); release() is ordered after that stream's work, and
+// the owner makes sure other streams are done with the buffer before (the domain joins its
+// private stream into its main stream after every use).
 template <typename T>
 struct DevBuf {
   T* ptr = nullptr;
   size_t count = 0;
+  cudaStream_t st = nullptr;
   DevBuf() = default;
   explicit DevBuf(size_t n) { alloc(n); }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), count(o.count) { o.ptr = nullptr; o.count = 0; }
+  DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), count(o.count), st(o.st) { o.ptr = nullptr; o.count = 0; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); ptr = o.ptr; count = o.count; o.ptr = nullptr; o.count = 0; }
+    if (this != &o) { release(); ptr = o.ptr; count = o.count; st = o.st; o.ptr = nullptr; o.count = 0; }
     return *this;
   }
   ~DevBuf() { release(); }
   void alloc(size_t n);
   void release() {
-    if (ptr) cudaFree(ptr);
+    if (ptr) cudaFreeAsync(ptr, st);
     ptr = nullptr;
     count = 0;
   }
@@ -70,11 +87,14 @@ template <typename T>
 void DevBuf<T>::alloc(size_t n) {
   release();
   if (n == 0) return;
-  cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
+  st = alloc_stream();
+  cudaError_t e = cudaMallocAsync(&ptr, n * sizeof(T), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
+    if (ptr) cudaFreeAsync(ptr, st);
     ptr = nullptr;
     (void)cudaGetLastError();
-    fail(DG_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
+    fail(DG_ERR_OOM, "allocation of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
   }
   count = n;
 }

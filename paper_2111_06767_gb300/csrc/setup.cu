@@ -328,6 +328,7 @@ void domain_setup(dg_domain* dom) {
   DG_CUDA(cudaMemsetAsync(dom->err_flag.get(), 0, sizeof(int), dom->stream));
   dom->lgl = make_lgl(d.N);
   upload_operator_tables();
+  keep_pool_memory();
   cudaStream_t s = dom->stream;
   const LglTables& t = dom->lgl;
   const int N = d.N;
@@ -475,7 +476,7 @@ void ensure_schwarz(dg_domain* dom, int level) {
         g_inv_bytes += mat;
       }
       void* keep = nullptr;
-      if (cudaMalloc(&keep, mat) != cudaSuccess) {
+      if (cudaMallocAsync(&keep, mat, s) != cudaSuccess) {
         (void)cudaGetLastError();
         std::lock_guard<std::mutex> lk(g_inv_mu);
         g_inv_bytes -= mat;
@@ -485,7 +486,7 @@ void ensure_schwarz(dg_domain* dom, int level) {
       DG_CUDA(cudaStreamSynchronize(s));
       std::lock_guard<std::mutex> lk(g_inv_mu);
       if (!g_inv->emplace(keys[missing[i]], keep).second) {
-        cudaFree(keep);
+        cudaFreeAsync(keep, s);
         g_inv_bytes -= mat;
       }
     }
