@@ -59,3 +59,47 @@ def fgmres(op, b, x0=None, precond=None, tol=1e-10, max_iter=200, rel_to="r0", c
     info["converged"] = info["true_residual"] <= tol * ref * (1 + 1e-6) or history[-1] <= tol * ref
     info["r0"] = beta
     return x.reshape(shape), info
+
+
+def fcg(op, b, x0=None, precond=None, tol=1e-10, max_iter=400, rel_to="r0", keep_directions=False):
+    """Flexible conjugate gradients for symmetric positive definite op (the alternative to FGMRES
+    for the SPD Poisson problem that Sec. III.B names: one search direction instead of a growing
+    basis). Each new direction is the preconditioned residual made A-orthogonal to the previous
+    direction (the flexible variant with one stored direction, so a preconditioner that is not
+    exactly symmetric or changes between iterations is tolerated):
+        z = M r,  p = z - (z.q_old / p_old.q_old) p_old,  q = A p,
+        alpha = (p.r) / (p.q),  x += alpha p,  r -= alpha q.
+    Stops when ||r|| <= tol * ||b - A x0|| (rel_to="r0") or tol * ||b||; the true residual is
+    recomputed at exit. With the identity preconditioner this is the conjugate gradient method."""
+    shape = b.shape
+    bf = b.ravel()
+    x = np.zeros_like(bf) if x0 is None else np.asarray(x0, dtype=np.float64).ravel().copy()
+    A = lambda v: op(v.reshape(shape)).ravel()
+    M = (lambda v: v) if precond is None else (lambda v: precond(v.reshape(shape)).ravel())
+    r = bf - A(x)
+    r0 = np.linalg.norm(r)
+    ref = r0 if rel_to == "r0" else np.linalg.norm(bf)
+    history = [r0]
+    info = {"iterations": 0, "history": history, "r0": r0, "directions": []}  # (p, A p) if kept
+    p = q = None
+    res = r0
+    for k in range(max_iter):
+        if res <= tol * ref or res == 0.0:
+            break
+        z = M(r)
+        if p is None:
+            p = z.copy()
+        else:
+            p = z - (z @ q) / (p @ q) * p
+        q = A(p)
+        alpha = (p @ r) / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        res = np.linalg.norm(r)
+        history.append(res)
+        info["iterations"] = k + 1
+        if keep_directions:
+            info["directions"].append((p, q))
+    info["true_residual"] = np.linalg.norm(bf - A(x))
+    info["converged"] = info["true_residual"] <= tol * ref * (1 + 1e-6)
+    return x.reshape(shape), info

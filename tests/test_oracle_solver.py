@@ -149,6 +149,49 @@ def test_fgmres_matches_direct_solve_and_basis_is_orthonormal():
         assert info8["orthonormality"] < 1e-9
 
 
+def test_fcg_without_preconditioner_is_conjugate_gradients():
+    """With M = I the flexible CG reduces to the textbook conjugate gradient method: the same
+    iterates as scipy's CG, mutually A-orthogonal search directions, and the dense direct solution
+    within n iterations."""
+    from scipy.sparse.linalg import cg
+
+    grid = _box((2, 1, 2), 3)
+    gr = grid.graph()
+    A = dg.assemble(gr)
+    n = A.shape[0]
+    b = workloads.uniform_vector(21, n, -1.0, 1.0)
+    op = lambda u: dg.apply(gr, u.reshape(-1, 3, 3, 3)).ravel()
+    steps = []
+    cg(A, b, rtol=1e-30, maxiter=8, callback=lambda xk: steps.append(xk.copy()))
+    for k, xk in enumerate(steps, start=1):
+        xf, _ = krylov.fcg(op, b, tol=1e-30, max_iter=k)
+        assert np.linalg.norm(xf - xk) <= 1e-9 * np.linalg.norm(xk)
+    x, info = krylov.fcg(op, b, tol=1e-12, max_iter=n + 5, keep_directions=True)
+    assert info["converged"] and info["iterations"] <= n
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(x)
+    P = [d[0] for d in info["directions"][:6]]
+    for i in range(len(P)):
+        for j in range(i):
+            c = P[i] @ A @ P[j] / math.sqrt((P[i] @ A @ P[i]) * (P[j] @ A @ P[j]))
+            assert abs(c) < 1e-8
+
+
+def test_fcg_with_multigrid_schwarz_matches_direct_solve():
+    """The flexible CG preconditioned by the multigrid-Schwarz V-cycle (not exactly symmetric: the
+    Schwarz weights act on one side only) reaches the direct solution, in a number of iterations of
+    the order of FGMRES's."""
+    grid = _box((4, 4, 2), 4)
+    pr = solve.Problem(grid)
+    x, y, z = grid.coordinates()
+    b = dg.rhs(pr.graphs[0], workloads.gaussian_source(2)(x, y, z))
+    ud = np.linalg.solve(dg.assemble(pr.graphs[0]), b.ravel())
+    u, info = krylov.fcg(pr.apply, b, precond=pr.vcycle, tol=1e-12)
+    assert info["converged"]
+    assert np.linalg.norm(u.ravel() - ud) <= 1e-10 * np.linalg.norm(ud)
+    _, ginfo = pr.solve_linear(b, tol=1e-12)
+    assert info["iterations"] <= 2 * ginfo["iterations"] + 2
+
+
 def test_multigrid_schwarz_beats_schwarz_beats_unpreconditioned():
     """Sec. IV.A: Schwarz preconditioning cuts iterations by about an order of magnitude,
     multigrid-Schwarz further."""
