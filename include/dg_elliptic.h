@@ -104,17 +104,21 @@ typedef struct dg_layout {
 } dg_layout;
 
 typedef struct dg_solve_opts {
-  int32_t max_iterations;      /* FGMRES iterations per linear solve (no restart); default 200 */
+  int32_t max_iterations;      /* Krylov iterations per linear solve (no restart); default 200 */
   int32_t precondition;        /* 0 none, 1 Schwarz only (presmooth+postsmooth steps), 2 multigrid V-cycle (default) */
   double linear_tol;           /* PUNCTURE: relative tolerance of each linearized solve; default 1e-4 */
   int32_t max_newton_steps;    /* PUNCTURE: default 20 */
   int32_t subdomain_iterations;/* PUNCTURE: GMRES iterations per subdomain solve; default 3 */
   int32_t relative_to_b;       /* 0: tol relative to ||b - A u0|| (default); 1: relative to ||b|| */
+  int32_t krylov;              /* 0: flexible GMRES (Sec. III.B, default); 1: flexible conjugate gradients
+                                  (one search direction, three reductions per iteration; the operator is
+                                  SPD for both problems): r = b - A x, z = M r,
+                                  p = z - (z.A p_old / p_old.A p_old) p_old, alpha = p.r / p.A p */
 } dg_solve_opts;
 
 typedef struct dg_solve_report {
   int32_t status;              /* dg_status of the solve */
-  int32_t iterations;          /* total FGMRES iterations (summed over Newton steps) */
+  int32_t iterations;          /* total Krylov iterations (summed over Newton steps) */
   int32_t newton_steps;
   int32_t line_search_steps;
   double initial_residual;     /* ||b - A(u0)||_2 */

@@ -68,10 +68,13 @@ def host_coordinates(desc):
     return tuple(out)
 
 
+KRYLOV = {"fgmres": 0, "fcg": 1}
+
+
 def solve_opts(max_iterations=200, precondition=2, linear_tol=1e-4, max_newton_steps=20, subdomain_iterations=3,
-               relative_to_b=False):
+               relative_to_b=False, krylov="fgmres"):
     return nat.dg_solve_opts(max_iterations, precondition, linear_tol, max_newton_steps, subdomain_iterations,
-                             int(relative_to_b))
+                             int(relative_to_b), KRYLOV[krylov])
 
 
 @dataclasses.dataclass

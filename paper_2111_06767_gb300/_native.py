@@ -39,7 +39,8 @@ class dg_layout(C.Structure):
 
 class dg_solve_opts(C.Structure):
     _fields_ = [("max_iterations", C.c_int32), ("precondition", C.c_int32), ("linear_tol", C.c_double),
-                ("max_newton_steps", C.c_int32), ("subdomain_iterations", C.c_int32), ("relative_to_b", C.c_int32)]
+                ("max_newton_steps", C.c_int32), ("subdomain_iterations", C.c_int32), ("relative_to_b", C.c_int32),
+                ("krylov", C.c_int32)]
 
 
 class dg_solve_report(C.Structure):

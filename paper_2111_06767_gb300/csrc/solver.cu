@@ -539,6 +539,66 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
   return R;
 }
 
+// Flexible conjugate gradients (the SPD alternative to FGMRES): one search direction, made
+// A-orthogonal to the previous one after every (possibly non-symmetric) V-cycle. Three host reads
+// per iteration: z.A p_old, (p.r, p.A p), ||r||. Vectors r and q = A p sit next to each other in
+// the Krylov buffer so that p.r and p.q are one two-vector reduction.
+LinearResult fcg(dg_domain* dom, const double* b, double* x, double tol, double ref_b_norm, int max_it, int pmode,
+                 bool rel_to_b) {
+  cudaStream_t s = dom->stream;
+  const int64_t n = dom->levels[0].ndof;
+  ensure_workspace(dom, 4);
+  LinearResult R;
+  double* r = dom->V.get();
+  double* q = r + n;
+  double* z = r + 2 * n;
+  double* p = r + 3 * n;
+  double* dh = dom->dots.get();
+  auto read = [&](int cnt, double* out) {
+    DG_CUDA(cudaMemcpyAsync(out, dh, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+  };
+  apply_level(dom, 0, x, r, b, true, s);  // r = b - A x
+  const double beta = norm2(dom, r, s);
+  R.r0 = beta;
+  const double ref = rel_to_b ? ref_b_norm : beta;
+  if (!std::isfinite(beta)) { R.status = DG_ERR_BREAKDOWN; return R; }
+  double res = beta, pq_old = 0.0;
+  for (int k = 0; k < max_it && res > tol * ref && res > 0.0; ++k) {
+    precondition(dom, pmode, r, z, s);
+    if (k == 0) {
+      DG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      launch_multidot(n, 1, q, n, z, dom->partial.get(), dh, s);  // z . A p_old
+      double zq;
+      read(1, &zq);
+      launch_axpby<double>(n, 1.0, z, -zq / pq_old, p, s);  // p = z - (z.q_old / p_old.q_old) p_old
+    }
+    apply_level(dom, 0, p, q, nullptr, true, s);  // q = A p
+    double pr_pq[2];
+    {
+      PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, 8.0 * n * 7.0, 8.0 * n * 4.0);
+      launch_multidot(n, 2, r, n, p, dom->partial.get(), dh, s);  // [p.r, p.q]
+      read(2, pr_pq);
+    }
+    if (!(pr_pq[1] > 0.0) || !std::isfinite(pr_pq[0])) { R.status = DG_ERR_BREAKDOWN; break; }
+    const double alpha = pr_pq[0] / pr_pq[1];
+    launch_axpby<double>(n, alpha, p, 1.0, x, s);
+    launch_axpby<double>(n, -alpha, q, 1.0, r, s);
+    pq_old = pr_pq[1];
+    res = norm2(dom, r, s);
+    R.iterations = k + 1;
+    if (!std::isfinite(res)) { R.status = DG_ERR_BREAKDOWN; break; }
+  }
+  apply_level(dom, 0, x, dom->r.get(), b, true, s);
+  R.final_res = norm2(dom, dom->r.get(), s);
+  if (R.status == DG_OK) {
+    if (!std::isfinite(R.final_res)) R.status = DG_ERR_BREAKDOWN;
+    else if (R.final_res > tol * ref * (1.0 + 1e-6)) R.status = DG_ERR_NOT_CONVERGED;
+  }
+  return R;
+}
+
 void set_linearization(dg_domain* dom, const double* u, cudaStream_t s) {
   launch_puncture_linearization(dom->levels[0].ndof, u, dom->mass.get(), dom->alpha.get(), dom->beta.get(),
                                 dom->lin64.get(), dom->lin32.get(), s);
@@ -573,13 +633,15 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
   const int max_it = o.max_iterations > 0 ? o.max_iterations : 200;
   const int pmode = o.precondition;
   DG_REQUIRE(pmode >= 0 && pmode <= 2, "precondition must be 0, 1 or 2");
+  DG_REQUIRE(o.krylov == 0 || o.krylov == 1, "krylov must be 0 (FGMRES) or 1 (flexible CG)");
   DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
   ensure_workspace(dom, std::min(max_it, 16));
   dg_solve_report R{};
   if (dom->desc.problem == DG_PROBLEM_POISSON) {
     const double bn = o.relative_to_b ? norm2(dom, b, s) : 0.0;
     dom->lin_set = false;
-    LinearResult L = fgmres(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0);
+    LinearResult L = o.krylov == 1 ? fcg(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0)
+                                   : fgmres(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0);
     R.iterations = L.iterations;
     R.initial_residual = L.r0;
     R.final_residual = L.final_res;
@@ -608,7 +670,8 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
       DG_CUDA(cudaMemsetAsync(dom->du.get(), 0, sizeof(double) * n, s));
       // the linear right-hand side is r (copied: the Krylov solver overwrites dom->r)
       DG_CUDA(cudaMemcpyAsync(dom->ut.get(), r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      LinearResult L = fgmres(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false);
+      LinearResult L = o.krylov == 1 ? fcg(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false)
+                                     : fgmres(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false);
       R.iterations += L.iterations;
       if (L.status == DG_ERR_BREAKDOWN) { R.status = L.status; break; }
       double lam = 1.0, rn_new = 0.0;

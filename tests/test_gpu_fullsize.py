@@ -39,6 +39,16 @@ def test_gaussian_8x8x8_N8_three_levels():
         sols[precision] = (uh, rep.iterations)
     assert rel(sols["mixed"][0], sols["fp64"][0]) < 1e-9
     assert abs(sols["mixed"][1] - sols["fp64"][1]) <= 1
+    # the flexible conjugate gradient method on the same problem (mixed precision)
+    d = dgg.Domain(n=n, N=N, precision="mixed", mg_levels=3, overlap=2)
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    u = torch.zeros_like(b)
+    rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(krylov="fcg"))
+    assert rep.status == 0 and rep.relative_residual <= 1e-10
+    uh = u.cpu().numpy()
+    r = b_ref - dg.apply(graph, uh.reshape(-1, N, N, N)).ravel()
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b_ref)
+    assert rel(uh, sols["fp64"][0]) < 1e-9
 
 
 def test_puncture_16x16x16_N6_newton():

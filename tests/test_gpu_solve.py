@@ -117,3 +117,43 @@ def test_solves_do_not_read_uninitialised_memory(precision):
         assert torch.equal(u, ref[mode])
         del d
     del keep
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_flexible_cg_matches_oracle(precision):
+    """elliptic_solve with the flexible conjugate gradient method (krylov = 1) against the oracle's
+    flexible CG and the dense direct solution: same iteration count within one in FP64, the direct
+    solution to 1e-9 at a 1e-10 residual in both precisions."""
+    from oracle import krylov
+
+    n, N = (4, 4, 2), 4
+    grid = box(n, N)
+    pr = solve.Problem(grid)
+    x, y, z = grid.coordinates()
+    f = workloads.gaussian_source(2)(x, y, z)
+    b_ref = dg.rhs(pr.graphs[0], f)
+    ud = np.linalg.solve(dg.assemble(pr.graphs[0]), b_ref.ravel())
+    _, info = krylov.fcg(pr.apply, b_ref, precond=pr.vcycle, tol=1e-10)
+    d = dgg.Domain(n=n, N=N, precision=precision)
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    u = torch.zeros_like(b)
+    rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(krylov="fcg"))
+    assert rep.status == 0 and rep.relative_residual <= 1e-10
+    assert rel(u.cpu().numpy(), ud) < 1e-9
+    if precision == "fp64":
+        assert abs(rep.iterations - info["iterations"]) <= 1
+
+
+def test_flexible_cg_newton_puncture():
+    """The Newton-Krylov puncture solve with flexible CG for the linearized (SPD) problems reaches
+    the same solution as with FGMRES."""
+    P = workloads.BINARY_PUNCTURES
+    sols = {}
+    for kr in ("fgmres", "fcg"):
+        d = dgg.Domain((-20.0,) * 3, (20.0,) * 3, (4, 4, 4), 5, precision="mixed", overlap=2, problem="puncture",
+                       punctures=P)
+        u = torch.zeros(d.n_dof, dtype=torch.float64, device="cuda")
+        rep = d.solve(None, u, tol=1e-10, opts=dgg.solve_opts(linear_tol=1e-4, krylov=kr))
+        assert rep.status == 0 and rep.relative_residual <= 1e-10
+        sols[kr] = u.cpu().numpy()
+    assert rel(sols["fcg"], sols["fgmres"]) < 1e-9
