@@ -17,7 +17,10 @@ Readings where the paper is silent (each also listed in the design notes):
     LGL collocation quadrature, so M and the face mass are diagonal, MD_i = M D_i exactly
     and L only touches face nodes;
   * h in the penalty: the element width along the face normal (affine boxes);
-  * Dirichlet boundaries are homogeneous (u_b = 0) in the operator; the paper's n^ext = -n^int.
+  * Dirichlet boundaries are homogeneous (u_b = 0) in the operator; the paper's n^ext = -n^int;
+  * Neumann boundaries (optional, per box face) are homogeneous: Eq. bc with the auxiliary
+    boundary flux taken from the interior, (n F_v)^b = (n F_v)^int (so u* = u^int), and the
+    primal boundary flux prescribed, (n F_u)^b = n . grad u_b = 0.
 
 Layout: nodal data u[..., e, k, j, i] with i (x) fastest; faces f = 2 d + side, d in
 {0: x, 1: y, 2: z}, side 0 = lower (n = -e_d), 1 = upper (n = +e_d).
@@ -32,6 +35,7 @@ from . import lgl
 
 EXTERNAL = -1  # external boundary face: Dirichlet fluxes of Eq. bc
 ZERO = -2      # internal face whose exterior data is zero (outside a Schwarz subdomain)
+NEUMANN = -3   # external boundary face: homogeneous Neumann fluxes of Eq. bc
 
 # node axis of dimension d in an array [..., e, k, j, i]
 _NODE_AXIS = {0: -1, 1: -2, 2: -3}
@@ -42,7 +46,7 @@ class ElementGraph:
     """Elements of one isotropic order N with their face connectivity.
 
     h[e, d]    element width along d
-    nbr[e, f]  exterior element index, EXTERNAL or ZERO
+    nbr[e, f]  exterior element index, EXTERNAL, NEUMANN or ZERO
     h_ext[e,f] width of the exterior element along the face normal (interior width at
                external faces)
     """
@@ -60,13 +64,15 @@ class ElementGraph:
 
 @dataclasses.dataclass
 class BoxGrid:
-    """A box [lower, upper] split uniformly into n[0] x n[1] x n[2] affine elements."""
+    """A box [lower, upper] split uniformly into n[0] x n[1] x n[2] affine elements. neumann[f]
+    marks box face f (-x, +x, -y, +y, -z, +z) as homogeneous Neumann (Dirichlet otherwise)."""
 
     lower: tuple
     upper: tuple
     n: tuple
     N: int
     penalty: float
+    neumann: tuple = (False,) * 6
 
     @property
     def n_elements(self) -> int:
@@ -88,7 +94,7 @@ class BoxGrid:
         d, side = divmod(f, 2)
         c[d] += 1 if side else -1
         if c[d] < 0 or c[d] >= self.n[d]:
-            return EXTERNAL
+            return NEUMANN if self.neumann[f] else EXTERNAL
         return self.element_index(*c)
 
     def graph(self) -> ElementGraph:
@@ -185,12 +191,15 @@ def apply(graph: ElementGraph, u: np.ndarray, dirichlet_value: float = 0.0) -> n
         gd_ext = gd_ext * mask
 
         ext_bc = (ext_type == EXTERNAL)[:, None, None]
+        ext_neu = (ext_type == NEUMANN)[:, None, None]
         # auxiliary normal fluxes (component d only): n_i F_v^i_d(u) = n_d u
         nFv_int = s * u_int
         nFv_ext = np.where(ext_bc, nFv_int - 2.0 * s * dirichlet_value, -s * u_ext)  # Eq. bc, Dirichlet
+        nFv_ext = np.where(ext_neu, -nFv_int, nFv_ext)  # Neumann: (n F_v)^b = (n F_v)^int
         # primal normal fluxes of the local gradients: n_i F_u^i(grad u) = n . g
         nFu_int = s * gd_int
         nFu_ext = np.where(ext_bc, nFu_int - 2.0 * nFu_int, -s * gd_ext)  # Eq. bc, (nF_u)^b = (nF_u)^int
+        nFu_ext = np.where(ext_neu, nFu_int, nFu_ext)  # Neumann: (n F_u)^b = n . grad u_b = 0
 
         # Eq. numfluxaux: component d of (n_i F_v^i)^*
         aux_star = 0.5 * (nFv_int - nFv_ext)

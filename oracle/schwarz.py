@@ -130,8 +130,8 @@ class SchwarzLevel:
         for s, g in enumerate(slots):
             for f in range(6):
                 q = nbr[g, f]
-                if q == dg.EXTERNAL:
-                    pn[s, f] = dg.EXTERNAL
+                if q in (dg.EXTERNAL, dg.NEUMANN):
+                    pn[s, f] = q
                 elif q in slot_of:
                     pn[s, f] = slot_of[q]
         patch = dg.ElementGraph(N, self.graph.penalty, self.graph.h[slots], pn, self.graph.h_ext[slots])

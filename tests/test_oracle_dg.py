@@ -11,16 +11,17 @@ import workloads
 from oracle import dg, lgl
 
 
-def _box(n, N, C=1.5, lower=(-1.0,) * 3, upper=(1.0,) * 3):
-    return dg.BoxGrid(tuple(lower), tuple(upper), tuple(n), N, C)
+def _box(n, N, C=1.5, lower=(-1.0,) * 3, upper=(1.0,) * 3, neumann=(False,) * 6):
+    return dg.BoxGrid(tuple(lower), tuple(upper), tuple(n), N, C, tuple(neumann))
 
 
 def sipg_matrix(grid: dg.BoxGrid) -> np.ndarray:
     """Independent brute-force assembly of the symmetric interior-penalty bilinear form
     a(w,u) = sum_K (grad w, grad u)_K - sum_F ({d_n w}[u] + {d_n u}[w])_F + sum_F (sigma_F [w][u])_F
     with LGL quadrature, sigma_F = C N^2 / h_perp on interior faces and 2 C N^2 / h_perp on
-    Dirichlet faces (the mirror ghost of Eq. bc doubles the jump). Summation by parts on LGL
-    points turns the paper's strong form into exactly this form."""
+    Dirichlet faces (the mirror ghost of Eq. bc doubles the jump), and no face term at all on
+    homogeneous Neumann faces (the natural boundary condition). Summation by parts on LGL points
+    turns the paper's strong form into exactly this form."""
     N, E = grid.N, grid.n_elements
     x, w = lgl.lgl_nodes(N), lgl.lgl_weights(N)
     Dh = lgl.diff_matrix(N)
@@ -65,6 +66,8 @@ def sipg_matrix(grid: dg.BoxGrid) -> np.ndarray:
                 dTe[:, blk(e)] = s * G[d][rows]
                 if q == dg.EXTERNAL:
                     jump, avg, sig = Te, dTe, 2 * sigma / h[d]
+                elif q == dg.NEUMANN:
+                    continue
                 elif side == 1:  # count each interior face once, from its lower element
                     rows_q = face_rows(d, 0)
                     Tq = np.zeros((len(rows), ndof))
@@ -159,3 +162,68 @@ def test_scaling_with_element_size():
     a = dg.assemble(_box((2, 1, 1), 3, lower=(0, 0, 0), upper=(2, 1, 1)).graph())
     b = dg.assemble(_box((2, 1, 1), 3, lower=(0, 0, 0), upper=(0.5, 0.25, 0.25)).graph())
     assert np.abs(b - 0.25 * a).max() <= 1e-13 * np.abs(a).max()
+
+
+# ---------------------------------------------------------------- homogeneous Neumann faces
+NEU_YZ = (False, False, True, True, True, True)  # Dirichlet at x = +-1, Neumann on the y and z faces
+
+
+@pytest.mark.parametrize("n,N,neu", [((1, 1, 1), 3, (True,) * 6), ((2, 1, 1), 3, NEU_YZ),
+                                     ((2, 2, 1), 3, (True, False, False, True, False, True)),
+                                     ((1, 2, 2), 4, NEU_YZ)])
+def test_neumann_strong_form_equals_sipg_bilinear_form(n, N, neu):
+    grid = _box(n, N, lower=(-1.0, -0.5, 0.0), upper=(1.0, 0.5, 3.0), neumann=neu)
+    A = dg.assemble(grid.graph())
+    S = sipg_matrix(grid)
+    assert np.abs(A - S).max() <= 1e-12 * np.abs(S).max()
+
+
+def test_pure_neumann_operator_annihilates_constants():
+    """With every box face Neumann, constants have zero gradient, zero jumps and zero boundary
+    flux, so A 1 = 0 exactly; the operator stays symmetric."""
+    for n, N in [((1, 1, 1), 4), ((2, 1, 3), 3), ((2, 2, 2), 5)]:
+        gr = _box(n, N, neumann=(True,) * 6).graph()
+        one = np.ones((gr.n_elements, N, N, N))
+        Au = dg.apply(gr, one)
+        A = dg.assemble(gr)
+        assert np.abs(Au).max() <= 1e-12 * np.abs(A).max()
+        assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("n,N,neu", [((2, 2, 2), 3, NEU_YZ), ((1, 2, 1), 4, (True,) * 5 + (False,)),
+                                     ((2, 1, 2), 4, (False, True, False, True, False, True))])
+def test_mixed_boundaries_symmetric_positive_definite(n, N, neu):
+    A = dg.assemble(_box(n, N, neumann=neu).graph())
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    np.linalg.cholesky(A)  # one Dirichlet face is enough
+
+
+def test_mixed_boundaries_polynomial_consistency():
+    """u = (1 - x^2)(1 - y^2)^2 (1 - z^2)^2 vanishes at x = +-1 and has zero normal derivative on
+    the y and z faces: no jump anywhere, every boundary flux exact, so A u = M (-Laplace u)."""
+    X, Y, Z = sp.symbols("x y z")
+    U = (1 - X**2) * (1 - Y**2) ** 2 * (1 - Z**2) ** 2
+    lap = sp.lambdify((X, Y, Z), -(sp.diff(U, X, 2) + sp.diff(U, Y, 2) + sp.diff(U, Z, 2)), "numpy")
+    uf = sp.lambdify((X, Y, Z), U, "numpy")
+    for n, N in [((2, 2, 2), 5), ((1, 3, 2), 6)]:
+        grid = _box(n, N, neumann=NEU_YZ)
+        gr = grid.graph()
+        x, y, z = grid.coordinates()
+        Au = dg.apply(gr, uf(x, y, z))
+        ref = dg.mass_diag(gr) * lap(x, y, z)
+        assert np.abs(Au - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_mixed_boundaries_manufactured_p_convergence():
+    """u = sin(pi x) cos(pi y) cos(pi z), f = 3 pi^2 u, Dirichlet at x = +-1 and Neumann on the other
+    faces (both hold exactly for this u): the nodal error decays exponentially in N."""
+    errs = []
+    for N in (4, 6, 8):
+        grid = _box((2, 2, 2), N, neumann=NEU_YZ)
+        gr = grid.graph()
+        x, y, z = grid.coordinates()
+        ue = np.sin(math.pi * x) * np.cos(math.pi * y) * np.cos(math.pi * z)
+        u = np.linalg.solve(dg.assemble(gr), dg.rhs(gr, 3 * math.pi**2 * ue).ravel())
+        errs.append(math.sqrt(np.mean((u - ue.ravel()) ** 2)))
+    assert errs[0] / errs[1] > 20 and errs[1] / errs[2] > 0.9 * errs[0] / errs[1]
+    assert errs[2] < 1e-5

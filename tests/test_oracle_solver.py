@@ -120,8 +120,9 @@ def test_subdomain_operator_is_restricted_global_operator():
         assert np.abs(lv.subdomain_matrix(e) - A[np.ix_(g, g)]).max() <= 1e-14 * np.abs(A).max()
 
 
-def test_single_element_schwarz_is_exact():
-    grid = _box((1, 1, 1), 5)
+@pytest.mark.parametrize("neumann", [(False,) * 6, (False, False, True, True, True, True)])
+def test_single_element_schwarz_is_exact(neumann):
+    grid = dg.BoxGrid((-1.0,) * 3, (1.0,) * 3, (1, 1, 1), 5, 1.5, neumann)
     gr = grid.graph()
     lv = schwarz.SchwarzLevel(grid, 2)
     x, y, z = grid.coordinates()
@@ -174,6 +175,19 @@ def test_fcg_without_preconditioner_is_conjugate_gradients():
         for j in range(i):
             c = P[i] @ A @ P[j] / math.sqrt((P[i] @ A @ P[i]) * (P[j] @ A @ P[j]))
             assert abs(c) < 1e-8
+
+
+def test_multigrid_schwarz_with_neumann_faces_matches_direct_solve():
+    """Mixed boundaries (Dirichlet at x = +-1, homogeneous Neumann elsewhere) on every level of the
+    V-cycle and in every subdomain matrix: FGMRES reaches the direct solution."""
+    grid = dg.BoxGrid((-1.0,) * 3, (1.0,) * 3, (4, 2, 2), 4, 1.5, (False, False, True, True, True, True))
+    pr = solve.Problem(grid)
+    x, y, z = grid.coordinates()
+    b = dg.rhs(pr.graphs[0], workloads.gaussian_source(3)(x, y, z))
+    ud = np.linalg.solve(dg.assemble(pr.graphs[0]), b.ravel())
+    u, info = pr.solve_linear(b, tol=1e-12)
+    assert info["converged"] and info["iterations"] < 30
+    assert np.linalg.norm(u.ravel() - ud) <= 1e-9 * np.linalg.norm(ud)
 
 
 def test_fcg_with_multigrid_schwarz_matches_direct_solve():
