@@ -80,6 +80,10 @@ typedef struct dg_domain_desc {
   int32_t n_punctures; /* DG_PROBLEM_PUNCTURE only, 0..DG_MAX_PUNCTURES */
   dg_puncture punctures[DG_MAX_PUNCTURES];
   int32_t subdomain_gemm; /* how du_S = A_S^-1 r_S is applied in a MIXED domain: enum dg_subdomain_gemm */
+  int32_t neumann_faces;  /* bit f set: box face f (0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z) carries the homogeneous
+                             Neumann condition n.grad u = 0 of Eq. bc (interior auxiliary flux, zero
+                             prescribed normal flux) instead of homogeneous Dirichlet; at least one
+                             face must stay Dirichlet (the pure Neumann operator is singular) */
 } dg_domain_desc;
 
 enum dg_subdomain_gemm {

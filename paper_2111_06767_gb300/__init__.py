@@ -39,7 +39,9 @@ GEMM_MODES = {"default": 0, "simt": 1, "tf32": 2}
 
 
 def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, overlap=2, presmooth=3,
-              postsmooth=3, problem="poisson", punctures=(), gemm="default"):
+              postsmooth=3, problem="poisson", punctures=(), gemm="default", neumann=()):
+    """neumann: indices of the box faces (0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z) with homogeneous
+    Neumann conditions (the others are homogeneous Dirichlet)."""
     d = nat.dg_domain_desc()
     for i in range(3):
         d.lower[i], d.upper[i], d.n[i] = lower[i], upper[i], n[i]
@@ -54,6 +56,7 @@ def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, ov
             d.punctures[q].momentum[i] = p.momentum[i]
         d.punctures[q].mass = p.mass
     d.subdomain_gemm = GEMM_MODES[gemm]
+    d.neumann_faces = sum(1 << int(f) for f in set(neumann))
     return d
 
 
@@ -94,9 +97,9 @@ class Domain:
 
     def __init__(self, lower=(-1.0,) * 3, upper=(1.0,) * 3, n=(2, 2, 2), N=6, penalty=1.5, precision="fp64",
                  mg_levels=0, overlap=2, presmooth=3, postsmooth=3, problem="poisson", punctures=(), stream=None,
-                 gemm="default"):
+                 gemm="default", neumann=()):
         self.desc = make_desc(lower, upper, n, N, penalty, precision, mg_levels, overlap, presmooth, postsmooth,
-                              problem, punctures, gemm)
+                              problem, punctures, gemm, neumann)
         self._h = C.c_void_p()
         st = _lib.dg_domain_create(C.byref(self.desc), _stream(stream), C.byref(self._h))
         if st != nat.DG_OK:

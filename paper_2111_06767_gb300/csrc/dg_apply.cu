@@ -12,7 +12,9 @@
 //           - sum_faces Bf [ s/2 (g_ext - g_int) + (sigma_d - 1/(w_0 h_d)) (u_ext - u_int) ]
 // where Bf = J_f w_a w_b is the face quadrature weight. At an external face Eq. bc with
 // (n F_v)^b = n u_b, u_b = 0, and (n F_u)^b = (n F_u)^int is the ghost state u_ext = -u_int,
-// g_ext = g_int, which this kernel uses.
+// g_ext = g_int, which this kernel uses on Dirichlet faces. On a homogeneous Neumann face of the
+// box (Eq. bc with (n F_v)^b = (n F_v)^int and a zero prescribed normal flux (n F_u)^b = 0) the
+// ghost state is u_ext = u_int, g_ext = -g_int: no jump, no lifting and a zero numerical flux.
 //
 // GB300 mapping: one thread per x-line of N points (the N contiguous values of u[e][k][j][:]),
 // N^2 threads per element, EPB elements per CTA. Every global access is a coalesced vector access of
@@ -86,13 +88,15 @@ struct LineShape {
 
 // Lifting and primal flux at one face point of normal s e_d: from the interior value ui and local
 // gradient component gi, the neighbour's value ue and normal derivative ge (has = the neighbour
-// exists; otherwise the Dirichlet ghost state of Eq. bc with u_b = 0), returns the lifted v_d and
-// adds the flux term of the point, weighted by the face quadrature weight Bf, to fl.
+// exists; otherwise the ghost state of Eq. bc: u_E = -u_i, g_E = g_i on a homogeneous Dirichlet
+// face, u_E = u_i, g_E = -g_i on a homogeneous Neumann face (neu), which makes the jump and the
+// numerical normal flux vanish), returns the lifted v_d and adds the flux term of the point,
+// weighted by the face quadrature weight Bf, to fl.
 template <typename T>
-__device__ __forceinline__ T face_point(T s, T ui, T gi, T ue, T ge, bool has, T lift, T sigma_minus_lift, T Bf,
-                                        T& fl) {
-  const T uE = has ? ue : -ui;
-  const T gE = has ? ge : gi;
+__device__ __forceinline__ T face_point(T s, T ui, T gi, T ue, T ge, bool has, bool neu, T lift,
+                                        T sigma_minus_lift, T Bf, T& fl) {
+  const T uE = has ? ue : (neu ? ui : -ui);
+  const T gE = has ? ge : (neu ? -gi : gi);
   const T jump = uE - ui;
   fl -= Bf * (T(0.5) * s * (gE - gi) + sigma_minus_lift * jump);
   return gi + s * jump * lift;
@@ -247,8 +251,9 @@ __device__ __forceinline__ void apply_line_block(const ApplyArgs<T>& A, int blk)
   for (int i = 0; i < N; ++i) o[i] = T(0);
   {
     const T Bf = g.Jf[0] * wj * wk, sml = g.sigma[0] - g.lift[0];
-    vx[0] = face_point(T(-1), ul[0], vx[0], uxm, gxm, hxm, g.lift[0], sml, Bf, o[0]);
-    vx[N - 1] = face_point(T(1), ul[N - 1], vx[N - 1], uxp, gxp, hxp, g.lift[0], sml, Bf, o[N - 1]);
+    vx[0] = face_point(T(-1), ul[0], vx[0], uxm, gxm, hxm, g.neumann & 1, g.lift[0], sml, Bf, o[0]);
+    vx[N - 1] = face_point(T(1), ul[N - 1], vx[N - 1], uxp, gxp, hxp, (g.neumann >> 1) & 1, g.lift[0], sml, Bf,
+                           o[N - 1]);
   }
   __syncthreads();  // face data written; every read of the neighbour blocks is done
   sst_line<N>(&sm[1][el][so], vy);
@@ -261,23 +266,23 @@ __device__ __forceinline__ void apply_line_block(const ApplyArgs<T>& A, int blk)
     const int py = k * N + j, pz = j * N + k;
     T fl = T(0);
     T* v = &sm[1][el][k * P + j];
-    *v = face_point(T(-1), sm[0][el][k * P + j], *v, sf[0][0][el][py], sf[0][1][el][py], hym, g.lift[1],
-                    g.sigma[1] - g.lift[1], g.Jf[1] * Bf, fl);
+    *v = face_point(T(-1), sm[0][el][k * P + j], *v, sf[0][0][el][py], sf[0][1][el][py], hym, (g.neumann >> 2) & 1,
+                    g.lift[1], g.sigma[1] - g.lift[1], g.Jf[1] * Bf, fl);
     sm[3][el][py] = fl;
     fl = T(0);
     v = &sm[1][el][k * P + (N - 1) * N + j];
     *v = face_point(T(1), sm[0][el][k * P + (N - 1) * N + j], *v, sf[1][0][el][py], sf[1][1][el][py], hyp,
-                    g.lift[1], g.sigma[1] - g.lift[1], g.Jf[1] * Bf, fl);
+                    (g.neumann >> 3) & 1, g.lift[1], g.sigma[1] - g.lift[1], g.Jf[1] * Bf, fl);
     sm[3][el][N2 + py] = fl;
     fl = T(0);
     v = &sm[2][el][j * N + k];
-    *v = face_point(T(-1), sm[0][el][j * N + k], *v, sf[2][0][el][pz], sf[2][1][el][pz], hzm, g.lift[2],
-                    g.sigma[2] - g.lift[2], g.Jf[2] * Bf, fl);
+    *v = face_point(T(-1), sm[0][el][j * N + k], *v, sf[2][0][el][pz], sf[2][1][el][pz], hzm, (g.neumann >> 4) & 1,
+                    g.lift[2], g.sigma[2] - g.lift[2], g.Jf[2] * Bf, fl);
     sm[4][el][pz] = fl;
     fl = T(0);
     v = &sm[2][el][(N - 1) * P + j * N + k];
     *v = face_point(T(1), sm[0][el][(N - 1) * P + j * N + k], *v, sf[3][0][el][pz], sf[3][1][el][pz], hzp,
-                    g.lift[2], g.sigma[2] - g.lift[2], g.Jf[2] * Bf, fl);
+                    (g.neumann >> 5) & 1, g.lift[2], g.sigma[2] - g.lift[2], g.Jf[2] * Bf, fl);
     sm[4][el][N2 + pz] = fl;
   }
   __syncthreads();

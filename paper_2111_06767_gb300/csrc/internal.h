@@ -124,10 +124,11 @@ struct OpGeom {
   T Jf[3];       // face Jacobian of faces normal to d: product of the tangential h/2
   T sigma[3];    // penalty C N^2 / h_d (Eq. penalty, equal neighbours)
   T lift[3];     // 1 / (w_0 h_d): L = M^-1 ML at a face node is 2 lift[d]
+  int neumann;   // bit f: box face f (= 2 d + side) is homogeneous Neumann, else Dirichlet
 };
 
 template <typename T>
-OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, const LglTables& t);
+OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, const LglTables& t, int neumann = 0);
 
 // ------------------------------------------------------------------ kernels (launchers)
 

@@ -102,8 +102,9 @@ LglTables make_lgl(int N) {
 }
 
 template <typename T>
-OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, const LglTables& t) {
+OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, const LglTables& t, int neumann) {
   OpGeom<T> g;
+  g.neumann = neumann;
   g.nx = n[0];
   g.ny = n[1];
   g.nz = n[2];
@@ -120,7 +121,7 @@ OpGeom<T> make_geom(const int n[3], const double h[3], int N, double penalty, co
   return g;
 }
 
-template OpGeom<double> make_geom<double>(const int*, const double*, int, double, const LglTables&);
-template OpGeom<float> make_geom<float>(const int*, const double*, int, double, const LglTables&);
+template OpGeom<double> make_geom<double>(const int*, const double*, int, double, const LglTables&, int);
+template OpGeom<float> make_geom<float>(const int*, const double*, int, double, const LglTables&, int);
 
 }  // namespace dg

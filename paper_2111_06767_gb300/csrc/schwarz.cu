@@ -30,8 +30,9 @@ namespace dg {
 // ------------------------------------------------------------------ A_S columns
 
 // Patch description per class: for slot s in 0..6 (0 = centre, 1 + f = neighbour across face f)
-// info[s*6 + f'] = face type of that slot's face f': >= 0 slot inside the patch, -1 external
-// boundary, -2 internal face with zero data outside the patch; info[42 + s] = slot exists.
+// info[s*6 + f'] = face type of that slot's face f': >= 0 slot inside the patch, -1 Dirichlet box
+// face, -2 internal face with zero data outside the patch, -3 Neumann box face; info[42 + s] = slot
+// exists.
 constexpr int kPatchInts = 49;
 
 template <int N>
@@ -142,6 +143,9 @@ __global__ void __launch_bounds__(ColumnShape<N>::threads) subdomain_column_kern
       } else if (t == -2) {
         u_ext = 0.0;
         g_ext = 0.0;
+      } else if (t == -3) {  // homogeneous Neumann face of the box
+        u_ext = u_int;
+        g_ext = -g_int;
       } else {
         // neighbour data is the unit vector restricted to slot t
         const int opp = side ? 0 : N - 1;

@@ -59,6 +59,10 @@ size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations) {
     size_t classes = (size_t)cats[0] * cats[1] * cats[2];
     if (hw[0] == hw[1] && hw[1] == hw[2] && cats[0] == cats[1] && cats[1] == cats[2])
       classes = (size_t)cats[0] * (cats[0] + 1) * (cats[0] + 2) / 6;
+    if (d.neumann_faces) {
+      // the two sides of a dimension may differ: up to 5 positions per dimension, no symmetry
+      classes = (size_t)std::min(n[0], 5) * std::min(n[1], 5) * std::min(n[2], 5);
+    }
     classes = std::min(classes, E);
     build_peak = std::max(build_peak, classes * nS * nS * 8);  // FP64 build, freed after inversion
     total += classes * ld * ld * fb;                            // stored inverses

@@ -84,10 +84,11 @@ void upload_arr(DevBuf<T>& buf, const double* src, int n, cudaStream_t s) {
 
 // Per-level subdomain classes and column order (cheap: done at creation).
 //
-// Per dimension a subdomain sees, on each side, no neighbour (code 0), a neighbour whose far face
-// is internal (1) or a neighbour whose far face is an external boundary (2). A_S depends only on
-// these six codes (uniform affine elements). The DG operator is invariant under reflecting a
-// dimension and under swapping dimensions of equal element width, so every subdomain is mapped
+// Per dimension a subdomain sees, on each side, a Dirichlet box face (code 0), a Neumann box face
+// (3), a neighbour whose far face is internal (1), or a neighbour whose far face is a Dirichlet (2)
+// or Neumann (4) box face. A_S depends only on these six codes (uniform affine elements). The DG
+// operator is invariant under reflecting a dimension and under swapping dimensions of equal element
+// width (with the boundary types moving along), so every subdomain is mapped
 // to a canonical orientation: each dimension reflected so that its lower code is the smaller,
 // then dimensions of equal width sorted by their code pair. Subdomains with equal canonical codes
 // share one explicit inverse, stored in the canonical point order; the gather and scatter kernels
@@ -100,20 +101,23 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   sw.ld = (sw.nS + 31) / 32 * 32;
   sw.geom = SubdomainGeom{{L.n[0], L.n[1], L.n[2]}, L.E, N, ov, sw.nS, sw.ld};
   const int E = L.E;
+  const int neu = dom->desc.neumann_faces;
+  auto is_nbr = [](int code) { return code == 1 || code == 2 || code == 4; };
   std::vector<int> key(E), xform(E);
   for (int e = 0; e < E; ++e) {
     const int c[3] = {e % L.n[0], (e / L.n[0]) % L.n[1], e / (L.n[0] * L.n[1])};
     int lo[3], hi[3], flip[3];
     for (int d = 0; d < 3; ++d) {
       const int n = L.n[d];
-      lo[d] = c[d] > 0 ? (c[d] - 1 == 0 ? 2 : 1) : 0;
-      hi[d] = c[d] < n - 1 ? (c[d] + 1 == n - 1 ? 2 : 1) : 0;
+      const int neu_lo = (neu >> (2 * d)) & 1, neu_hi = (neu >> (2 * d + 1)) & 1;
+      lo[d] = c[d] > 0 ? (c[d] - 1 == 0 ? (neu_lo ? 4 : 2) : 1) : (neu_lo ? 3 : 0);
+      hi[d] = c[d] < n - 1 ? (c[d] + 1 == n - 1 ? (neu_hi ? 4 : 2) : 1) : (neu_hi ? 3 : 0);
       flip[d] = lo[d] > hi[d];
       if (flip[d]) std::swap(lo[d], hi[d]);
     }
     // canonical axis a <- actual axis perm[a]; only dimensions of equal width may be exchanged
     int perm[3] = {0, 1, 2};
-    auto pair_key = [&](int d) { return lo[d] * 3 + hi[d]; };
+    auto pair_key = [&](int d) { return lo[d] * 5 + hi[d]; };
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j + 1 < 3 - i; ++j) {
         const int a = perm[j], b = perm[j + 1];
@@ -121,7 +125,7 @@ void classify_schwarz(dg_domain* dom, Level& L) {
       }
     int k = 0, fl = 0;
     for (int a = 0; a < 3; ++a) {
-      k = k * 9 + pair_key(perm[a]);
+      k = k * 25 + pair_key(perm[a]);
       fl |= flip[perm[a]] << a;
     }
     int pi = 0;
@@ -161,9 +165,9 @@ void classify_schwarz(dg_domain* dom, Level& L) {
     int codes[3][2];  // [canonical axis][side]
     int k = kv.first;
     for (int a = 2; a >= 0; --a) {
-      codes[a][0] = (k % 9) / 3;
-      codes[a][1] = k % 3;
-      k /= 9;
+      codes[a][0] = (k % 25) / 5;
+      codes[a][1] = k % 5;
+      k /= 25;
     }
     int* P = &sw.patch[(size_t)kv.second * 49];
     for (int s = 0; s < 7; ++s) P[42 + s] = 0;
@@ -171,15 +175,15 @@ void classify_schwarz(dg_domain* dom, Level& L) {
     for (int f = 0; f < 6; ++f) {
       const int a = f >> 1, side = f & 1;
       const int cd = codes[a][side];
-      P[f] = cd ? 1 + f : -1;
-      P[42 + 1 + f] = cd != 0;
-      if (!cd) continue;
+      P[f] = is_nbr(cd) ? 1 + f : (cd == 0 ? -1 : -3);
+      P[42 + 1 + f] = is_nbr(cd);
+      if (!is_nbr(cd)) continue;
       const int back = 2 * a + (1 - side);
       for (int ff = 0; ff < 6; ++ff) {
         const int aa = ff >> 1, ss = ff & 1;
         if (ff == back) P[(1 + f) * 6 + ff] = 0;                 // faces the centre
-        else if (ff == f) P[(1 + f) * 6 + ff] = cd == 2 ? -1 : -2;  // far face
-        else P[(1 + f) * 6 + ff] = codes[aa][ss] ? -2 : -1;     // tangential: as the centre's
+        else if (ff == f) P[(1 + f) * 6 + ff] = cd == 2 ? -1 : (cd == 4 ? -3 : -2);  // far face
+        else P[(1 + f) * 6 + ff] = is_nbr(codes[aa][ss]) ? -2 : (codes[aa][ss] == 0 ? -1 : -3);  // as the centre's
       }
     }
   }
@@ -306,6 +310,8 @@ void domain_setup(dg_domain* dom) {
   DG_REQUIRE(d.precision == DG_PRECISION_FP64 || d.precision == DG_PRECISION_MIXED, "bad precision");
   DG_REQUIRE(d.problem == DG_PROBLEM_POISSON || d.problem == DG_PROBLEM_PUNCTURE, "bad problem");
   DG_REQUIRE(d.mg_levels >= 0 && d.mg_levels <= DG_MAX_LEVELS, "mg_levels must be in [0, 8]");
+  DG_REQUIRE(d.neumann_faces >= 0 && d.neumann_faces < 63,
+             "neumann_faces must be a mask of box faces with at least one Dirichlet face");
   DG_REQUIRE(d.subdomain_gemm >= DG_GEMM_DEFAULT && d.subdomain_gemm <= DG_GEMM_TENSOR_TF32, "bad subdomain_gemm");
   DG_REQUIRE(d.subdomain_gemm != DG_GEMM_TENSOR_TF32 || d.precision == DG_PRECISION_MIXED,
              "tensor-core subdomain GEMM needs a MIXED domain");
@@ -351,8 +357,8 @@ void domain_setup(dg_domain* dom) {
     }
     L.E = n[0] * n[1] * n[2];
     L.ndof = (int64_t)L.E * N * N * N;
-    L.g64 = make_geom<double>(L.n, L.h, N, d.penalty, t);
-    L.g32 = make_geom<float>(L.n, L.h, N, d.penalty, t);
+    L.g64 = make_geom<double>(L.n, L.h, N, d.penalty, t, d.neumann_faces);
+    L.g32 = make_geom<float>(L.n, L.h, N, d.penalty, t, d.neumann_faces);
     dom->levels.push_back(std::move(L));
     if ((int)dom->levels.size() == (d.mg_levels ? d.mg_levels : DG_MAX_LEVELS)) break;
     if (n[0] % 2 && n[1] % 2 && n[2] % 2) break;
