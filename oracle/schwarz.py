@@ -228,6 +228,23 @@ def gmres_subdomain_solver(level: SchwarzLevel, diag: np.ndarray, iterations: in
     return solve
 
 
+def inverse_subdomain_solver(level: SchwarzLevel, diag: np.ndarray):
+    """Subdomain solver for a linearized operator A_S + D_S (D_S diagonal) by the explicit inverse
+    of every subdomain's own linearized matrix: Sec. III.E's explicit-inverse solver applied to the
+    full linearized operator instead of its Laplacian approximation. The matrices depend on the
+    linearization point, so they are formed afresh for every linearization (here: every call)."""
+    dflat = diag.ravel()
+
+    def solve(A_S, rS, members):
+        out = np.zeros_like(rS)
+        for m, e in enumerate(members):
+            D = dflat[level.subdomains[e]["glob"]]
+            out[m] = np.linalg.inv(A_S + np.diag(D)) @ rS[m]
+        return out
+
+    return solve
+
+
 def _gmres_right(op, prec, r, iterations):
     """Right-preconditioned GMRES with a zero initial guess (Saad Alg. 9.5), fixed iterations."""
     beta = np.linalg.norm(r)

@@ -51,17 +51,27 @@ class PunctureProblem(Problem):
         """b - A(u) with b = 0 and A(u) = A_Delta u + M S(u)."""
         return -(self.apply(u) + self.mass * puncture.source(u, self.alpha, self.beta))
 
-    def linear_solve(self, u, r, tol=1e-4, max_iter=100, subdomain_iterations=3):
+    def linear_solve(self, u, r, tol=1e-4, max_iter=100, subdomain_iterations=3, subdomain_solver="gmres"):
+        """One linearized solve (Eq. linearized) by FGMRES with the multigrid-Schwarz V-cycle. The
+        finest level's subdomain problems A_S + D_S are solved by GMRES preconditioned with the
+        Poisson inverse (subdomain_solver "gmres", Sec. III.E's Laplacian approximation) or by the
+        explicit inverse of each subdomain's A_S + D_S ("inverse")."""
         D = self.mass * puncture.source_deriv(u, self.alpha, self.beta)
         lin = lambda du: self.apply(du) + D * du
         ops = [lin] + [lambda x, l=l: self.apply(x, l) for l in range(1, len(self.levels))]
-        fine_solver = schwarz.gmres_subdomain_solver(self.schwarz[0], D, subdomain_iterations)
+        if subdomain_solver == "gmres":
+            fine_solver = schwarz.gmres_subdomain_solver(self.schwarz[0], D, subdomain_iterations)
+        elif subdomain_solver == "inverse":
+            fine_solver = schwarz.inverse_subdomain_solver(self.schwarz[0], D)
+        else:
+            raise ValueError(subdomain_solver)
         smoothers = [lambda b, x, it: self.schwarz[0].smooth(b, x, it, lin, fine_solver)]
         smoothers += [lambda b, x, it, s=s: s.smooth(b, x, it) for s in self.schwarz[1:]]
         pre = lambda v: self.vcycle(v, ops, smoothers)
         du, info = krylov.fgmres(lin, r, None, pre, tol, max_iter)
         return du, info
 
-    def solve(self, u0=None, tol=1e-10, linear_tol=1e-4, max_steps=20):
+    def solve(self, u0=None, tol=1e-10, linear_tol=1e-4, max_steps=20, subdomain_solver="gmres"):
         u0 = np.zeros_like(self.mass) if u0 is None else u0
-        return newton.newton(self.residual, lambda u, r: self.linear_solve(u, r, linear_tol), u0, tol, max_steps)
+        lin = lambda u, r: self.linear_solve(u, r, linear_tol, subdomain_solver=subdomain_solver)
+        return newton.newton(self.residual, lin, u0, tol, max_steps)

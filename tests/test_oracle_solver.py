@@ -284,6 +284,61 @@ def test_newton_result_independent_of_subdomain_solver():
     assert np.linalg.norm(u1 - u2) <= 1e-9 * np.linalg.norm(u2)
 
 
+def _linearization(grid, seed):
+    """A positive diagonal D = M S'(u) at a seeded state u of the binary-puncture source."""
+    pr = solve.PunctureProblem(grid, workloads.BINARY_PUNCTURES)
+    u = 0.1 * workloads.uniform_vector(seed, pr.mass.size, 0.0, 1.0).reshape(pr.mass.shape)
+    return pr, pr.mass * puncture.source_deriv(u, pr.alpha, pr.beta)
+
+
+def test_linearized_inverse_smoother_single_element_is_exact():
+    """n = 1: the one subdomain is the whole domain, so one step of the per-subdomain linearized
+    inverse solves (A + D) u = b exactly (dense solve of the assembled operator)."""
+    grid = _box((1, 1, 1), 5, lower=(-4,) * 3, upper=(4,) * 3)
+    pr, D = _linearization(grid, 7)
+    assert D.min() > 0 and D.max() > 1e-3 * np.abs(dg.assemble(pr.graphs[0])).max()
+    lv = pr.schwarz[0]
+    b = workloads.uniform_vector(8, D.size, -1.0, 1.0).reshape(D.shape)
+    lin = lambda x: dg.apply(pr.graphs[0], x) + D * x
+    u = lv.smooth(b, np.zeros_like(b), 1, lin, schwarz.inverse_subdomain_solver(lv, D))
+    exact = np.linalg.solve(dg.assemble(pr.graphs[0]) + np.diag(D.ravel()), b.ravel())
+    assert np.linalg.norm(u.ravel() - exact) <= 1e-12 * np.linalg.norm(exact)
+
+
+def test_linearized_inverse_smoother_special_cases():
+    """D = 0 gives the Poisson smoother; with D != 0 it equals the GMRES subdomain solver run to
+    convergence (enough iterations that the Krylov space holds the exact subdomain solution)."""
+    grid = _box((3, 2, 2), 3, lower=(-4,) * 3, upper=(4,) * 3)
+    pr, D = _linearization(grid, 9)
+    lv = pr.schwarz[0]
+    b = workloads.uniform_vector(10, D.size, -1.0, 1.0).reshape(D.shape)
+    u0 = workloads.uniform_vector(11, D.size, -1.0, 1.0).reshape(D.shape)
+    zero = np.zeros_like(D)
+    poisson = lv.smooth(b, u0, 2)
+    assert np.linalg.norm(lv.smooth(b, u0, 2, None, schwarz.inverse_subdomain_solver(lv, zero)) - poisson) \
+        <= 1e-12 * np.linalg.norm(poisson)
+    lin = lambda x: dg.apply(pr.graphs[0], x) + D * x
+    inv = lv.smooth(b, u0, 2, lin, schwarz.inverse_subdomain_solver(lv, D))
+    gm = lv.smooth(b, u0, 2, lin, schwarz.gmres_subdomain_solver(lv, D, 40))
+    assert np.linalg.norm(inv - gm) <= 1e-9 * np.linalg.norm(inv)
+    # the linearization term does enter the subdomain solves
+    no_d = lv.smooth(b, u0, 2, lin, schwarz.inverse_subdomain_solver(lv, zero))
+    assert np.linalg.norm(inv - no_d) > 1e-4 * np.linalg.norm(inv)
+
+
+def test_newton_with_linearized_inverse_subdomains_matches_default():
+    """The nonlinear solution does not depend on the subdomain solver; the exact linearized
+    subdomain solves take no more Krylov iterations than 3 GMRES iterations on them."""
+    grid = _box((2, 2, 2), 4, lower=(-20,) * 3, upper=(20,) * 3)
+    pr = solve.PunctureProblem(grid, workloads.BINARY_PUNCTURES)
+    u1, r1 = pr.solve(tol=1e-10, linear_tol=1e-4)
+    u2, r2 = pr.solve(tol=1e-10, linear_tol=1e-4, subdomain_solver="inverse")
+    assert r1["converged"] and r2["converged"]
+    assert np.linalg.norm(u1 - u2) <= 1e-9 * np.linalg.norm(u1)
+    its = lambda r: sum(info["iterations"] for info in r["linear_iterations"])
+    assert its(r2) <= its(r1)
+
+
 def test_line_search_backtracks_on_overshoot():
     # scalar problem r(u) = b - atan(u): a full Newton step from u = 3 overshoots
     b = 0.0
