@@ -304,6 +304,53 @@ def concurrent_run(dgg, workloads, torch, n_streams=8, rounds=4):
             "timing": "host wall clock over all threads (each solve ends with a host read of its residual)"}
 
 
+def puncture_compare(dgg, workloads, torch, stream, steps):
+    """The binary-puncture workload (16^3 elements, N = 6, [-20,20]^3, 884,736 DOF, mixed precision,
+    Newton to 1e-10 with linearized solves to 1e-4) with the two finest-level subdomain solvers:
+    3 GMRES iterations preconditioned by the Poisson class inverses (Laplacian approximation) and
+    the explicit inverse of every subdomain's linearized matrix, rebuilt at every Newton step."""
+    d = dgg.Domain((-20.0,) * 3, (20.0,) * 3, (16, 16, 16), 6, precision="mixed", overlap=2, problem="puncture",
+                   punctures=workloads.BINARY_PUNCTURES, stream=stream)
+    u = torch.zeros(d.n_dof, dtype=torch.float64, device="cuda")
+    out, sols = {}, {}
+    for solver in ("gmres", "inverse"):
+        opts = dgg.solve_opts(linear_tol=1e-4, subdomain_solver=solver)
+        times, reps = [], []
+        for i in range(1 + steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                u.zero_()
+                e0.record(stream)
+                rep = d.solve(None, u, TOL, opts=opts)
+                e1.record(stream)
+            e1.synchronize()
+            if i > 0:
+                times.append(e0.elapsed_time(e1))
+                reps.append(rep)
+        sols[solver] = u.clone()
+        d.profile(True)
+        with torch.cuda.stream(stream):
+            u.zero_()
+            d.solve(None, u, TOL, opts=opts)
+        stream.synchronize()
+        prof = d.profile_read()
+        d.profile(False)
+        ms = sum(times) / len(times)
+        out[solver] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "newton_steps": reps[0].newton_steps,
+                       "krylov_iterations": reps[0].iterations,
+                       "relative_residual": max(r.relative_residual for r in reps),
+                       "phases_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]}}
+        if solver == "inverse":
+            g = prof["subdomain_gemm"]
+            out[solver]["inverse_apply_GB/s"] = g["bytes"] / max(g["ms"], 1e-12) / 1e6
+    nS = d.layout.subdomain_size
+    out["per_subdomain_inverse_bytes"] = 16**3 * nS * nS * 4
+    out["solution_rel_diff"] = float((sols["inverse"] - sols["gmres"]).norm() / sols["gmres"].norm())
+    d.close()
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -502,6 +549,8 @@ def run_ours(args):
               if args.served_seconds > 0 and rank == 0 else None)
     batched = (batched_compare(dgg, workloads, args.batched, args.batched_fp64)
                if args.batched > 0 and rank == 0 else None)
+    punct = (puncture_compare(dgg, workloads, torch, stream, args.puncture_steps)
+             if args.puncture_steps > 0 and rank == 0 else None)
 
     lat = sorted(times)
     p50 = lat[len(lat) // 2]
@@ -529,6 +578,7 @@ def run_ours(args):
         "served": served,
         "batched": batched,
         "concurrent": concurrent,
+        "puncture_16cubed_N6": punct,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -552,6 +602,8 @@ def main():
                     help="also solve the headline problem on this many streams at once (0: skip)")
     ap.add_argument("--batched-fp64", type=int, default=32,
                     help="prefix of the batched stream also solved in plain FP64 for the mixed/FP64 ratio")
+    ap.add_argument("--puncture-steps", type=int, default=2,
+                    help="timed solves of the 16^3 puncture workload per subdomain solver (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

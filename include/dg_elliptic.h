@@ -118,6 +118,10 @@ typedef struct dg_solve_opts {
                                   (one search direction, three reductions per iteration; the operator is
                                   SPD for both problems): r = b - A x, z = M r,
                                   p = z - (z.A p_old / p_old.A p_old) p_old, alpha = p.r / p.A p */
+  int32_t subdomain_solver;    /* PUNCTURE, finest level: 0 GMRES on A_S + D_S preconditioned by the Poisson
+                                  class inverse (Sec. III.E's Laplacian approximation, default); 1 the
+                                  explicit inverse of every subdomain's A_S + D_S, rebuilt at every
+                                  linearization (E n_S^2 values of the smoother's precision on the device) */
 } dg_solve_opts;
 
 typedef struct dg_solve_report {
@@ -207,6 +211,14 @@ dg_status dg_dot_noalloc(int64_t n, int32_t m, const double* V, int64_t ld, cons
 dg_status dg_nonlinear_residual(struct dg_domain* dom, const double* u, const double* b, double* r, void* stream);
 /* PUNCTURE: linearize at u (Eq. linearized): dg_apply then applies A + M diag(S'(u)). NULL clears. */
 dg_status dg_set_linearization(struct dg_domain* dom, const double* u, void* stream);
+/* PUNCTURE: how the finest level's Schwarz subdomain problems (A_S + D_S) du_S = r_S of the
+ * linearized operator are solved by dg_schwarz_smooth and the V-cycle (Sec. III.E): solver 0 by
+ * `iterations` GMRES iterations (0..16; 0 applies the Poisson inverse alone) right-preconditioned
+ * by the Poisson class inverse; solver 1 by the explicit inverse of every subdomain's own A_S + D_S.
+ * Those inverses (E n_S^2 values in the smoother's precision; DG_ERR_OOM if they do not fit) are
+ * built by dg_set_linearization, or by this call when a linearization is already set.
+ * elliptic_solve sets the same state from its options. Default: solver 0, 3 iterations. */
+dg_status dg_set_subdomain_solver(struct dg_domain* dom, int32_t solver, int32_t iterations, void* stream);
 /* PUNCTURE: copy the library-computed alpha and beta at the nodes into caller-owned device buffers. */
 dg_status dg_puncture_fields(const struct dg_domain* dom, double* alpha, double* beta, void* stream);
 
@@ -234,7 +246,8 @@ enum dg_phase {
   DG_PHASE_KRYLOV = 6,      /* FGMRES vector kernels and precision conversions */
   DG_PHASE_COARSE_SMOOTH = 7, /* fused Schwarz smoothing on a coarse level (residual, subdomain
                                  solves and scatter of all steps in one launch) */
-  DG_PHASE_COUNT = 8
+  DG_PHASE_SUBDOMAIN_BUILD = 8, /* per-subdomain linearized matrices A_S + D_S and their inversion */
+  DG_PHASE_COUNT = 9
 };
 
 typedef struct dg_phase_stats {

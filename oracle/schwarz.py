@@ -232,14 +232,18 @@ def inverse_subdomain_solver(level: SchwarzLevel, diag: np.ndarray):
     """Subdomain solver for a linearized operator A_S + D_S (D_S diagonal) by the explicit inverse
     of every subdomain's own linearized matrix: Sec. III.E's explicit-inverse solver applied to the
     full linearized operator instead of its Laplacian approximation. The matrices depend on the
-    linearization point, so they are formed afresh for every linearization (here: every call)."""
+    linearization point, so they are formed afresh for every linearization: one solver object
+    per linearization, which keeps each subdomain's inverse after its first use."""
     dflat = diag.ravel()
+    inverses = {}  # per subdomain: formed on first use, kept for this linearization
 
     def solve(A_S, rS, members):
         out = np.zeros_like(rS)
         for m, e in enumerate(members):
-            D = dflat[level.subdomains[e]["glob"]]
-            out[m] = np.linalg.inv(A_S + np.diag(D)) @ rS[m]
+            if e not in inverses:
+                D = dflat[level.subdomains[e]["glob"]]
+                inverses[e] = np.linalg.inv(A_S + np.diag(D))
+            out[m] = inverses[e] @ rS[m]
         return out
 
     return solve

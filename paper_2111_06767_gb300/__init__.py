@@ -74,10 +74,13 @@ def host_coordinates(desc):
 KRYLOV = {"fgmres": 0, "fcg": 1}
 
 
+SUBDOMAIN_SOLVERS = {"gmres": 0, "inverse": 1}
+
+
 def solve_opts(max_iterations=200, precondition=2, linear_tol=1e-4, max_newton_steps=20, subdomain_iterations=3,
-               relative_to_b=False, krylov="fgmres"):
+               relative_to_b=False, krylov="fgmres", subdomain_solver="gmres"):
     return nat.dg_solve_opts(max_iterations, precondition, linear_tol, max_newton_steps, subdomain_iterations,
-                             int(relative_to_b), KRYLOV[krylov])
+                             int(relative_to_b), KRYLOV[krylov], SUBDOMAIN_SOLVERS[subdomain_solver])
 
 
 @dataclasses.dataclass
@@ -192,6 +195,9 @@ class Domain:
 
     def set_linearization(self, u, stream=None):
         check(_lib.dg_set_linearization(self._h, _ptr(u), _stream(stream)), self._h)
+
+    def set_subdomain_solver(self, solver="gmres", iterations=3, stream=None):
+        check(_lib.dg_set_subdomain_solver(self._h, SUBDOMAIN_SOLVERS[solver], iterations, _stream(stream)), self._h)
 
     def puncture_fields(self):
         a, b = self._new(), self._new()

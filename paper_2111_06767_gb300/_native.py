@@ -40,7 +40,7 @@ class dg_layout(C.Structure):
 class dg_solve_opts(C.Structure):
     _fields_ = [("max_iterations", C.c_int32), ("precondition", C.c_int32), ("linear_tol", C.c_double),
                 ("max_newton_steps", C.c_int32), ("subdomain_iterations", C.c_int32), ("relative_to_b", C.c_int32),
-                ("krylov", C.c_int32)]
+                ("krylov", C.c_int32), ("subdomain_solver", C.c_int32)]
 
 
 class dg_solve_report(C.Structure):
@@ -49,7 +49,8 @@ class dg_solve_report(C.Structure):
                 ("final_residual", C.c_double), ("relative_residual", C.c_double), ("seconds", C.c_double)]
 
 
-PHASES = ("apply_fp64", "apply_fp32", "gather", "subdomain_gemm", "scatter", "transfer", "krylov", "coarse_smooth")
+PHASES = ("apply_fp64", "apply_fp32", "gather", "subdomain_gemm", "scatter", "transfer", "krylov", "coarse_smooth",
+          "subdomain_build")
 
 
 class dg_phase_stats(C.Structure):
@@ -91,6 +92,7 @@ SIGNATURES = {
     "dg_dot_noalloc": (C.c_int, [C.c_int64, _i32, _vp, C.c_int64, _vp, _vp, _vp]),
     "dg_nonlinear_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dg_set_linearization": (C.c_int, [_vp, _vp, _vp]),
+    "dg_set_subdomain_solver": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp]),
     "dg_puncture_fields": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_copy_coordinates": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dg_layout_coordinates_host": (C.c_int, [C.POINTER(dg_domain_desc), C.POINTER(C.c_double),

@@ -25,6 +25,7 @@ int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 void puncture_residual_api(dg_domain* dom, const double* u, const double* b, double* r, cudaStream_t s);
 const char* noalloc_last_error();
 void puncture_linearize_api(dg_domain* dom, const double* u, cudaStream_t s);
+void subdomain_solver_api(dg_domain* dom, int solver, int iterations, cudaStream_t s);
 
 }  // namespace dg
 
@@ -237,6 +238,14 @@ dg_status dg_set_linearization(dg_domain* dom, const double* u, void* stream) {
   return guarded(dom, [&] {
     DG_REQUIRE(dom->desc.problem == DG_PROBLEM_PUNCTURE, "not a PUNCTURE domain");
     dg::puncture_linearize_api(dom, u, pick(dom, stream));
+  });
+}
+
+dg_status dg_set_subdomain_solver(dg_domain* dom, int32_t solver, int32_t iterations, void* stream) {
+  if (!dom) return DG_ERR_INVALID_ARG;
+  return guarded(dom, [&] {
+    DG_REQUIRE(dom->desc.problem == DG_PROBLEM_PUNCTURE, "not a PUNCTURE domain");
+    dg::subdomain_solver_api(dom, solver, iterations, pick(dom, stream));
   });
 }
 

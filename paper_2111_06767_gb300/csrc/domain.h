@@ -23,6 +23,7 @@ struct SchwarzLevel {
   double inv_scale = 1.0;          // stored inverses are built at unit element width: A_S^-1 = inv_scale x stored
   DevBuf<int> elem_of_col;         // subdomain column -> element
   DevBuf<int> col_of_elem;         // element -> subdomain column
+  DevBuf<int> class_of_col;        // subdomain column -> class
   DevBuf<int> xform_of_elem;       // orientation index 8 perm + flips (canonical -> actual frame)
   DevBuf<double> inv64;            // [n_classes][nS][nS] explicit inverses (FP64 mode)
   DevBuf<float> inv32;             // FP32 copies (mixed mode)
@@ -40,6 +41,9 @@ struct LevelWork {
   DevBuf<T> b, u, r, rS, duS;
   // puncture subdomain GMRES (finest level only)
   DevBuf<T> gV, gZ, gW, gD, gH;
+  // per-subdomain linearized inverses (finest level only): class matrices A_S at the actual
+  // element widths [n_classes][nS][nS] and the inverses of A_S + D_S [E][nS][nS]
+  DevBuf<T> linA, linv;
 };
 
 struct Level {
@@ -121,8 +125,10 @@ struct dg_domain {
   size_t bytes = 0;
   int subdomain_iterations = 3;
   dg::Profiler prof;
-  bool use_tc = false;
-  bool coarse_fused = false;  // fused cooperative smoother on coarse levels (DG_COARSE_FUSED=1 turns it on)            // subdomain GEMM on tcgen05 tensor cores (MIXED)
+  int subdomain_solver = 0;  // linearized finest-level subdomain problems: 0 GMRES, 1 per-subdomain inverses
+  bool linv_current = false; // per-subdomain inverses built for the current linearization
+  bool use_tc = false;       // subdomain GEMM on tcgen05 tensor cores (MIXED)
+  bool coarse_fused = false; // fused cooperative smoother on coarse levels (DG_COARSE_FUSED=1 turns it on)
   dg::DevBuf<int> err_flag;       // set by device code whose bounded wait gave up
   // the V-cycle replayed as one CUDA graph (fixed input/output buffers; captured on the second use)
   bool graphs = true;
@@ -132,6 +138,7 @@ struct dg_domain {
   bool vgraph_prof = false;
   int64_t vgraph_kernels = 0;  // kernels in the captured graph (counted again at every replay)
   int vgraph_m = -1;
+  int vgraph_sub = -1;
   dg::DevBuf<double> vin64, vout64;
   cudaStream_t gstream = nullptr;  // private stream the graph is captured on and replayed in
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;

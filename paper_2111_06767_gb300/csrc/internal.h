@@ -237,6 +237,14 @@ void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* 
 template <typename T>
 void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s);
 
+// Per-subdomain linearized inverses (finest level of a linearized problem): assemble
+// M_c = A_{class(c)} + diag(d_S[:, c]) (compact n_S x n_S per column), then du_S = Minv_c r_S.
+template <typename T>
+void launch_lin_assemble(const T* A, const int* class_of_col, const T* dS, int nS, int ld, int E, T* M,
+                         cudaStream_t s);
+template <typename T>
+void launch_lin_gemv(const T* Minv, const T* rS, int nS, int ld, int E, T* duS, cudaStream_t s);
+
 // Multigrid transfers (per dimension: 0 lower half, 1 upper half, 2 full).
 template <typename T>
 void launch_prolongate_add(int N, const int nf[3], const int nc[3], const T* Ilo, const T* Ihi, const T* uc, T* uf,

@@ -38,7 +38,7 @@ struct Job {
 namespace dg {
 
 // Upper bound of a domain's device footprint (bytes) before it is built.
-size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations) {
+size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations, bool linearized_inverses) {
   const int N = d.N, ov = d.overlap;
   const size_t nS = (size_t)N * N * N + 6 * (size_t)ov * N * N;
   const size_t ld = (nS + 31) / 32 * 32;
@@ -72,6 +72,10 @@ size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations) {
       if (n[i] % 2 == 0) n[i] /= 2;
   }
   const size_t ndof0 = (size_t)d.n[0] * d.n[1] * d.n[2] * N * N * N;
+  if (linearized_inverses && d.problem == DG_PROBLEM_PUNCTURE) {
+    // per-subdomain inverses of the finest level plus its class matrices (at most one per element)
+    total += 2 * (size_t)d.n[0] * d.n[1] * d.n[2] * nS * nS * fb;
+  }
   // Krylov basis: grown on demand; admission counts up to 64 iterations
   total += ndof0 * 8 * (2 * (size_t)std::min(max_iterations, 64) + 16);
   return total + build_peak + (8u << 20);
@@ -202,7 +206,8 @@ dg_status elliptic_serve_submit(dg_server* srv, const dg_request* req, uint64_t*
   if (d.N < 2 || d.N > DG_MAX_N || d.n[0] < 1 || d.n[1] < 1 || d.n[2] < 1) return DG_ERR_INVALID_ARG;
   if (d.problem == DG_PROBLEM_POISSON && !req->f_host) return DG_ERR_INVALID_ARG;
   const int max_it = req->opts.max_iterations > 0 ? req->opts.max_iterations : 200;
-  const size_t bytes = dg::estimate_domain_bytes(d, max_it);
+  if (req->opts.subdomain_solver != 0 && req->opts.subdomain_solver != 1) return DG_ERR_INVALID_ARG;
+  const size_t bytes = dg::estimate_domain_bytes(d, max_it, req->opts.subdomain_solver == 1);
   Job* job = new (std::nothrow) Job();
   if (!job) return DG_ERR_OOM;
   job->req = *req;

@@ -190,6 +190,11 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   cudaStream_t s = dom->stream;
   upload(sw.elem_of_col, elem_of_col, s);
   upload(sw.col_of_elem, sw.position, s);
+  {
+    std::vector<int> class_of_col(E);
+    for (int e = 0; e < E; ++e) class_of_col[sw.position[e]] = sw.class_of[e];
+    upload(sw.class_of_col, class_of_col, s);
+  }
   upload(sw.xform_of_elem, xform, s);
   std::vector<int4> tiles;
   for (int c = 0; c < nc; ++c)
@@ -516,13 +521,14 @@ size_t domain_device_bytes(const dg_domain* dom) {
              dom->vout64.bytes() + dom->err_flag.bytes();
   for (const auto& L : dom->levels) {
     const auto& sw = L.sw;
-    b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.xform_of_elem.bytes() + sw.inv64.bytes() +
+    b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.class_of_col.bytes() + sw.xform_of_elem.bytes() +
+         sw.inv64.bytes() +
          sw.inv32.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() + sw.units.bytes() + sw.bar.bytes();
     for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
-                    &L.w64.gH})
+                    &L.w64.gH, &L.w64.linA, &L.w64.linv})
       b += p->bytes();
     for (auto* p : {&L.w32.b, &L.w32.u, &L.w32.r, &L.w32.rS, &L.w32.duS, &L.w32.gV, &L.w32.gZ, &L.w32.gW, &L.w32.gD,
-                    &L.w32.gH})
+                    &L.w32.gH, &L.w32.linA, &L.w32.linv})
       b += p->bytes();
   }
   return b;

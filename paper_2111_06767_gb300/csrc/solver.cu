@@ -86,6 +86,14 @@ const double* lin_diag<double>(const dg_domain* dom) { return dom->lin64.get(); 
 template <>
 const float* lin_diag<float>(const dg_domain* dom) { return dom->lin32.get(); }
 
+// The finest level of a linearized problem smooths with the linearized subdomain problems
+// A_S + D_S (per-subdomain inverses, or GMRES with the Poisson inverse as preconditioner).
+template <typename T>
+bool linearized_smoother(const dg_domain* dom, int level) {
+  return level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE && lin_diag<T>(dom) != nullptr &&
+         (dom->subdomain_solver == 1 || dom->subdomain_iterations > 0);
+}
+
 template <typename T>
 void apply_T(dg_domain* dom, int level, const T* u, T* out, const T* b, cudaStream_t s,
              const SubdomainOut* so = nullptr);
@@ -167,8 +175,9 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
   DG_REQUIRE(inverses<T>(sw) != nullptr && shares<T>(dom) != nullptr,
              "Schwarz data of this precision are not built for this domain");
   if (iterations <= 0) return;
-  const bool linearized_level = level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE &&
-                                dom->subdomain_iterations > 0 && lin_diag<T>(dom) != nullptr;
+  const bool linearized_level = linearized_smoother<T>(dom, level);
+  DG_REQUIRE(!linearized_level || dom->subdomain_solver != 1 || dom->linv_current,
+             "per-subdomain linearized inverses are not built for the current linearization");
   if constexpr (std::is_same<T, float>::value) {
     if (dom->coarse_fused && L.E <= kCoarseFusedElems && !linearized_level && coarse_smooth_available(dom->N)) {
       // all steps of this call in one cooperative launch
@@ -215,8 +224,7 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     } else {
       apply_T<T>(dom, level, u, nullptr, b, s, &so);  // r = b - A u, written straight into r_S
     }
-    const bool linearized = level == 0 && dom->lin_set && dom->desc.problem == DG_PROBLEM_PUNCTURE &&
-                            dom->subdomain_iterations > 0 && lin_diag<T>(dom) != nullptr;
+    const bool linearized = linearized_level;
     auto gemm = [&](const T* X, T* Y) {
       PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * sz + 2 * vec,
                     2.0 * sw.nS * (double)sw.nS * L.E);
@@ -224,6 +232,11 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     };
     if (!linearized) {
       gemm(W.rS.get(), W.duS.get());
+    } else if (dom->subdomain_solver == 1) {
+      // du_S = (A_S + D_S)^-1 r_S with every subdomain's own inverse (built at the linearization)
+      PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)L.E * sw.nS * sw.nS * sz + 2 * vec,
+                    2.0 * sw.nS * (double)sw.nS * L.E);
+      launch_lin_gemv<T>(W.linv.get(), W.rS.get(), sw.nS, ld, L.E, W.duS.get(), s);
     } else {
       // GMRES on (A_S + D_S), right-preconditioned by the Poisson inverse A_S^-1 (Sec. III.E)
       const int m = dom->subdomain_iterations;
@@ -306,8 +319,10 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
   };
   const bool lin = dom->lin_set;
   const int m = dom->subdomain_iterations;
+  const int sub = dom->subdomain_solver;
   const bool prof = dom->prof.on;
-  if (dom->vgraph && (dom->vgraph_lin != lin || dom->vgraph_m != m || dom->vgraph_prof != prof)) {
+  if (dom->vgraph &&
+      (dom->vgraph_lin != lin || dom->vgraph_m != m || dom->vgraph_sub != sub || dom->vgraph_prof != prof)) {
     // different kernels: drop the graph and run once uncaptured (it may allocate) before re-capturing
     cudaGraphExecDestroy(dom->vgraph);
     dom->vgraph = nullptr;
@@ -354,6 +369,7 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
     DG_CUDA(e);
     dom->vgraph_lin = lin;
     dom->vgraph_m = m;
+    dom->vgraph_sub = sub;
     dom->vgraph_prof = prof;
   }
   DG_CUDA(cudaGraphLaunch(dom->vgraph, gs));
@@ -599,10 +615,54 @@ LinearResult fcg(dg_domain* dom, const double* b, double* x, double tol, double 
   return R;
 }
 
+// Inverses of A_S + D_S for every finest-level subdomain at the current linearization: the class
+// matrices A_S at the actual element widths (built once), d_S = R_S (M S'(u)) gathered into the
+// subdomain columns, M_c = A_S + diag(d_S) per column, then batched in-place Gauss-Jordan.
+template <typename T>
+void build_linearized_inverses(dg_domain* dom, cudaStream_t s) {
+  ensure_schwarz(dom, 0);
+  Level& L = dom->levels[0];
+  SchwarzLevel& sw = L.sw;
+  LevelWork<T>& W = work<T>(L);
+  const int nS = sw.nS, ld = sw.ld, E = L.E, nc = sw.n_classes, N = dom->N;
+  const size_t n2 = (size_t)nS * nS;
+  const T* Dt;
+  const T* wt;
+  if constexpr (std::is_same<T, float>::value) { Dt = dom->D32.get(); wt = dom->w32.get(); }
+  else { Dt = dom->D64.get(); wt = dom->w64.get(); }
+  if (!W.linA.get()) {
+    DevBuf<int> d_patch(sw.patch.size());
+    DG_CUDA(cudaMemcpyAsync(d_patch.get(), sw.patch.data(), sizeof(int) * sw.patch.size(), cudaMemcpyHostToDevice, s));
+    const OpGeom<T> g = make_geom<T>(L.n, L.h, N, dom->desc.penalty, dom->lgl);
+    W.linA.alloc((size_t)nc * n2);
+    launch_build_subdomain_matrices<T>(N, dom->desc.overlap, g, Dt, wt, d_patch.get(), nc, nS, W.linA.get(), s);
+    DG_CUDA(cudaStreamSynchronize(s));
+  }
+  if (W.linv.count < (size_t)E * n2) W.linv.alloc((size_t)E * n2);
+  if (W.gD.count < (size_t)E * ld) W.gD.alloc((size_t)E * ld);
+  const double sz = sizeof(T);
+  PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_BUILD, s, 3.0 * E * n2 * sz, 2.0 * E * (double)n2 * nS);
+  launch_gather_tab<T>(sw.geom, lin_diag<T>(dom), sw.elem_of_col.get(), sw.xform_of_elem.get(), dom->orient_map.get(),
+                       W.gD.get(), s);
+  launch_lin_assemble<T>(W.linA.get(), sw.class_of_col.get(), W.gD.get(), nS, ld, E, W.linv.get(), s);
+  constexpr int kMaxBatch = 65535;  // grid z limit of the Gauss-Jordan update kernel
+  for (int c0 = 0; c0 < E; c0 += kMaxBatch)
+    launch_invert_spd_batched<T>(W.linv.get() + (size_t)c0 * n2, nS, std::min(kMaxBatch, E - c0), s);
+}
+
+void build_linearized(dg_domain* dom, cudaStream_t s) {
+  dom->linv_current = false;
+  if (dom->mixed) build_linearized_inverses<float>(dom, s);
+  else build_linearized_inverses<double>(dom, s);
+  dom->linv_current = true;
+}
+
 void set_linearization(dg_domain* dom, const double* u, cudaStream_t s) {
   launch_puncture_linearization(dom->levels[0].ndof, u, dom->mass.get(), dom->alpha.get(), dom->beta.get(),
                                 dom->lin64.get(), dom->lin32.get(), s);
   dom->lin_set = true;
+  dom->linv_current = false;
+  if (dom->subdomain_solver == 1) build_linearized(dom, s);
 }
 
 // r = b - A(u)
@@ -622,8 +682,15 @@ void puncture_residual_api(dg_domain* dom, const double* u, const double* b, dou
   nonlinear_residual(dom, u, b, r, s);
 }
 void puncture_linearize_api(dg_domain* dom, const double* u, cudaStream_t s) {
-  if (!u) { dom->lin_set = false; return; }
+  if (!u) { dom->lin_set = false; dom->linv_current = false; return; }
   set_linearization(dom, u, s);
+}
+void subdomain_solver_api(dg_domain* dom, int solver, int iterations, cudaStream_t s) {
+  DG_REQUIRE(solver == 0 || solver == 1, "subdomain solver must be 0 (GMRES) or 1 (per-subdomain inverses)");
+  DG_REQUIRE(iterations >= 0 && iterations <= 16, "subdomain_iterations must be in [0, 16]");
+  dom->subdomain_solver = solver;
+  dom->subdomain_iterations = iterations;
+  if (solver == 1 && dom->lin_set && !dom->linv_current) build_linearized(dom, s);
 }
 
 dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg_solve_opts& o, dg_solve_report* rep) {
@@ -653,8 +720,10 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
     const double c = 1e-4;
     const double lin_tol = o.linear_tol > 0 ? o.linear_tol : 1e-4;
     const int max_steps = o.max_newton_steps > 0 ? o.max_newton_steps : 20;
+    DG_REQUIRE(o.subdomain_solver == 0 || o.subdomain_solver == 1, "subdomain_solver must be 0 or 1");
     dom->subdomain_iterations = o.subdomain_iterations >= 0 ? o.subdomain_iterations : 3;
     DG_REQUIRE(dom->subdomain_iterations <= 16, "subdomain_iterations must be at most 16");
+    dom->subdomain_solver = o.subdomain_solver;
     double* r = dom->rt.get();
     nonlinear_residual(dom, u, b, r, s);
     double rn = norm2(dom, r, s);
@@ -692,6 +761,7 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
       if (!std::isfinite(rn)) R.status = DG_ERR_BREAKDOWN;
     }
     dom->lin_set = false;
+    dom->linv_current = false;
     R.newton_steps = step;
     R.final_residual = rn;
     R.relative_residual = ref > 0 ? rn / ref : 0.0;
