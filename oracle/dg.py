@@ -61,6 +61,12 @@ class ElementGraph:
     def n_elements(self) -> int:
         return self.h.shape[0]
 
+    per_element = False  # one operator per neighbour pattern (uniform affine elements)
+
+    def subgraph(self, slots, pn):
+        """The elements `slots` with the face connectivity pn (a Schwarz patch)."""
+        return ElementGraph(self.N, self.penalty, self.h[slots], pn, self.h_ext[slots])
+
 
 @dataclasses.dataclass
 class BoxGrid:
@@ -103,6 +109,10 @@ class BoxGrid:
         nbr = np.array([[self.neighbor(e, f) for f in range(6)] for e in range(E)], dtype=np.int64)
         h_ext = np.repeat(h, 2, axis=1)
         return ElementGraph(self.N, self.penalty, h, nbr, h_ext)
+
+    def coarsen(self, coarse_n):
+        """The grid of the next multigrid level, with coarse_n elements per dimension."""
+        return BoxGrid(self.lower, self.upper, tuple(coarse_n), self.N, self.penalty, self.neumann)
 
     def coordinates(self):
         """Physical coordinates (x, y, z) of every node, each shaped (E, N, N, N)."""
@@ -157,6 +167,8 @@ def operators(N):
 
 def apply(graph: ElementGraph, u: np.ndarray, dirichlet_value: float = 0.0) -> np.ndarray:
     """A u for nodal data u[..., E, N, N, N] (Eqs. dg_op_auxvars and dg_op_primal)."""
+    if hasattr(graph, "apply_operator"):  # curved elements (oracle.curved)
+        return graph.apply_operator(u)
     N = graph.N
     E = graph.n_elements
     u = np.asarray(u, dtype=np.float64)
@@ -233,6 +245,8 @@ def apply(graph: ElementGraph, u: np.ndarray, dirichlet_value: float = 0.0) -> n
 
 def mass_diag(graph: ElementGraph) -> np.ndarray:
     """Diagonal of the LGL mass matrix M (Eq. massmat), shaped (E, N, N, N)."""
+    if hasattr(graph, "mass"):  # curved elements (oracle.curved)
+        return graph.mass()
     _, _, _, mass, _ = operators(graph.N)
     m1 = np.diag(mass)
     W3 = m1[:, None, None] * m1[None, :, None] * m1[None, None, :]

@@ -26,7 +26,7 @@ def hierarchy(grid: dg.BoxGrid, max_levels: int = 0):
         if all(c % 2 for c in n):
             break
         coarse_n = tuple(c // 2 if c % 2 == 0 else c for c in n)
-        levels.append(dg.BoxGrid(grid.lower, grid.upper, coarse_n, grid.N, grid.penalty, grid.neumann))
+        levels.append(levels[-1].coarsen(coarse_n))
     return levels
 
 

@@ -134,7 +134,7 @@ class SchwarzLevel:
                     pn[s, f] = q
                 elif q in slot_of:
                     pn[s, f] = slot_of[q]
-        patch = dg.ElementGraph(N, self.graph.penalty, self.graph.h[slots], pn, self.graph.h_ext[slots])
+        patch = self.graph.subgraph(slots, pn)
         # points of S: all of the centre, then N_overlap layers of each face neighbour
         glob, local, weight = [], [], []
         kk, jj, ii = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
@@ -160,6 +160,8 @@ class SchwarzLevel:
                     weight.append(self.shares[q, k, j, i, 1 + f_back])
             s += 1
         key = (tuple(map(tuple, pn.tolist())),)
+        if self.graph.per_element:  # curved elements: every subdomain has its own operator
+            key = key + (e,)
         return {
             "slots": slots,
             "patch": patch,
