@@ -84,6 +84,13 @@ typedef struct dg_domain_desc {
                              Neumann condition n.grad u = 0 of Eq. bc (interior auxiliary flux, zero
                              prescribed normal flux) instead of homogeneous Dirichlet; at least one
                              face must stay Dirichlet (the pure Neumann operator is singular) */
+  const double* node_xyz; /* NULL: the affine box. Otherwise curved (mapped) elements (POISSON only): host
+                             pointer to 3 n_dof doubles, the physical x, then y, then z coordinates of every
+                             LGL node in the element-major layout, each element mapped isoparametrically
+                             (Sec. II with the metric terms of Eqs. massmat, stiffmat, liftop); read only
+                             during dg_domain_create. Shared face nodes must coincide; a folded or
+                             left-handed element is DG_ERR_INVALID_ARG. Every subdomain then has its own
+                             explicit inverse (E n_S^2 values per level) */
 } dg_domain_desc;
 
 enum dg_subdomain_gemm {

@@ -53,6 +53,9 @@ struct Level {
   double h[3] = {0, 0, 0};
   OpGeom<double> g64{};
   OpGeom<float> g32{};
+  // curved elements: metric, face-node penalty, face-node normal fluxes (scratch of every apply)
+  DevBuf<double> geo64, sig64, trace64;
+  DevBuf<float> geo32, sig32, trace32;
   SchwarzLevel sw;
   LevelWork<double> w64;
   LevelWork<float> w32;
@@ -105,6 +108,7 @@ struct dg_domain {
   std::string err;
   int N = 0;
   bool mixed = false;
+  bool curved = false;  // mapped elements (node coordinates given at creation)
   dg::LglTables lgl;
   dg::DevBuf<double> D64, w64, Ilo64, Ihi64, x1;
   dg::DevBuf<float> D32, w32, Ilo32, Ihi32;

@@ -237,6 +237,37 @@ void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* 
 template <typename T>
 void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s);
 
+// Curved (mapped) elements: metric [10][ndof] (J, then G^j_i = dxi^j/dx^i at 1 + 3 j + i), penalty
+// at every face node [E][6][N^2], outward normal fluxes of u at every face node [E][6][N^2].
+template <typename T>
+struct CurvedArgs {
+  int n[3];
+  int neumann;
+  int64_t ndof;
+  const T* geo;
+  const T* sigma;
+  const T* D;
+  const T* w;
+  const T* u;
+  const T* b;
+  T* out;
+  T* trace;
+};
+// out = A u (or b - A u): the trace pass, then the operator pass.
+template <typename T>
+void launch_curved_apply(int N, const CurvedArgs<T>& a, int E, cudaStream_t s);
+// Row-major subdomain matrices A_S of subdomains e0 .. e0 + count - 1 into A_out.
+template <typename T>
+void launch_curved_columns(int N, const CurvedArgs<T>& a, int ov, int nS, int e0, int count, T* A_out,
+                           cudaStream_t s);
+void launch_curved_metric(int N, int64_t E, const double* xyz, const double* D, double* geo64, float* geo32, int* bad,
+                          cudaStream_t s);
+void launch_curved_sigma(int N, const int n[3], double penalty, const double* geo64, double* sig64, float* sig32,
+                         cudaStream_t s);
+void launch_curved_coarsen(int N, const int cn[3], const int fn[3], const double* C, const double* fine_xyz,
+                           double* coarse_xyz, cudaStream_t s);
+void launch_curved_mass(int N, const double* w, const double* geo64, int64_t ndof, double* mass, cudaStream_t s);
+
 // Per-subdomain linearized inverses (finest level of a linearized problem): assemble
 // M_c = A_{class(c)} + diag(d_S[:, c]) (compact n_S x n_S per column), then du_S = Minv_c r_S.
 template <typename T>

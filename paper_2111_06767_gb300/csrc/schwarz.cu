@@ -36,28 +36,6 @@ namespace dg {
 constexpr int kPatchInts = 49;
 
 template <int N>
-__device__ __forceinline__ int node_of(int d, int idx_d, int a1, int a2) {
-  int c0, c1, c2;
-  if (d == 0) { c0 = idx_d; c1 = a1; c2 = a2; }
-  else if (d == 1) { c0 = a1; c1 = idx_d; c2 = a2; }
-  else { c0 = a1; c1 = a2; c2 = idx_d; }
-  return (c2 * N + c1) * N + c0;
-}
-
-// Subdomain row of point p of slot s, or -1 if outside S.
-template <int N>
-__device__ __forceinline__ int subdomain_row(int s, int p, int ov) {
-  if (s == 0) return p;
-  const int f = s - 1, d = f >> 1, side = f & 1;
-  const int c[3] = {p % N, (p / N) % N, p / (N * N)};
-  const int depth = side ? c[d] : N - 1 - c[d];
-  if (depth >= ov) return -1;
-  const int a1 = d == 0 ? c[1] : c[0];
-  const int a2 = d == 2 ? c[1] : c[2];
-  return N * N * N + f * ov * N * N + (depth * N + a2) * N + a1;
-}
-
-template <int N>
 struct ColumnShape {
   static constexpr int n3 = N * N * N;
   static constexpr int threads = n3 > 512 ? 512 : n3;

@@ -132,6 +132,10 @@ void classify_schwarz(dg_domain* dom, Level& L) {
     while (!(kPerms[pi][0] == perm[0] && kPerms[pi][1] == perm[1] && kPerms[pi][2] == perm[2])) ++pi;
     key[e] = k;
     xform[e] = pi * 8 + fl;
+    if (dom->curved) {  // mapped elements: every subdomain is its own class, in its own orientation
+      key[e] = e;
+      xform[e] = 0;
+    }
   }
   std::map<int, int> cls_id;
   for (int e = 0; e < E; ++e) cls_id.emplace(key[e], 0);
@@ -162,6 +166,7 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   // canonical patch of every class (slot 0 centre, 1 + f neighbour across canonical face f)
   sw.patch.assign((size_t)nc * 49, -2);
   for (auto& kv : cls_id) {
+    if (dom->curved) break;  // curved subdomain matrices are built from the grid itself
     int codes[3][2];  // [canonical axis][side]
     int k = kv.first;
     for (int a = 2; a >= 0; --a) {
@@ -197,21 +202,21 @@ void classify_schwarz(dg_domain* dom, Level& L) {
   }
   upload(sw.xform_of_elem, xform, s);
   std::vector<int4> tiles;
-  for (int c = 0; c < nc; ++c)
+  for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 64)
       for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
         tiles.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles = (int)tiles.size();
   upload(sw.tiles, tiles, s);
   std::vector<int4> tiles_tc;
-  for (int c = 0; c < nc; ++c)
+  for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 128)
       for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
         tiles_tc.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles_tc = (int)tiles_tc.size();
   upload(sw.tiles_tc, tiles_tc, s);
   std::vector<int4> units;
-  for (int c = 0; c < nc; ++c)
+  for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 16) units.push_back(make_int4(c, r0, sw.class_first[c], sw.class_count[c]));
   sw.n_units = (int)units.size();
   upload(sw.units, units, s);
@@ -302,6 +307,66 @@ void alloc_work(LevelWork<T>& w, const Level& L, cudaStream_t s) {
 
 }  // namespace
 
+// Curved elements: the level-0 node coordinates from the caller, the coarse levels' nodes on the
+// interpolated fine map (per coarsened dimension the coarse node xi_c lies in the lower child,
+// xi_c <= 0, at child coordinate 2 xi_c + 1, or in the upper one at 2 xi_c - 1), then per level the
+// nodal metric and the face-node penalty; the mass diagonal w_p J_p of level 0.
+void setup_curved_geometry(dg_domain* dom, const double* host_xyz) {
+  const int N = dom->N;
+  cudaStream_t s = dom->stream;
+  const LglTables& t = dom->lgl;
+  const Level& L0 = dom->levels[0];
+  const size_t n0 = (size_t)L0.ndof;
+  DevBuf<double> xyz(3 * n0);
+  DG_CUDA(cudaMemcpyAsync(xyz.get(), host_xyz, 3 * n0 * sizeof(double), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(dom->X.get(), xyz.get(), n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(dom->Y.get(), xyz.get() + n0, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(dom->Z.get(), xyz.get() + 2 * n0, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // coarsening weights: [lower child][c][q], [upper child][c][q], identity, upper-half flag per node
+  std::vector<double> C(3 * N * N + N, 0.0);
+  auto lagrange = [&](int q, double x) {
+    double v = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != q) v *= (x - t.x[m]) / (t.x[q] - t.x[m]);
+    return v;
+  };
+  for (int c = 0; c < N; ++c) {
+    const bool upper = t.x[c] > 0.0;
+    for (int q = 0; q < N; ++q) {
+      C[(upper ? N * N : 0) + c * N + q] = lagrange(q, upper ? 2.0 * t.x[c] - 1.0 : 2.0 * t.x[c] + 1.0);
+      C[2 * N * N + c * N + q] = c == q ? 1.0 : 0.0;
+    }
+    C[3 * N * N + c] = upper ? 1.0 : 0.0;
+  }
+  DevBuf<double> dC;
+  upload(dC, C, s);
+  DevBuf<int> bad(1);
+  DG_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+  DevBuf<double> cur = std::move(xyz);
+  for (size_t l = 0; l < dom->levels.size(); ++l) {
+    Level& L = dom->levels[l];
+    if (l > 0) {
+      DevBuf<double> next(3 * (size_t)L.ndof);
+      launch_curved_coarsen(N, L.n, dom->levels[l - 1].n, dC.get(), cur.get(), next.get(), s);
+      cur = std::move(next);
+    }
+    L.geo64.alloc(10 * (size_t)L.ndof);
+    L.geo32.alloc(10 * (size_t)L.ndof);
+    launch_curved_metric(N, L.E, cur.get(), dom->D64.get(), L.geo64.get(), L.geo32.get(), bad.get(), s);
+    const size_t nf = (size_t)L.E * 6 * N * N;
+    L.sig64.alloc(nf);
+    L.sig32.alloc(nf);
+    launch_curved_sigma(N, L.n, dom->desc.penalty, L.geo64.get(), L.sig64.get(), L.sig32.get(), s);
+    L.trace32.alloc(nf);
+    L.trace64.alloc(nf);
+  }
+  launch_curved_mass(N, dom->w64.get(), L0.geo64.get(), L0.ndof, dom->mass.get(), s);
+  int h_bad = 0;
+  DG_CUDA(cudaMemcpyAsync(&h_bad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  DG_REQUIRE(!h_bad, "node coordinates give a folded or left-handed element (Jacobian determinant <= 0)");
+}
+
 void domain_setup(dg_domain* dom) {
   const dg_domain_desc& d = dom->desc;
   DG_REQUIRE(d.N >= 2 && d.N <= DG_MAX_N, "N must be in [2, 10]");
@@ -322,14 +387,16 @@ void domain_setup(dg_domain* dom) {
              "tensor-core subdomain GEMM needs a MIXED domain");
   DG_REQUIRE(d.problem != DG_PROBLEM_PUNCTURE || (d.n_punctures >= 0 && d.n_punctures <= DG_MAX_PUNCTURES),
              "bad puncture count");
+  DG_REQUIRE(!d.node_xyz || d.problem == DG_PROBLEM_POISSON, "curved elements are supported for POISSON only");
   const int64_t ndof = (int64_t)d.n[0] * d.n[1] * d.n[2] * d.N * d.N * d.N;
   DG_REQUIRE(ndof < (int64_t)1 << 31, "problem too large for 32-bit point indices");
   dom->N = d.N;
   dom->mixed = d.precision == DG_PRECISION_MIXED;
+  dom->curved = d.node_xyz != nullptr;
   dom->use_tc = dom->mixed && d.subdomain_gemm != DG_GEMM_SIMT;
   {
     const char* v = std::getenv("DG_COARSE_FUSED");
-    dom->coarse_fused = v && std::strcmp(v, "1") == 0;
+    dom->coarse_fused = v && std::strcmp(v, "1") == 0 && !dom->curved;
   }
   if (dom->use_tc && !tc_gemm_available()) {
     DG_REQUIRE(d.subdomain_gemm != DG_GEMM_TENSOR_TF32, "tensor-core GEMM requested but TMA encoding is unavailable");
@@ -374,9 +441,14 @@ void domain_setup(dg_domain* dom) {
   dom->X.alloc(L0.ndof);
   dom->Y.alloc(L0.ndof);
   dom->Z.alloc(L0.ndof);
-  launch_node_coords(N, L0.n, d.lower, L0.h, dom->x1.get(), dom->X.get(), dom->Y.get(), dom->Z.get(), s);
   dom->mass.alloc(L0.ndof);
-  launch_mass_diag<double>(N, L0.g64, dom->w64.get(), L0.ndof, dom->mass.get(), s);
+  if (dom->curved) {
+    setup_curved_geometry(dom, d.node_xyz);
+    dom->desc.node_xyz = nullptr;  // the caller's buffer is not kept
+  } else {
+    launch_node_coords(N, L0.n, d.lower, L0.h, dom->x1.get(), dom->X.get(), dom->Y.get(), dom->Z.get(), s);
+    launch_mass_diag<double>(N, L0.g64, dom->w64.get(), L0.ndof, dom->mass.get(), s);
+  }
   for (auto& L : dom->levels) classify_schwarz(dom, L);
   build_shares(dom);
   build_orientation_tables(dom);
@@ -416,12 +488,55 @@ size_t g_inv_bytes = 0;
 
 }  // namespace
 
+namespace {
+// Curved elements: the explicit inverse of every subdomain's own A_S (row-major, compact n_S x n_S),
+// built column by column from the curved operator on its patch, inverted in place by Gauss-Jordan
+// without pivoting (the symmetric part of A_S is positive definite, so no pivot vanishes).
+template <typename T>
+void build_curved_inverses(dg_domain* dom, Level& L, DevBuf<T>& inv, const T* geo, const T* sig, const T* D,
+                           const T* w, cudaStream_t s) {
+  const int nS = L.sw.nS, E = L.E;
+  const size_t n2 = (size_t)nS * nS;
+  inv.alloc((size_t)E * n2);
+  CurvedArgs<T> a{};
+  for (int i = 0; i < 3; ++i) a.n[i] = L.n[i];
+  a.neumann = dom->desc.neumann_faces;
+  a.ndof = L.ndof;
+  a.geo = geo;
+  a.sigma = sig;
+  a.D = D;
+  a.w = w;
+  constexpr int kBatch = 65535;  // grid limits of the column and Gauss-Jordan launches
+  for (int e0 = 0; e0 < E; e0 += kBatch) {
+    const int cnt = std::min(kBatch, E - e0);
+    launch_curved_columns<T>(dom->N, a, dom->desc.overlap, nS, e0, cnt, inv.get() + (size_t)e0 * n2, s);
+    launch_invert_spd_batched<T>(inv.get() + (size_t)e0 * n2, nS, cnt, s);
+  }
+}
+}  // namespace
+
 // Explicit inverses and work vectors of one level, built on first use (Sec. III.E: construction
 // cost amortised over all later solves).
 void ensure_schwarz(dg_domain* dom, int level) {
   Level& L = dom->levels[level];
   SchwarzLevel& sw = L.sw;
   if (sw.built) return;
+  if (dom->curved) {
+    cudaStream_t s = dom->stream;
+    sw.inv_scale = 1.0;
+    if (dom->mixed) {
+      build_curved_inverses<float>(dom, L, sw.inv32, L.geo32.get(), L.sig32.get(), dom->D32.get(), dom->w32.get(), s);
+      alloc_work(L.w32, L, s);
+    } else {
+      build_curved_inverses<double>(dom, L, sw.inv64, L.geo64.get(), L.sig64.get(), dom->D64.get(), dom->w64.get(),
+                                    s);
+      alloc_work(L.w64, L, s);
+    }
+    DG_CUDA(cudaStreamSynchronize(s));
+    sw.built = true;
+    dom->bytes = domain_device_bytes(dom);
+    return;
+  }
   const int N = dom->N, ov = dom->desc.overlap, nS = sw.nS, nc = sw.n_classes;
   cudaStream_t s = dom->stream;
   DG_CUDA(cudaStreamSynchronize(s));
@@ -521,6 +636,8 @@ size_t domain_device_bytes(const dg_domain* dom) {
              dom->vout64.bytes() + dom->err_flag.bytes();
   for (const auto& L : dom->levels) {
     const auto& sw = L.sw;
+    b += L.geo64.bytes() + L.geo32.bytes() + L.sig64.bytes() + L.sig32.bytes() + L.trace64.bytes() +
+         L.trace32.bytes();
     b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.class_of_col.bytes() + sw.xform_of_elem.bytes() +
          sw.inv64.bytes() +
          sw.inv32.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() + sw.units.bytes() + sw.bar.bytes();

@@ -34,9 +34,41 @@ int apply_variant(dg_domain* dom, Level& L, bool fused, const std::function<void
 }
 }  // namespace
 
+namespace {
+// Curved elements: out = A u (or b - A u); into the subdomain vectors through the level's residual
+// buffer and a gather.
+template <typename T>
+void curved_apply(dg_domain* dom, Level& L, const T* u, T* out, const T* b, cudaStream_t s, const SubdomainOut* so,
+                  const T* geo, const T* sig, T* trace, const T* D, const T* w, T* r_scratch) {
+  CurvedArgs<T> a{};
+  for (int i = 0; i < 3; ++i) a.n[i] = L.n[i];
+  a.neumann = dom->desc.neumann_faces;
+  a.ndof = L.ndof;
+  a.geo = geo;
+  a.sigma = sig;
+  a.D = D;
+  a.w = w;
+  a.u = u;
+  a.b = b;
+  a.trace = trace;
+  a.out = so ? r_scratch : out;
+  DG_REQUIRE(a.out != nullptr, "curved residual needs the level's work vectors");
+  launch_curved_apply<T>(dom->N, a, L.E, s);
+  if (so)
+    launch_gather_tab<T>(L.sw.geom, a.out, L.sw.elem_of_col.get(), L.sw.xform_of_elem.get(), dom->orient_map.get(),
+                         static_cast<T*>(so->rS), s);
+}
+}  // namespace
+
 void apply_level(dg_domain* dom, int level, const double* u, double* out, const double* b, bool with_lin,
                  cudaStream_t s, const SubdomainOut* so) {
   Level& L = dom->levels[level];
+  if (dom->curved) {
+    PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP64, s, (double)L.ndof * 8 * (b ? 3 : 2) + 80.0 * L.ndof, 0.0);
+    curved_apply<double>(dom, L, u, out, b, s, so, L.geo64.get(), L.sig64.get(), L.trace64.get(), dom->D64.get(),
+                         dom->w64.get(), L.w64.r.get());
+    return;
+  }
   const double* diag = (with_lin && level == 0 && dom->lin_set) ? dom->lin64.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP64, s, apply_bytes(L.ndof, 8, b, diag), apply_flops(L.ndof, dom->N));
   auto run = [&](int v) {
@@ -48,6 +80,12 @@ void apply_level(dg_domain* dom, int level, const double* u, double* out, const 
 void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, const float* b, bool with_lin,
                      cudaStream_t s, const SubdomainOut* so) {
   Level& L = dom->levels[level];
+  if (dom->curved) {
+    PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP32, s, (double)L.ndof * 4 * (b ? 3 : 2) + 40.0 * L.ndof, 0.0);
+    curved_apply<float>(dom, L, u, out, b, s, so, L.geo32.get(), L.sig32.get(), L.trace32.get(), dom->D32.get(),
+                        dom->w32.get(), L.w32.r.get());
+    return;
+  }
   const float* diag = (with_lin && level == 0 && dom->lin_set && dom->lin32.get()) ? dom->lin32.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP32, s, apply_bytes(L.ndof, 4, b, diag), apply_flops(L.ndof, dom->N));
   auto run = [&](int v) {
@@ -134,11 +172,19 @@ void class_gemm(dg_domain* dom, Level& L, const T* X, T* Y, cudaStream_t s);
 template <>
 void class_gemm<double>(dg_domain* dom, Level& L, const double* X, double* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
+  if (dom->curved) {  // one inverse per subdomain
+    launch_lin_gemv<double>(sw.inv64.get(), X, sw.nS, sw.ld, L.E, Y, s);
+    return;
+  }
   launch_class_gemm_tiles<double>(sw.inv64.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, sw.inv_scale, s);
 }
 template <>
 void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
+  if (dom->curved) {  // one inverse per subdomain
+    launch_lin_gemv<float>(sw.inv32.get(), X, sw.nS, sw.ld, L.E, Y, s);
+    return;
+  }
   if (dom->use_tc) {
     auto run = [&](int split) {
       launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, sw.tiles_tc.get(), sw.n_tiles_tc,
@@ -701,6 +747,7 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
   const int pmode = o.precondition;
   DG_REQUIRE(pmode >= 0 && pmode <= 2, "precondition must be 0, 1 or 2");
   DG_REQUIRE(o.krylov == 0 || o.krylov == 1, "krylov must be 0 (FGMRES) or 1 (flexible CG)");
+  DG_REQUIRE(!dom->curved || o.krylov == 0, "flexible CG needs a symmetric operator; curved elements are not");
   DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
   ensure_workspace(dom, std::min(max_it, 16));
   dg_solve_report R{};
