@@ -351,6 +351,79 @@ def puncture_compare(dgg, workloads, torch, stream, steps):
     return out
 
 
+def warp_map(X, Y, Z):
+    """Smooth warp of [-1,1]^3 that keeps the six faces planar (curved interior elements)."""
+    return (X + 0.1 * (1 - X**2) * Y, Y + 0.12 * (1 - Y**2) * Z * X, Z + 0.1 * (1 - Z**2) * (X + Y))
+
+
+def curved_compare(dgg, workloads, torch, stream, steps):
+    """The Gaussian workload (8^3 elements, N = 8, 3 levels) on a warped mesh of curved elements:
+    set-up (metric, 584 per-subdomain inverses), solves/s in mixed precision and FP64, and the
+    curved DG apply rate at the workload size and at 64^3 elements, N = 4 (16.8M DOF)."""
+    out = {}
+    desc = dgg.make_desc((-1.0,) * 3, (1.0,) * 3, n_CFG, N_CFG)
+    xyz = warp_map(*dgg.host_coordinates(desc))
+    src = workloads.gaussian_source(2)
+    for prec in ("mixed", "fp64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            d = dgg.Domain(n=n_CFG, N=N_CFG, precision=prec, mg_levels=LEVELS, overlap=2, stream=stream, node_xyz=xyz)
+            x, y, z = d.coordinates()
+            b = d.rhs(src(x, y, z).contiguous(), stream=stream)
+            u = torch.zeros_like(b)
+            rep = d.solve(b, u, TOL)  # builds the per-subdomain inverses of every level
+        stream.synchronize()
+        setup_s = time.perf_counter() - t0
+        k = steps if prec == "mixed" else 1
+        times = []
+        for i in range(k):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                u.zero_()
+                e0.record(stream)
+                rep = d.solve(b, u, TOL)
+                e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": rep.iterations,
+                     "relative_residual": rep.relative_residual, "first_solve_with_setup_s": setup_s,
+                     "device_bytes": d.layout.device_bytes}
+        d.close()
+    # apply rates: the operator reads u and the metric (J and 9 G entries per node) and writes A u
+    def rate(dom, prec, reps):
+        n = dom.n_dof
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        uu = torch.empty(n, dtype=dt, device="cuda").uniform_(-1, 1)
+        o = torch.empty_like(uu)
+        fn = (lambda: dom.apply(uu, o, stream=stream)) if prec == "fp64" else (
+            lambda: dom.apply_f32(uu, 0, o, stream=stream))
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        e1.synchronize()
+        return n / (e0.elapsed_time(e1) / 1e3 / reps) / 1e9
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    for name, n, N in (("config_8cubed_N8", n_CFG, N_CFG), ("roofline_size_64cubed_N4", (64, 64, 64), 4)):
+        dsc = dgg.make_desc((-1.0,) * 3, (1.0,) * 3, n, N)
+        with torch.cuda.stream(stream):
+            dom = dgg.Domain(n=n, N=N, mg_levels=1, overlap=1, precision="mixed", stream=stream,
+                             node_xyz=warp_map(*dgg.host_coordinates(dsc)))
+        g64, g32 = rate(dom, "fp64", 5), rate(dom, "fp32", 10)
+        out[f"apply_{name}"] = {"dof": dom.n_dof, "fp64_gdofs": g64, "fp32_gdofs": g32,
+                                "fp64_hbm_frac": 96.0 * g64 / hbm, "fp32_hbm_frac": 48.0 * g32 / hbm,
+                                "algorithmic_bytes_per_dof": {"fp64": 96, "fp32": 48}}
+        dom.close()
+    return out
+
+
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "subdomain_gemm_traffic_poisson-gauss16-8x8x8-N8.md")
 GEMM_SOURCES = ("tc_gemm.cu",)
 
@@ -579,6 +652,8 @@ def run_ours(args):
                if args.batched > 0 and rank == 0 else None)
     punct = (puncture_compare(dgg, workloads, torch, stream, args.puncture_steps)
              if args.puncture_steps > 0 and rank == 0 else None)
+    curv = (curved_compare(dgg, workloads, torch, stream, args.curved_steps)
+            if args.curved_steps > 0 and rank == 0 else None)
 
     lat = sorted(times)
     p50 = lat[len(lat) // 2]
@@ -607,6 +682,7 @@ def run_ours(args):
         "batched": batched,
         "concurrent": concurrent,
         "puncture_16cubed_N6": punct,
+        "curved_warped_8cubed_N8": curv,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -632,6 +708,8 @@ def main():
                     help="prefix of the batched stream also solved in plain FP64 for the mixed/FP64 ratio")
     ap.add_argument("--puncture-steps", type=int, default=2,
                     help="timed solves of the 16^3 puncture workload per subdomain solver (0: skip)")
+    ap.add_argument("--curved-steps", type=int, default=3,
+                    help="timed mixed solves of the warped-mesh workload (0: skip the curved leg)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

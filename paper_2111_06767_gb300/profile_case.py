@@ -6,7 +6,7 @@
 
 --op smooth: Schwarz smoothing steps on the finest level (residual apply, gather, subdomain GEMM,
 scatter); --op apply: the DG operator alone (FP32 for --precision mixed, FP64 otherwise);
---op vcycle: full V-cycles; --op solve: FGMRES solves to 1e-10 of the 16-Gaussian source (one
+--op vcycle: full V-cycles; --warp: curved elements (a smooth warp of the box's nodes); --op solve: FGMRES solves to 1e-10 of the 16-Gaussian source (one
 untimed solve first, then --reps solves inside the NVTX range "timed", a 256 MB buffer written
 before each so that L2 starts cold as in bench.py). The domain is [-1,1]^3 with n^3 elements and
 N points per dimension.
@@ -29,8 +29,14 @@ def main():
     ap.add_argument("--gemm", choices=["default", "simt", "tf32"], default="default")
     ap.add_argument("--levels", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warp", action="store_true", help="curved elements: a smooth warp of the box's nodes")
     a = ap.parse_args()
-    d = dgg.Domain(n=(a.n,) * 3, N=a.N, precision=a.precision, mg_levels=a.levels, overlap=2, gemm=a.gemm)
+    xyz = None
+    if a.warp:
+        X, Y, Z = dgg.host_coordinates(dgg.make_desc((-1.0,) * 3, (1.0,) * 3, (a.n,) * 3, a.N))
+        xyz = (X + 0.1 * (1 - X**2) * Y, Y + 0.12 * (1 - Y**2) * Z * X, Z + 0.1 * (1 - Z**2) * (X + Y))
+    d = dgg.Domain(n=(a.n,) * 3, N=a.N, precision=a.precision, mg_levels=a.levels, overlap=2, gemm=a.gemm,
+                   node_xyz=xyz)
     g = torch.Generator(device="cuda").manual_seed(7)
     dt = torch.float32 if (a.op == "apply" and a.precision == "mixed") else torch.float64
     x = torch.empty(d.n_dof, dtype=dt, device="cuda").uniform_(-1, 1, generator=g)
