@@ -1,4 +1,5 @@
-"""Strong-form DG Poisson operator of Sec. II on curved (mapped) hexahedral elements.
+"""Strong-form DG operator of Sec. II for -div(K grad u) = f on curved (mapped) hexahedral elements,
+with a positive scalar coefficient field K (K = 1: the Poisson operator).
 
 Oracle code (test infrastructure only).
 
@@ -12,10 +13,12 @@ quadrature of Eqs. massmat, stiffmat and liftop (flat metric, sqrt g = 1) become
     (MD_i)_pq = w_p J_p G^j_i(p) Dhat_j,pq               (chain rule at the node)
     ML       = w_a w_b J^f on face nodes,  J^f = J |G^d|   (surface Jacobian, Nanson's relation)
 
-and the operator is Eqs. dg_op_auxvars and dg_op_primal with the flux of Eq. numflux:
+and the operator is Eqs. dg_op_auxvars and dg_op_primal with the fluxes F_v^i_j = u delta^i_j and
+F_u^i = K v^i and the flux of Eq. numflux:
 
     v_i  = G^j_i Dhat_j u + L (n_i (u* - u))
-    A u  = -M G^j_i Dhat_j v^i - ML ((n.grad u)* - n.v)
+    A u  = -M G^j_i Dhat_j (K v^i) - ML ((n.F_u)* - K n.v)
+    (n.F_u)* = (K n.grad u + K^ext n.grad u^ext) / 2 - sigma (K u - K^ext u^ext)
 
 Readings (each also listed in the design notes):
   * the unit normal at a face node is the element's own, n_i = s G^d_i / |G^d|, and the
@@ -24,7 +27,9 @@ Readings (each also listed in the design notes):
     h = 2 J / J^f = 2 / |G^d| (the element width for affine elements), and sigma takes the
     smaller of the two sides' values at the node; external faces use the interior value;
   * the coarse multigrid levels inherit the geometry of the fine one: a coarse element's nodes
-    are placed on the fine elements' interpolated map (the coarse map interpolates the fine one).
+    are placed on the fine elements' interpolated map (the coarse map interpolates the fine one),
+    and the coefficient K is interpolated the same way;
+  * on a boundary face the coefficient of the exterior state is the interior one.
 """
 from __future__ import annotations
 
@@ -55,6 +60,7 @@ class CurvedGraph:
     """Elements of one order N with their face connectivity and nodal metric.
 
     nbr[e, f]       exterior element, dg.EXTERNAL, dg.NEUMANN or dg.ZERO
+    K[e]            coefficient at the nodes
     J[e]            Jacobian determinant at the nodes
     G[e, j, i]      dxi^j / dx^i at the nodes
     hf_ext[e, f]    the exterior element's normal size at the face nodes (the interior's at
@@ -67,6 +73,11 @@ class CurvedGraph:
     J: np.ndarray
     G: np.ndarray
     hf_ext: np.ndarray
+    K: np.ndarray = None
+
+    def __post_init__(self):
+        if self.K is None:
+            self.K = np.ones_like(self.J)
 
     @property
     def n_elements(self) -> int:
@@ -75,7 +86,7 @@ class CurvedGraph:
     per_element = True  # operators differ between elements with the same neighbour pattern
 
     def subgraph(self, slots, pn):
-        return CurvedGraph(self.N, self.penalty, pn, self.J[slots], self.G[slots], self.hf_ext[slots])
+        return CurvedGraph(self.N, self.penalty, pn, self.J[slots], self.G[slots], self.hf_ext[slots], self.K[slots])
 
     def mass(self):
         w = lgl.lgl_weights(self.N)
@@ -91,7 +102,7 @@ def face_size(N, J, G, d, side):
     return 2.0 / np.sqrt((Gd**2).sum(axis=0))
 
 
-def make_graph(N, penalty, nbr, J, G) -> CurvedGraph:
+def make_graph(N, penalty, nbr, J, G, K=None) -> CurvedGraph:
     E = J.shape[0]
     hf_ext = np.zeros((E, 6, N, N))
     for f in range(6):
@@ -100,11 +111,12 @@ def make_graph(N, penalty, nbr, J, G) -> CurvedGraph:
         other = face_size(N, J, G, d, 1 - side)  # every element's opposite face
         has = nbr[:, f] >= 0
         hf_ext[:, f] = np.where(has[:, None, None], other[np.where(has, nbr[:, f], 0)], own)
-    return CurvedGraph(N, penalty, nbr, J, G, hf_ext)
+    return CurvedGraph(N, penalty, nbr, J, G, hf_ext, K)
 
 
 def apply(graph: CurvedGraph, u: np.ndarray) -> np.ndarray:
     """A u for nodal data u[..., E, N, N, N] on curved elements (homogeneous boundary data)."""
+    K = graph.K
     N, E = graph.N, graph.n_elements
     u = np.asarray(u, dtype=np.float64)
     assert u.shape[-4:] == (E, N, N, N), u.shape
@@ -139,21 +151,24 @@ def apply(graph: CurvedGraph, u: np.ndarray) -> np.ndarray:
         u_ext = dg._face(u, d, 1 - side, N)[..., nb, :, :] * mask
         g_int = [dg._face(grad[i], d, side, N) for i in range(3)]
         g_ext = [dg._face(grad[i], d, 1 - side, N)[..., nb, :, :] * mask for i in range(3)]
+        K_int = dg._face(K, d, side, N)
+        K_nbr = dg._face(K, d, 1 - side, N)[nb]
+        K_ext = np.where(has[:, None, None], K_nbr, K_int)  # boundary: the interior coefficient
 
         # auxiliary normal fluxes n_i F_v^i_j = n_j u, vector over j; exterior per Eq. bc
         nFv_int = [n[j] * u_int for j in range(3)]
         nFv_nbr = [-n[j] * u_ext for j in range(3)]  # n^ext = -n^int
         nFv_ext = [np.where(ext_bc, nFv_int[j], np.where(ext_neu, -nFv_int[j], nFv_nbr[j])) for j in range(3)]
-        # primal normal fluxes of the local gradients, n_i F_u^i = n . grad u
-        nFu_int = sum(n[i] * g_int[i] for i in range(3))
-        nFu_nbr = -sum(n[i] * g_ext[i] for i in range(3))
+        # primal normal fluxes of the local gradients, n_i F_u^i = K n . grad u
+        nFu_int = K_int * sum(n[i] * g_int[i] for i in range(3))
+        nFu_nbr = -K_ext * sum(n[i] * g_ext[i] for i in range(3))
         nFu_ext = np.where(ext_bc, -nFu_int, np.where(ext_neu, nFu_int, nFu_nbr))
 
         aux_star = [0.5 * (nFv_int[j] - nFv_ext[j]) for j in range(3)]  # Eq. numfluxaux
         h_int = face_size(N, graph.J, G, d, side)
         sigma = graph.penalty * N**2 / np.minimum(h_int, graph.hf_ext[:, f])  # Eq. penalty, p = N - 1
-        # n^int.F_u(n^int F_v(u^int)) - n^ext.F_u(n^ext F_v(u^ext)) = u^int + n . nFv_ext
-        pen = u_int + sum(n[j] * nFv_ext[j] for j in range(3))
+        # n^int.F_u(n^int F_v(u^int)) - n^ext.F_u(n^ext F_v(u^ext)) = K u^int + K^ext n . nFv_ext
+        pen = K_int * u_int + K_ext * sum(n[j] * nFv_ext[j] for j in range(3))
         prim_star = 0.5 * (nFu_int - nFu_ext) - sigma * pen  # Eq. numfluxprimal
 
         for j in range(3):
@@ -163,9 +178,9 @@ def apply(graph: CurvedGraph, u: np.ndarray) -> np.ndarray:
     Au = np.zeros_like(u)
     for i in range(3):
         for j in range(3):
-            Au -= Mdiag * (G[:, j, i] * dg._deriv(v[i], j, Dhat))
+            Au -= Mdiag * (G[:, j, i] * dg._deriv(K * v[i], j, Dhat))
     for d, side, n, Bf, prim_star in prim_face:
-        nv_int = sum(n[i] * dg._face(v[i], d, side, N) for i in range(3))
+        nv_int = dg._face(K, d, side, N) * sum(n[i] * dg._face(v[i], d, side, N) for i in range(3))
         Au -= dg._lift_to_volume(Bf * (prim_star - nv_int), d, side, N)
     return Au
 
@@ -183,15 +198,19 @@ def _coarse_eval_matrices(N):
 @dataclasses.dataclass
 class MappedGrid(dg.BoxGrid):
     """A box of n[0] x n[1] x n[2] elements in logical space whose elements are mapped
-    isoparametrically to the given physical node coordinates xyz = (x, y, z), each (E, N, N, N)."""
+    isoparametrically to the given physical node coordinates xyz = (x, y, z), each (E, N, N, N),
+    with the coefficient K at the nodes (None: K = 1)."""
 
     xyz: tuple = None
+    K: np.ndarray = None
 
     @classmethod
-    def from_mapping(cls, box: dg.BoxGrid, mapping):
-        """Nodes placed by a smooth map of the box's own node coordinates."""
-        return cls(box.lower, box.upper, box.n, box.N, box.penalty, box.neumann,
-                   tuple(np.asarray(c, float) for c in mapping(*box.coordinates())))
+    def from_mapping(cls, box: dg.BoxGrid, mapping, coefficient=None):
+        """Nodes placed by a smooth map of the box's own node coordinates; coefficient(x, y, z) gives
+        K at the mapped nodes."""
+        xyz = tuple(np.asarray(c, float) for c in mapping(*box.coordinates()))
+        K = None if coefficient is None else np.asarray(coefficient(*xyz), float)
+        return cls(box.lower, box.upper, box.n, box.N, box.penalty, box.neumann, xyz, K)
 
     def coordinates(self):
         return tuple(c.copy() for c in self.xyz)
@@ -200,14 +219,15 @@ class MappedGrid(dg.BoxGrid):
         E = self.n_elements
         nbr = np.array([[self.neighbor(e, f) for f in range(6)] for e in range(E)], dtype=np.int64)
         J, G = metric(self.N, *self.xyz)
-        return make_graph(self.N, self.penalty, nbr, J, G)
+        return make_graph(self.N, self.penalty, nbr, J, G, self.K)
 
     def coarsen(self, coarse_n):
         """The next multigrid level: coarse nodes on the interpolated fine map."""
         N = self.N
         box = dg.BoxGrid(self.lower, self.upper, tuple(coarse_n), N, self.penalty, self.neumann)
         C = _coarse_eval_matrices(N)
-        out = [np.zeros((box.n_elements, N, N, N)) for _ in range(3)]
+        fields = list(self.xyz) + ([] if self.K is None else [self.K])
+        out = [np.zeros((box.n_elements, N, N, N)) for _ in fields]
         for e in range(self.n_elements):
             c = self.element_coords(e)
             pc, halves = [], []
@@ -220,6 +240,7 @@ class MappedGrid(dg.BoxGrid):
                     halves.append(c[d] % 2)
             p = box.element_index(*pc)
             hx, hy, hz = halves
-            for i in range(3):
-                out[i][p] += np.einsum("kc,jb,ia,cba->kji", C[hz], C[hy], C[hx], self.xyz[i][e])
-        return MappedGrid(self.lower, self.upper, tuple(coarse_n), N, self.penalty, self.neumann, tuple(out))
+            for i, fld in enumerate(fields):
+                out[i][p] += np.einsum("kc,jb,ia,cba->kji", C[hz], C[hy], C[hx], fld[e])
+        K = out[3] if self.K is not None else None
+        return MappedGrid(self.lower, self.upper, tuple(coarse_n), N, self.penalty, self.neumann, tuple(out[:3]), K)

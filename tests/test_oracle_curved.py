@@ -2,7 +2,9 @@
 Eqs. massmat, stiffmat and liftop: reduction to the affine operator, invariance under rigid
 motions (full metric tensor, tilted normals), exactness on fields linear in the physical
 coordinates for a polynomial map, exact inheritance of a polynomial map by the coarse levels,
-spectral convergence on a warped mesh, and the Schwarz/multigrid solver on curved elements."""
+spectral convergence on a warped mesh, and the Schwarz/multigrid solver on curved elements; for a
+variable coefficient K in -div(K grad u): scaling by a constant K, symmetry and definiteness on
+affine elements, interpolation to the coarse levels, and spectral convergence."""
 import numpy as np
 import pytest
 
@@ -127,3 +129,53 @@ def test_curved_schwarz_and_multigrid_solve():
     direct = np.linalg.solve(dg.assemble(pr.graphs[0]), b.ravel())
     assert np.linalg.norm(u.ravel() - direct) <= 1e-8 * np.linalg.norm(direct)
     assert info["iterations"] <= 30
+
+
+# ---------------------------------------------------------------- variable coefficient: -div(K grad u)
+
+def coef(x, y, z):
+    return 1.0 + 0.5 * x**2 + 0.2 * y * z
+
+
+def test_constant_coefficient_scales_the_operator():
+    for mapping in (lambda X, Y, Z: (X, Y, Z), warp):
+        box = _box((2, 2, 1), 4)
+        plain = curved.MappedGrid.from_mapping(box, mapping)
+        scaled = curved.MappedGrid.from_mapping(box, mapping, lambda x, y, z: 2.5 + 0 * x)
+        u = RNG.uniform(-1, 1, (box.n_elements, 4, 4, 4))
+        ref = 2.5 * dg.apply(plain.graph(), u)
+        assert np.abs(dg.apply(scaled.graph(), u) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_variable_coefficient_on_affine_elements_is_symmetric_positive_definite():
+    """On affine elements the collocated strong form stays symmetric with K inside the divergence
+    (summation by parts of the LGL operators), and positive definite."""
+    g = curved.MappedGrid.from_mapping(_box((2, 2, 2), 4), lambda X, Y, Z: (X, Y, Z), coef)
+    A = dg.assemble(g.graph())
+    assert np.abs(A - A.T).max() <= 1e-13 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_coarse_levels_interpolate_the_coefficient():
+    """K(warp(X)) has degree 4 in the logical coordinates, reproduced by N = 6 elements: the coarse
+    level's interpolated coefficient is K at the coarse nodes."""
+    box = _box((4, 2, 2), 6)
+    fine = curved.MappedGrid.from_mapping(box, warp, coef)
+    coarse = fine.coarsen((2, 1, 1))
+    assert np.abs(coarse.K - coef(*warp(*box.coarsen((2, 1, 1)).coordinates()))).max() <= 1e-12
+
+
+def test_variable_coefficient_spectral_convergence_on_a_warped_mesh():
+    """u = sin(pi x) sin(pi y) sin(pi z) with K = 1 + x^2 / 2 solves -div(K grad u) = f with
+    f = 3 pi^2 K u - x du/dx; the discrete solution converges exponentially in N."""
+    errs = []
+    K = lambda x, y, z: 1.0 + 0.5 * x**2
+    for N in (4, 6, 8):
+        g = curved.MappedGrid.from_mapping(_box((2, 2, 2), N), warp, K)
+        gr = g.graph()
+        x, y, z = g.coordinates()
+        exact = np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        f = 3 * np.pi**2 * K(x, y, z) * exact - x * np.pi * np.cos(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        u = np.linalg.solve(dg.assemble(gr), dg.rhs(gr, f).ravel())
+        errs.append(np.sqrt(np.mean((u - exact.ravel()) ** 2)))
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10 and errs[2] < 1e-4, errs
