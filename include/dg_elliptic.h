@@ -91,6 +91,11 @@ typedef struct dg_domain_desc {
                              during dg_domain_create. Shared face nodes must coincide; a folded or
                              left-handed element is DG_ERR_INVALID_ARG. Every subdomain then has its own
                              explicit inverse (E n_S^2 values per level) */
+  const double* coef;     /* NULL: K = 1. Otherwise the operator is -div(K grad u) (fluxes F_u = K v in
+                             Eq. fluxform, the penalty flux of Eq. numflux on K u; POISSON only): host pointer
+                             to n_dof positive values of K at the nodes, read only during dg_domain_create;
+                             the coarse levels interpolate it. As for curved elements, every subdomain then
+                             has its own explicit inverse */
 } dg_domain_desc;
 
 enum dg_subdomain_gemm {

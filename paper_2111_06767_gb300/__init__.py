@@ -39,12 +39,13 @@ GEMM_MODES = {"default": 0, "simt": 1, "tf32": 2}
 
 
 def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, overlap=2, presmooth=3,
-              postsmooth=3, problem="poisson", punctures=(), gemm="default", neumann=(), node_xyz=None):
+              postsmooth=3, problem="poisson", punctures=(), gemm="default", neumann=(), node_xyz=None,
+              coef=None):
     """neumann: indices of the box faces (0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z) with homogeneous
     Neumann conditions (the others are homogeneous Dirichlet). node_xyz: None for the affine box,
     else the physical (x, y, z) of every LGL node (three arrays of n_dof values in the element-major
-    layout) of curved elements; the returned descriptor points at a float64 host copy kept as
-    desc.node_xyz_host."""
+    layout) of curved elements; coef: None for K = 1, else K at every node (-div(K grad u)). The
+    returned descriptor points at float64 host copies kept as desc.node_xyz_host / desc.coef_host."""
     d = nat.dg_domain_desc()
     for i in range(3):
         d.lower[i], d.upper[i], d.n[i] = lower[i], upper[i], n[i]
@@ -69,6 +70,15 @@ def make_desc(lower, upper, n, N, penalty=1.5, precision="fp64", mg_levels=0, ov
             raise ValueError("node_xyz needs n_dof coordinates per dimension")
         d.node_xyz = host.ctypes.data_as(C.POINTER(C.c_double))
         d.node_xyz_host = host
+    if coef is not None:
+        import numpy as np
+
+        k = coef.detach().cpu().numpy() if isinstance(coef, torch.Tensor) else coef
+        host_k = np.ascontiguousarray(np.asarray(k, dtype=np.float64).ravel())
+        if host_k.size != n[0] * n[1] * n[2] * N**3:
+            raise ValueError("coef needs n_dof values")
+        d.coef = host_k.ctypes.data_as(C.POINTER(C.c_double))
+        d.coef_host = host_k
     return d
 
 
@@ -112,9 +122,9 @@ class Domain:
 
     def __init__(self, lower=(-1.0,) * 3, upper=(1.0,) * 3, n=(2, 2, 2), N=6, penalty=1.5, precision="fp64",
                  mg_levels=0, overlap=2, presmooth=3, postsmooth=3, problem="poisson", punctures=(), stream=None,
-                 gemm="default", neumann=(), node_xyz=None):
+                 gemm="default", neumann=(), node_xyz=None, coef=None):
         self.desc = make_desc(lower, upper, n, N, penalty, precision, mg_levels, overlap, presmooth, postsmooth,
-                              problem, punctures, gemm, neumann, node_xyz)
+                              problem, punctures, gemm, neumann, node_xyz, coef)
         self._h = C.c_void_p()
         st = _lib.dg_domain_create(C.byref(self.desc), _stream(stream), C.byref(self._h))
         if st != nat.DG_OK:

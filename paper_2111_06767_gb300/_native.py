@@ -28,7 +28,7 @@ class dg_domain_desc(C.Structure):
                 ("overlap", C.c_int32), ("presmooth", C.c_int32), ("postsmooth", C.c_int32),
                 ("problem", C.c_int32), ("n_punctures", C.c_int32), ("punctures", dg_puncture * DG_MAX_PUNCTURES),
                 ("subdomain_gemm", C.c_int32), ("neumann_faces", C.c_int32),
-                ("node_xyz", C.POINTER(C.c_double))]
+                ("node_xyz", C.POINTER(C.c_double)), ("coef", C.POINTER(C.c_double))]
 
 
 class dg_layout(C.Structure):

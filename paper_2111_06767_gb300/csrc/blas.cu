@@ -37,6 +37,19 @@ void launch_axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
 template void launch_axpby<double>(int64_t, double, const double*, double, double*, cudaStream_t);
 template void launch_axpby<float>(int64_t, float, const float*, float, float*, cudaStream_t);
 
+template <typename T>
+__global__ void fill_kernel(int64_t n, T v, T* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) y[i] = v;
+}
+
+template <typename T>
+void launch_fill(int64_t n, T v, T* y, cudaStream_t s) {
+  if (n == 0) return;
+  fill_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, v, y);
+  DG_LAUNCHED(1);
+}
+template void launch_fill<double>(int64_t, double, double*, cudaStream_t);
+
 __global__ void d2f_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];

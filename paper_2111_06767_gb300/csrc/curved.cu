@@ -1,5 +1,6 @@
-// DG Poisson operator on curved (mapped) hexahedral elements (Sec. II with the metric terms of
-// Eqs. massmat, stiffmat and liftop, flat background metric) and the pieces a curved domain needs
+// DG operator of -div(K grad u) on curved (mapped) hexahedral elements (Sec. II with the metric
+// terms of Eqs. massmat, stiffmat and liftop, flat background metric, fluxes F_v = u, F_u = K v with
+// a positive scalar coefficient K per node; K = 1 is the Poisson operator) and the pieces it needs
 // around it: the nodal metric, the penalty at every face node, the mass diagonal, the coarse-level
 // node coordinates, and the explicit Schwarz subdomain matrices, one per subdomain.
 //
@@ -8,12 +9,13 @@
 // (G^j_i = dxi^j/dx^i), LGL collocation gives M = w_p J_p, (MD_i)_pq = w_p J_p G^j_i(p) Dhat_j,pq and
 // the face mass w_a w_b J^f with J^f = J |G^d| (Nanson's relation), so per element
 //   v_i  = G^j_i Dhat_j u + (|G^d| / w_0) n_i (u_E - u) / 2                  on face nodes
-//   A u  = -w_p J G^j_i Dhat_j v^i - w_a w_b J |G^d| [ (n.g - F_E)/2 - sigma (u - u_E) - n.v ]
+//   A u  = -w_p J G^j_i Dhat_j (K v^i)
+//          - w_a w_b J |G^d| [ (K n.g - F_E)/2 - sigma (K u - K_E u_E) - K n.v ]
 // with the unit outward normal n = s G^d / |G^d|, the local gradient g = G^j Dhat_j u, the exterior
-// value u_E and the exterior's own outward normal flux F_E = n_E.g_E = -n.g_E (Eq. numflux), and
-// the ghost states of Eq. bc on box faces (Dirichlet: u_E = -u, F_E = -n.g; Neumann: u_E = u,
-// F_E = n.g). sigma = C N^2 / min(h, h_E) with h = 2 / |G^d| the element size normal to the face
-// at the node (the element width for affine elements).
+// value u_E, coefficient K_E and own outward normal flux F_E = K_E n_E.g_E (Eq. numflux), and the
+// ghost states of Eq. bc on box faces (K_E = K; Dirichlet: u_E = -u, F_E = -K n.g; Neumann:
+// u_E = u, F_E = K n.g). sigma = C N^2 / min(h, h_E) with h = 2 / |G^d| the element size normal to
+// the face at the node (the element width for affine elements).
 //
 // GB300 mapping: one CTA per element, one thread per node (N^3 threads), the element's values, the
 // lifted auxiliary field and the exterior face data staged in shared memory. The exterior normal
@@ -38,8 +40,9 @@ struct CurvedSmem {
   T u[N * N * N];
   T v[3][N * N * N];
   T uE[6][N * N];  // exterior value at each face node (kNbr faces)
-  T fE[6][N * N];  // exterior's own outward normal flux n_E.g_E (kNbr faces)
+  T fE[6][N * N];  // exterior's own outward normal flux K_E n_E.g_E (kNbr faces)
   int type[6];
+  int eE[6];       // exterior element (kNbr faces): its coefficient is read at the matching node
 };
 
 __device__ __forceinline__ int elem_nbr(int nx, int ny, int nz, int e, int f) {
@@ -91,6 +94,7 @@ __device__ T curved_element(CurvedSmem<N, T>& S, const T* __restrict__ geo, int6
   const int idx[3] = {i, j, k};
   T J, G[3][3];
   load_metric<N, T>(geo, ndof, gbase + p, J, G);
+  const T Kp = geo[10 * ndof + gbase + p];
   T du[3];
   logical_grad<N, T>(S.D, S.u, i, j, k, du);
   T g[3], v[3];
@@ -117,9 +121,9 @@ __device__ T curved_element(CurvedSmem<N, T>& S, const T* __restrict__ geo, int6
     for (int c = 0; c < 3; ++c) v[c] += s * G[d][c] / norm * lift;
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) S.v[c][p] = v[c];
+  for (int c = 0; c < 3; ++c) S.v[c][p] = Kp * v[c];
   __syncthreads();
-  // divergence of the lifted field: sum_i sum_j G^j_i Dhat_j v^i
+  // divergence of the flux K v: sum_i sum_j G^j_i Dhat_j (K v^i)
   T div = 0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -145,10 +149,14 @@ __device__ T curved_element(CurvedSmem<N, T>& S, const T* __restrict__ geo, int6
       ng += nc * g[c];
       nv += nc * v[c];
     }
+    ng *= Kp;  // n.F_u of the local gradient
+    nv *= Kp;
     const int t = S.type[f];
     const T uE = t == kNbr ? S.uE[f][ab] : (t == kDirichlet ? -up : (t == kNeumann ? up : T(0)));
     const T fE = t == kNbr ? S.fE[f][ab] : (t == kDirichlet ? -ng : (t == kNeumann ? ng : T(0)));
-    const T prim = T(0.5) * (ng - fE) - sigma_e[f * N2 + ab] * (up - uE);
+    const T KE = t == kNbr ? geo[10 * ndof + (int64_t)S.eE[f] * (N * N2) + node_of<N>(d, side ? 0 : N - 1, a1, a2)]
+                           : Kp;
+    const T prim = T(0.5) * (ng - fE) - sigma_e[f * N2 + ab] * (Kp * up - KE * uE);
     Au -= S.w[a1] * S.w[a2] * J * norm * (prim - nv);
   }
   return Au;
@@ -173,6 +181,7 @@ __global__ void __launch_bounds__(N * N * N) curved_trace_kernel(CurvedArgs<T> a
   __syncthreads();
   T J, G[3][3];
   load_metric<N, T>(a.geo, a.ndof, (int64_t)e * N3 + p, J, G);
+  const T Kp = a.geo[10 * a.ndof + (int64_t)e * N3 + p];
   T du[3];
   logical_grad<N, T>(sD, su, i, j, k, du);
   const int idx[3] = {i, j, k};
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(N * N * N) curved_trace_kernel(CurvedArgs<T> a
     T ng = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) ng += s * G[d][c] / norm * (G[0][c] * du[0] + G[1][c] * du[1] + G[2][c] * du[2]);
-    a.trace[((int64_t)e * 6 + f) * N2 + a2 * N + a1] = ng;
+    a.trace[((int64_t)e * 6 + f) * N2 + a2 * N + a1] = Kp * ng;
   }
 }
 
@@ -202,6 +211,7 @@ __global__ void __launch_bounds__(N * N * N) curved_apply_kernel(CurvedArgs<T> a
   if (p < 6) {
     const int nb = elem_nbr(a.n[0], a.n[1], a.n[2], e, p);
     S.type[p] = nb >= 0 ? kNbr : (((a.neumann >> p) & 1) ? kNeumann : kDirichlet);
+    S.eE[p] = nb;
   }
   for (int t = p; t < 6 * N2; t += N3) {
     const int f = t / N2, ab = t - f * N2, d = f >> 1, side = f & 1;
@@ -255,6 +265,7 @@ __global__ void __launch_bounds__(N * N * N) curved_column_kernel(CurvedArgs<T> 
     __syncthreads();
     T J, G[3][3];
     load_metric<N, T>(a.geo, a.ndof, (int64_t)selem[P] * N3 + p, J, G);
+    const T Kp = a.geo[10 * a.ndof + (int64_t)selem[P] * N3 + p];
     T du[3];
     logical_grad<N, T>(S.D, S.u, i, j, k, du);
     const int idx[3] = {i, j, k};
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(N * N * N) curved_column_kernel(CurvedArgs<T> 
       T ng = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) ng += s * G[d][c] / norm * (G[0][c] * du[0] + G[1][c] * du[1] + G[2][c] * du[2]);
-      sTP[f][a2 * N + a1] = ng;
+      sTP[f][a2 * N + a1] = Kp * ng;
     }
     __syncthreads();
   }
@@ -290,6 +301,7 @@ __global__ void __launch_bounds__(N * N * N) curved_column_kernel(CurvedArgs<T> 
                                                                 : (((a.neumann >> f) & 1) ? kNeumann : kDirichlet);
       }
       S.type[f] = t;
+      S.eE[f] = t == kNbr ? selem[X == 0 ? 1 + f : 0] : -1;
     }
     for (int t = p; t < 6 * N2; t += N3) {
       const int f = t / N2, ab = t - f * N2, d = f >> 1, side = f & 1;
@@ -306,12 +318,13 @@ __global__ void __launch_bounds__(N * N * N) curved_column_kernel(CurvedArgs<T> 
   }
 }
 
-// J and G = Jac^-1 at every node from the nodal coordinates (FP64), written as [10][ndof].
+// J and G = Jac^-1 at every node from the nodal coordinates (FP64), and the coefficient K: [11][ndof].
 template <int N>
 __global__ void __launch_bounds__(N * N * N) curved_metric_kernel(const double* __restrict__ x, const double* __restrict__ y,
-                                                                  const double* __restrict__ z, const double* __restrict__ D,
-                                                                  int64_t ndof, double* __restrict__ geo64,
-                                                                  float* __restrict__ geo32, int* __restrict__ bad) {
+                                                                  const double* __restrict__ z, const double* __restrict__ K,
+                                                                  const double* __restrict__ D, int64_t ndof,
+                                                                  double* __restrict__ geo64, float* __restrict__ geo32,
+                                                                  int* __restrict__ bad) {
   constexpr int N2 = N * N, N3 = N * N * N;
   __shared__ double sD[N2];
   __shared__ double sx[3][N3];
@@ -343,8 +356,11 @@ __global__ void __launch_bounds__(N * N * N) curved_metric_kernel(const double* 
   G[0][2] = (jac[0][1] * jac[1][2] - jac[0][2] * jac[1][1]) * inv;
   G[1][2] = (jac[0][2] * jac[1][0] - jac[0][0] * jac[1][2]) * inv;
   G[2][2] = (jac[0][0] * jac[1][1] - jac[0][1] * jac[1][0]) * inv;
+  if (!(K[gp] > 0.0)) atomicExch(bad, 2);  // the coefficient must be positive
   geo64[gp] = det;
   geo32[gp] = (float)det;
+  geo64[10 * ndof + gp] = K[gp];
+  geo32[10 * ndof + gp] = (float)K[gp];
 #pragma unroll
   for (int m = 0; m < 3; ++m)
 #pragma unroll
@@ -405,7 +421,7 @@ __global__ void curved_coarsen_kernel(int cx, int cy, int cz, int fx, int fy, in
       }
     }
     const int64_t fe = child[0] + (int64_t)fx * (child[1] + (int64_t)fy * child[2]);
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {  // x, y, z and the coefficient
       const double* src = fin + c * fndof + fe * N3;
       double acc = 0.0;
       for (int kk = 0; kk < N; ++kk)
@@ -470,8 +486,8 @@ void launch_curved_metric(int N, int64_t E, const double* xyz, const double* D, 
   const int64_t ndof = E * N * N * N;
 #define DG_CASE(NN)                                                                                           \
   case NN:                                                                                                    \
-    curved_metric_kernel<NN><<<(unsigned)E, NN * NN * NN, 0, s>>>(xyz, xyz + ndof, xyz + 2 * ndof, D, ndof, \
-                                                                   geo64, geo32, bad);                        \
+    curved_metric_kernel<NN><<<(unsigned)E, NN * NN * NN, 0, s>>>(xyz, xyz + ndof, xyz + 2 * ndof,          \
+                                                                   xyz + 3 * ndof, D, ndof, geo64, geo32, bad); \
     break;
   DG_CURVED_SWITCH(DG_CASE)
 #undef DG_CASE

@@ -108,7 +108,8 @@ struct dg_domain {
   std::string err;
   int N = 0;
   bool mixed = false;
-  bool curved = false;  // mapped elements (node coordinates given at creation)
+  bool curved = false;  // per-element operators: mapped elements or a variable coefficient
+  bool mapped = false;  // node coordinates given at creation (the operator is then not symmetric)
   dg::LglTables lgl;
   dg::DevBuf<double> D64, w64, Ilo64, Ihi64, x1;
   dg::DevBuf<float> D32, w32, Ilo32, Ihi32;

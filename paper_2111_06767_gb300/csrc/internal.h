@@ -237,7 +237,8 @@ void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* 
 template <typename T>
 void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s);
 
-// Curved (mapped) elements: metric [10][ndof] (J, then G^j_i = dxi^j/dx^i at 1 + 3 j + i), penalty
+// Curved (mapped) elements and variable coefficients: metric [11][ndof] (J, then G^j_i = dxi^j/dx^i
+// at 1 + 3 j + i, then the coefficient K at 10), penalty
 // at every face node [E][6][N^2], outward normal fluxes of u at every face node [E][6][N^2].
 template <typename T>
 struct CurvedArgs {
@@ -287,6 +288,8 @@ void launch_restrict(int N, const int nf[3], const int nc[3], const T* Ilo, cons
 // Vector kernels.
 template <typename T>
 void launch_axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s);  // y = a x + b y
+template <typename T>
+void launch_fill(int64_t n, T v, T* y, cudaStream_t s);  // y = v
 void launch_convert_d2f(int64_t n, const double* x, float* y, cudaStream_t s);
 void launch_convert_f2d(int64_t n, const float* x, double* y, cudaStream_t s);
 void launch_add_f2d(int64_t n, const float* x, double* y, cudaStream_t s);  // y += x

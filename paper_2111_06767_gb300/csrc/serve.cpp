@@ -205,7 +205,7 @@ dg_status elliptic_serve_submit(dg_server* srv, const dg_request* req, uint64_t*
   const dg_domain_desc& d = req->domain;
   if (d.N < 2 || d.N > DG_MAX_N || d.n[0] < 1 || d.n[1] < 1 || d.n[2] < 1) return DG_ERR_INVALID_ARG;
   if (d.problem == DG_PROBLEM_POISSON && !req->f_host) return DG_ERR_INVALID_ARG;
-  if (d.node_xyz) return DG_ERR_INVALID_ARG;  // curved domains are not served (the coordinates are not copied)
+  if (d.node_xyz || d.coef) return DG_ERR_INVALID_ARG;  // per-node geometry or coefficients are not copied
   const int max_it = req->opts.max_iterations > 0 ? req->opts.max_iterations : 200;
   if (req->opts.subdomain_solver != 0 && req->opts.subdomain_solver != 1) return DG_ERR_INVALID_ARG;
   const size_t bytes = dg::estimate_domain_bytes(d, max_it, req->opts.subdomain_solver == 1);

@@ -307,21 +307,34 @@ void alloc_work(LevelWork<T>& w, const Level& L, cudaStream_t s) {
 
 }  // namespace
 
-// Curved elements: the level-0 node coordinates from the caller, the coarse levels' nodes on the
-// interpolated fine map (per coarsened dimension the coarse node xi_c lies in the lower child,
+// Curved elements or a variable coefficient: the level-0 node coordinates (the caller's, else the
+// box's) and coefficient (the caller's, else 1), the coarse levels' nodes and coefficient on the
+// interpolated fine fields (per coarsened dimension the coarse node xi_c lies in the lower child,
 // xi_c <= 0, at child coordinate 2 xi_c + 1, or in the upper one at 2 xi_c - 1), then per level the
 // nodal metric and the face-node penalty; the mass diagonal w_p J_p of level 0.
-void setup_curved_geometry(dg_domain* dom, const double* host_xyz) {
+void setup_curved_geometry(dg_domain* dom, const double* host_xyz, const double* host_coef) {
   const int N = dom->N;
   cudaStream_t s = dom->stream;
   const LglTables& t = dom->lgl;
   const Level& L0 = dom->levels[0];
   const size_t n0 = (size_t)L0.ndof;
-  DevBuf<double> xyz(3 * n0);
-  DG_CUDA(cudaMemcpyAsync(xyz.get(), host_xyz, 3 * n0 * sizeof(double), cudaMemcpyHostToDevice, s));
-  DG_CUDA(cudaMemcpyAsync(dom->X.get(), xyz.get(), n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  DG_CUDA(cudaMemcpyAsync(dom->Y.get(), xyz.get() + n0, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  DG_CUDA(cudaMemcpyAsync(dom->Z.get(), xyz.get() + 2 * n0, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  DevBuf<double> xyz(4 * n0);  // x, y, z, K
+  if (host_xyz) {
+    DG_CUDA(cudaMemcpyAsync(xyz.get(), host_xyz, 3 * n0 * sizeof(double), cudaMemcpyHostToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(dom->X.get(), xyz.get(), n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(dom->Y.get(), xyz.get() + n0, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(dom->Z.get(), xyz.get() + 2 * n0, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    launch_node_coords(N, L0.n, dom->desc.lower, L0.h, dom->x1.get(), dom->X.get(), dom->Y.get(), dom->Z.get(), s);
+    DG_CUDA(cudaMemcpyAsync(xyz.get(), dom->X.get(), n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(xyz.get() + n0, dom->Y.get(), n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(xyz.get() + 2 * n0, dom->Z.get(), n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (host_coef) {
+    DG_CUDA(cudaMemcpyAsync(xyz.get() + 3 * n0, host_coef, n0 * sizeof(double), cudaMemcpyHostToDevice, s));
+  } else {
+    launch_fill<double>((int64_t)n0, 1.0, xyz.get() + 3 * n0, s);
+  }
   // coarsening weights: [lower child][c][q], [upper child][c][q], identity, upper-half flag per node
   std::vector<double> C(3 * N * N + N, 0.0);
   auto lagrange = [&](int q, double x) {
@@ -346,12 +359,12 @@ void setup_curved_geometry(dg_domain* dom, const double* host_xyz) {
   for (size_t l = 0; l < dom->levels.size(); ++l) {
     Level& L = dom->levels[l];
     if (l > 0) {
-      DevBuf<double> next(3 * (size_t)L.ndof);
+      DevBuf<double> next(4 * (size_t)L.ndof);
       launch_curved_coarsen(N, L.n, dom->levels[l - 1].n, dC.get(), cur.get(), next.get(), s);
       cur = std::move(next);
     }
-    L.geo64.alloc(10 * (size_t)L.ndof);
-    L.geo32.alloc(10 * (size_t)L.ndof);
+    L.geo64.alloc(11 * (size_t)L.ndof);
+    L.geo32.alloc(11 * (size_t)L.ndof);
     launch_curved_metric(N, L.E, cur.get(), dom->D64.get(), L.geo64.get(), L.geo32.get(), bad.get(), s);
     const size_t nf = (size_t)L.E * 6 * N * N;
     L.sig64.alloc(nf);
@@ -364,7 +377,8 @@ void setup_curved_geometry(dg_domain* dom, const double* host_xyz) {
   int h_bad = 0;
   DG_CUDA(cudaMemcpyAsync(&h_bad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
-  DG_REQUIRE(!h_bad, "node coordinates give a folded or left-handed element (Jacobian determinant <= 0)");
+  DG_REQUIRE(h_bad != 1, "node coordinates give a folded or left-handed element (Jacobian determinant <= 0)");
+  DG_REQUIRE(h_bad != 2, "the coefficient must be positive at every node");
 }
 
 void domain_setup(dg_domain* dom) {
@@ -387,12 +401,14 @@ void domain_setup(dg_domain* dom) {
              "tensor-core subdomain GEMM needs a MIXED domain");
   DG_REQUIRE(d.problem != DG_PROBLEM_PUNCTURE || (d.n_punctures >= 0 && d.n_punctures <= DG_MAX_PUNCTURES),
              "bad puncture count");
-  DG_REQUIRE(!d.node_xyz || d.problem == DG_PROBLEM_POISSON, "curved elements are supported for POISSON only");
+  DG_REQUIRE((!d.node_xyz && !d.coef) || d.problem == DG_PROBLEM_POISSON,
+             "curved elements and variable coefficients are supported for POISSON only");
   const int64_t ndof = (int64_t)d.n[0] * d.n[1] * d.n[2] * d.N * d.N * d.N;
   DG_REQUIRE(ndof < (int64_t)1 << 31, "problem too large for 32-bit point indices");
   dom->N = d.N;
   dom->mixed = d.precision == DG_PRECISION_MIXED;
-  dom->curved = d.node_xyz != nullptr;
+  dom->curved = d.node_xyz != nullptr || d.coef != nullptr;
+  dom->mapped = d.node_xyz != nullptr;
   dom->use_tc = dom->mixed && d.subdomain_gemm != DG_GEMM_SIMT;
   {
     const char* v = std::getenv("DG_COARSE_FUSED");
@@ -443,8 +459,9 @@ void domain_setup(dg_domain* dom) {
   dom->Z.alloc(L0.ndof);
   dom->mass.alloc(L0.ndof);
   if (dom->curved) {
-    setup_curved_geometry(dom, d.node_xyz);
-    dom->desc.node_xyz = nullptr;  // the caller's buffer is not kept
+    setup_curved_geometry(dom, d.node_xyz, d.coef);
+    dom->desc.node_xyz = nullptr;  // the caller's buffers are not kept
+    dom->desc.coef = nullptr;
   } else {
     launch_node_coords(N, L0.n, d.lower, L0.h, dom->x1.get(), dom->X.get(), dom->Y.get(), dom->Z.get(), s);
     launch_mass_diag<double>(N, L0.g64, dom->w64.get(), L0.ndof, dom->mass.get(), s);

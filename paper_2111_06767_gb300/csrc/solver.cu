@@ -747,7 +747,7 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
   const int pmode = o.precondition;
   DG_REQUIRE(pmode >= 0 && pmode <= 2, "precondition must be 0, 1 or 2");
   DG_REQUIRE(o.krylov == 0 || o.krylov == 1, "krylov must be 0 (FGMRES) or 1 (flexible CG)");
-  DG_REQUIRE(!dom->curved || o.krylov == 0, "flexible CG needs a symmetric operator; curved elements are not");
+  DG_REQUIRE(!dom->mapped || o.krylov == 0, "flexible CG needs a symmetric operator; curved elements are not");
   DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
   ensure_workspace(dom, std::min(max_it, 16));
   dg_solve_report R{};

@@ -1,4 +1,5 @@
-"""GPU parity on curved (mapped) elements against the oracle (oracle.curved), through the C ABI:
+"""GPU parity on curved (mapped) elements and with a variable coefficient K in -div(K grad u) against
+the oracle (oracle.curved), through the C ABI:
 the operator (FP64 1e-12, FP32 2e-5 relative), the mass matrix and coarse levels, the Schwarz
 smoother with one explicit inverse per subdomain (FP64 1e-10, MIXED 1e-4), the V-cycle, FGMRES
 solves against the dense direct solution, spectral accuracy on a manufactured solution, argument
@@ -188,3 +189,79 @@ def test_curved_8x8x8_N8_workload():
     uh = sols["fp64"][0].reshape(-1, N, N, N)
     res = dg.rhs(gr, f) - dg.apply(gr, uh)
     assert np.linalg.norm(res) <= 1.01e-10 * np.linalg.norm(sols["fp64"][2])
+
+
+# ---------------------------------------------------------------- variable coefficient: -div(K grad u)
+
+def coef(x, y, z):
+    """A smooth coefficient, positive on every mesh used here (>= 0.8)."""
+    return 1.0 + 0.5 * x**2 + 0.2 * np.tanh(y * z)
+
+
+@pytest.mark.parametrize("n,N,mapping,neumann", [((2, 2, 2), 4, None, ()), ((3, 2, 1), 5, warp, (1,)),
+                                                 ((2, 1, 2), 6, sheared_warp, ()), ((1, 2, 1), 10, None, (2, 3))])
+def test_variable_coefficient_apply_matches_oracle(n, N, mapping, neumann):
+    ident = lambda X, Y, Z: (X, Y, Z)
+    g = curved.MappedGrid.from_mapping(dg.BoxGrid((-1.0,) * 3, (1.0,) * 3, n, N, 1.5,
+                                                  tuple(f in neumann for f in range(6))), mapping or ident, coef)
+    xyz = None if mapping is None else g.coordinates()
+    d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=1, neumann=neumann, node_xyz=xyz, coef=g.K)
+    u = rand(140 + N, (g.n_elements, N, N, N))
+    ref = dg.apply(g.graph(), u)
+    assert rel(d.apply(dev(u)).cpu().numpy(), ref) < 1e-12
+    assert rel(d.apply_f32(dev(u).float()).double().cpu().numpy(), ref) < 2e-5
+
+
+def test_variable_coefficient_levels_smoother_and_vcycle():
+    n, N = (4, 4, 2), 4
+    g = curved.MappedGrid.from_mapping(dg.BoxGrid((-1.0,) * 3, (1.0,) * 3, n, N, 1.5), warp, coef)
+    d = domain(g, mg_levels=3, overlap=2, coef=g.K)
+    for level, gl in enumerate(mg.hierarchy(g, 3)):
+        u = rand(150 + level, (gl.n_elements, N, N, N))
+        assert rel(d.apply_level(level, dev(u)).cpu().numpy(), dg.apply(gl.graph(), u)) < 1e-12, level
+    pr = solve.Problem(g, mg_levels=3)
+    b = rand(151, (g.n_elements, N, N, N))
+    u0 = rand(152, (g.n_elements, N, N, N))
+    assert rel(d.schwarz_smooth(0, dev(b), dev(u0), 2).cpu().numpy(), pr.schwarz[0].smooth(b, u0, 2)) < 1e-10
+    assert rel(d.vcycle(dev(b)).cpu().numpy(), pr.vcycle(b)) < 1e-10
+
+
+def test_variable_coefficient_solves():
+    """Affine elements with K: the operator is symmetric, so flexible CG is allowed as well as FGMRES;
+    both precisions reach the oracle's direct solution."""
+    n, N = (2, 2, 2), 5
+    g = curved.MappedGrid.from_mapping(dg.BoxGrid((-1.0,) * 3, (1.0,) * 3, n, N, 1.5), lambda X, Y, Z: (X, Y, Z), coef)
+    gr = g.graph()
+    x, y, z = g.coordinates()
+    f = workloads.gaussian_source(2)(x, y, z)
+    direct = np.linalg.solve(dg.assemble(gr), dg.rhs(gr, f).ravel())
+    for precision in ("fp64", "mixed"):
+        d = dgg.Domain(n=n, N=N, precision=precision, coef=g.K)
+        b = d.rhs(dev(f))
+        for krylov in ("fgmres", "fcg"):
+            u = torch.zeros_like(b)
+            rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(krylov=krylov))
+            assert rep.relative_residual <= 1e-10
+            assert rel(u.cpu().numpy(), direct) < 1e-9, (precision, krylov)
+
+
+def test_variable_coefficient_manufactured_solution():
+    """u = sin(pi x) sin(pi y) sin(pi z), K = 1 + x^2 / 2: f = 3 pi^2 K u - x du/dx on the warped mesh;
+    2^3 elements, N = 8 are within 1e-4 of u (the oracle's pin)."""
+    K = lambda x, y, z: 1.0 + 0.5 * x**2
+    g = curved.MappedGrid.from_mapping(dg.BoxGrid((-1.0,) * 3, (1.0,) * 3, (2, 2, 2), 8, 1.5), warp, K)
+    d = domain(g, precision="mixed", coef=g.K)
+    X, Y, Z = (c.cpu().numpy() for c in d.coordinates())
+    exact = np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)
+    f = 3 * np.pi**2 * K(X, Y, Z) * exact - X * np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)
+    b = d.rhs(dev(f))
+    u = torch.zeros_like(b)
+    assert d.solve(b, u, tol=1e-12).relative_residual <= 1e-12
+    assert np.sqrt(np.mean((u.cpu().numpy() - exact) ** 2)) < 1e-4
+
+
+def test_nonpositive_coefficient_is_rejected():
+    k = np.ones(8 * 27)
+    k[5] = 0.0
+    with pytest.raises(dgg.NativeError):
+        dgg.Domain(n=(2, 2, 2), N=3, coef=k)
