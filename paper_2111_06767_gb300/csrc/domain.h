@@ -27,6 +27,8 @@ struct SchwarzLevel {
   DevBuf<int> xform_of_elem;       // orientation index 8 perm + flips (canonical -> actual frame)
   DevBuf<double> inv64;            // [n_classes][nS][nS] explicit inverses (FP64 mode)
   DevBuf<float> inv32;             // FP32 copies (mixed mode)
+  DevBuf<uint16_t> inv16;          // curved MIXED domains: per-subdomain inverses in FP16, each scaled
+  DevBuf<float> inv16_scale;       //   by its largest magnitude (kept here)
   DevBuf<int4> tiles;              // SIMT GEMM tile list (class, row0, col0, columns left): 64 x 64
   int n_tiles = 0;
   DevBuf<int4> tiles_tc;           // tensor-core GEMM tiles: 128 rows x 64 columns

@@ -276,6 +276,11 @@ void launch_lin_assemble(const T* A, const int* class_of_col, const T* dS, int n
                          cudaStream_t s);
 template <typename T>
 void launch_lin_gemv(const T* Minv, const T* rS, int nS, int ld, int E, T* duS, cudaStream_t s);
+// FP16 copies of E compact n_S x n_S FP32 matrices, each scaled by its largest magnitude (scale[c]),
+// and du_S = scale Minv16 r_S with FP32 vectors and sums.
+void launch_to_half_scaled(const float* src, int nS, int E, uint16_t* dst, float* scale, cudaStream_t s);
+void launch_lin_gemv_half(const uint16_t* Minv, const float* scale, const float* rS, int nS, int ld, int E,
+                          float* duS, cudaStream_t s);
 
 // Multigrid transfers (per dimension: 0 lower half, 1 upper half, 2 full).
 template <typename T>

@@ -6,6 +6,8 @@
 // batched Gauss-Jordan kernels, and every smoothing step applies them with one batched
 // matrix-vector product. Both are HBM streams over E n_S^2 values: the product reads each inverse
 // once per smoothing step.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "internal.h"
@@ -109,6 +111,104 @@ void launch_lin_gemv(const T* Minv, const T* rS, int nS, int ld, int E, T* duS, 
                    (reinterpret_cast<uintptr_t>(rS) % 16) == 0;
   if (vec) lin_gemv_kernel<T, VV, 4><<<grid, 256, 0, s>>>(Minv, rS, nS, ld, rps, duS);
   else lin_gemv_kernel<T, 1, 4><<<grid, 256, 0, s>>>(Minv, rS, nS, ld, rps, duS);
+  DG_LAUNCHED(1);
+}
+
+// FP16 copies of per-subdomain inverses for the MIXED curved smoother: every matrix is divided by
+// its largest magnitude (kept in scale[c]) and rounded to FP16, whose 11-bit significand matches the
+// TF32 inputs of the tensor-core GEMM used for the shared class inverses; products accumulate in
+// FP32 and are rescaled.
+__global__ void __launch_bounds__(256) to_half_kernel(const float* __restrict__ src, int64_t n2,
+                                                      uint16_t* __restrict__ dst, float* __restrict__ scale) {
+  __shared__ float red[8];
+  const int c = blockIdx.x;
+  const float* a = src + (size_t)c * n2;
+  float m = 0.f;
+  for (int64_t t = threadIdx.x; t < n2; t += blockDim.x) m = fmaxf(m, fabsf(a[t]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int q = 0; q < 8; ++q) m = fmaxf(m, red[q]);
+  const float inv = m > 0.f ? 1.f / m : 0.f;
+  __half* d = reinterpret_cast<__half*>(dst) + (size_t)c * n2;
+  for (int64_t t = threadIdx.x; t < n2; t += blockDim.x) d[t] = __float2half_rn(a[t] * inv);
+  if (threadIdx.x == 0) scale[c] = m;
+}
+
+void launch_to_half_scaled(const float* src, int nS, int E, uint16_t* dst, float* scale, cudaStream_t s) {
+  if (E == 0) return;
+  to_half_kernel<<<E, 256, 0, s>>>(src, (int64_t)nS * nS, dst, scale);
+  DG_LAUNCHED(1);
+}
+
+// du_S[:, c] = scale[c] (Minv16_c r_S[:, c]): as lin_gemv_kernel with FP16 matrix entries (eight
+// per 16-byte load when the rows allow it) and FP32 vectors and sums.
+template <int V, int R>
+__global__ void __launch_bounds__(256) lin_gemv_half_kernel(const uint16_t* __restrict__ Minv,
+                                                            const float* __restrict__ scale,
+                                                            const float* __restrict__ rS, int nS, int ld,
+                                                            int rows_per_split, float* __restrict__ duS) {
+  const int c = blockIdx.x;
+  const int r0 = blockIdx.y * rows_per_split, r1 = min(nS, r0 + rows_per_split);
+  const __half* m = reinterpret_cast<const __half*>(Minv) + (size_t)c * nS * nS;
+  const float* x = rS + (size_t)c * ld;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = nS / V;
+  for (int rb = r0 + warp * R; rb < r1; rb += 8 * R) {
+    float acc[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = 0.f;
+    for (int j = lane; j < nv; j += 32) {
+      if constexpr (V == 8) {
+        const float4 x0 = reinterpret_cast<const float4*>(x)[2 * j], x1 = reinterpret_cast<const float4*>(x)[2 * j + 1];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          if (rb + q >= r1) continue;
+          const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(m + (size_t)(rb + q) * nS) + j);
+          const __half2* h = reinterpret_cast<const __half2*>(&raw);
+          const float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]);
+          const float2 f2 = __half22float2(h[2]), f3 = __half22float2(h[3]);
+          acc[q] += f0.x * x0.x + f0.y * x0.y + f1.x * x0.z + f1.y * x0.w + f2.x * x1.x + f2.y * x1.y +
+                    f3.x * x1.z + f3.y * x1.w;
+        }
+      } else {
+        const float xv = x[j];
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (rb + q < r1) acc[q] += __half2float(m[(size_t)(rb + q) * nS + j]) * xv;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    }
+    if (lane < R && rb + lane < r1) {
+      float v = acc[0];
+#pragma unroll
+      for (int q = 1; q < R; ++q)
+        if (lane == q) v = acc[q];
+      duS[(size_t)c * ld + rb + lane] = scale[c] * v;
+    }
+  }
+}
+
+void launch_lin_gemv_half(const uint16_t* Minv, const float* scale, const float* rS, int nS, int ld, int E,
+                          float* duS, cudaStream_t s) {
+  if (E == 0) return;
+  int dev = 0, n_sm = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const int want = std::max(1, (8 * n_sm + E - 1) / E);
+  const int splits = std::max(1, std::min(want, nS / 64));
+  const int rps = (nS + splits - 1) / splits;
+  const dim3 grid(E, splits);
+  const bool vec = nS % 8 == 0 && ld % 8 == 0 && (reinterpret_cast<uintptr_t>(Minv) % 16) == 0 &&
+                   (reinterpret_cast<uintptr_t>(rS) % 32) == 0;
+  if (vec) lin_gemv_half_kernel<8, 4><<<grid, 256, 0, s>>>(Minv, scale, rS, nS, ld, rps, duS);
+  else lin_gemv_half_kernel<1, 4><<<grid, 256, 0, s>>>(Minv, scale, rS, nS, ld, rps, duS);
   DG_LAUNCHED(1);
 }
 

@@ -543,6 +543,15 @@ void ensure_schwarz(dg_domain* dom, int level) {
     sw.inv_scale = 1.0;
     if (dom->mixed) {
       build_curved_inverses<float>(dom, L, sw.inv32, L.geo32.get(), L.sig32.get(), dom->D32.get(), dom->w32.get(), s);
+      if (dom->desc.subdomain_gemm != DG_GEMM_SIMT) {
+        // the smoother streams every inverse once per step: keep them in FP16 (scaled per subdomain),
+        // the input precision of the tensor-core path; "simt" keeps FP32
+        sw.inv16.alloc((size_t)L.E * sw.nS * sw.nS);
+        sw.inv16_scale.alloc(L.E);
+        launch_to_half_scaled(sw.inv32.get(), sw.nS, L.E, sw.inv16.get(), sw.inv16_scale.get(), s);
+        DG_CUDA(cudaStreamSynchronize(s));
+        sw.inv32.release();
+      }
       alloc_work(L.w32, L, s);
     } else {
       build_curved_inverses<double>(dom, L, sw.inv64, L.geo64.get(), L.sig64.get(), dom->D64.get(), dom->w64.get(),
@@ -657,7 +666,8 @@ size_t domain_device_bytes(const dg_domain* dom) {
          L.trace32.bytes();
     b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.class_of_col.bytes() + sw.xform_of_elem.bytes() +
          sw.inv64.bytes() +
-         sw.inv32.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() + sw.units.bytes() + sw.bar.bytes();
+         sw.inv32.bytes() + sw.inv16.bytes() + sw.inv16_scale.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() +
+         sw.units.bytes() + sw.bar.bytes();
     for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
                     &L.w64.gH, &L.w64.linA, &L.w64.linv})
       b += p->bytes();

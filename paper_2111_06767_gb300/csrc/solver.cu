@@ -182,7 +182,10 @@ template <>
 void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaStream_t s) {
   const SchwarzLevel& sw = L.sw;
   if (dom->curved) {  // one inverse per subdomain
-    launch_lin_gemv<float>(sw.inv32.get(), X, sw.nS, sw.ld, L.E, Y, s);
+    if (sw.inv16.get())
+      launch_lin_gemv_half(sw.inv16.get(), sw.inv16_scale.get(), X, sw.nS, sw.ld, L.E, Y, s);
+    else
+      launch_lin_gemv<float>(sw.inv32.get(), X, sw.nS, sw.ld, L.E, Y, s);
     return;
   }
   if (dom->use_tc) {
@@ -218,7 +221,7 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
   Level& L = dom->levels[level];
   LevelWork<T>& W = work<T>(L);
   SchwarzLevel& sw = L.sw;
-  DG_REQUIRE(inverses<T>(sw) != nullptr && shares<T>(dom) != nullptr,
+  DG_REQUIRE((inverses<T>(sw) != nullptr || (sizeof(T) == 4 && sw.inv16.get())) && shares<T>(dom) != nullptr,
              "Schwarz data of this precision are not built for this domain");
   if (iterations <= 0) return;
   const bool linearized_level = linearized_smoother<T>(dom, level);
