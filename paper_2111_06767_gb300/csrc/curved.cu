@@ -104,21 +104,37 @@ __device__ T curved_element(CurvedSmem<N, T>& S, const T* __restrict__ geo, int6
     v[c] = g[c];
   }
   const T up = S.u[p];
+  // the faces through the node, at most one per dimension: their unit outward normals and |G^d|
+  // (one square root and one division per face)
+  int fside[3];
+  T nn[3][3], nrm[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    fside[d] = idx[d] == 0 ? 0 : (idx[d] == N - 1 ? 1 : -1);
+    nrm[d] = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nn[d][c] = T(0);
+    if (fside[d] >= 0) {
+      nrm[d] = sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
+      const T sc = (fside[d] ? T(1) : T(-1)) / nrm[d];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nn[d][c] = sc * G[d][c];
+    }
+  }
+  const T half_w0inv = T(0.5) / S.w[0];
   // lifting of the auxiliary flux on every face through the node
 #pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, side = f & 1;
-    if (idx[d] != (side ? N - 1 : 0)) continue;
+  for (int d = 0; d < 3; ++d) {
+    if (fside[d] < 0) continue;
+    const int f = 2 * d + fside[d];
     int a1, a2;
     face_coords(d, i, j, k, a1, a2);
     const int ab = a2 * N + a1;
-    const T norm = sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
-    const T s = side ? T(1) : T(-1);
     const int t = S.type[f];
     const T uE = t == kNbr ? S.uE[f][ab] : (t == kDirichlet ? -up : (t == kNeumann ? up : T(0)));
-    const T lift = T(0.5) * (uE - up) * norm / S.w[0];
+    const T lift = (uE - up) * nrm[d] * half_w0inv;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] += s * G[d][c] / norm * lift;
+    for (int c = 0; c < 3; ++c) v[c] += nn[d][c] * lift;
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) S.v[c][p] = Kp * v[c];
@@ -134,20 +150,17 @@ __device__ T curved_element(CurvedSmem<N, T>& S, const T* __restrict__ geo, int6
   const T wp = S.w[i] * S.w[j] * S.w[k];
   T Au = -wp * J * div;
 #pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, side = f & 1;
-    if (idx[d] != (side ? N - 1 : 0)) continue;
+  for (int d = 0; d < 3; ++d) {
+    if (fside[d] < 0) continue;
+    const int side = fside[d], f = 2 * d + side;
     int a1, a2;
     face_coords(d, i, j, k, a1, a2);
     const int ab = a2 * N + a1;
-    const T norm = sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
-    const T s = side ? T(1) : T(-1);
     T ng = 0, nv = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const T nc = s * G[d][c] / norm;
-      ng += nc * g[c];
-      nv += nc * v[c];
+      ng += nn[d][c] * g[c];
+      nv += nn[d][c] * v[c];
     }
     ng *= Kp;  // n.F_u of the local gradient
     nv *= Kp;
@@ -157,7 +170,7 @@ __device__ T curved_element(CurvedSmem<N, T>& S, const T* __restrict__ geo, int6
     const T KE = t == kNbr ? geo[10 * ndof + (int64_t)S.eE[f] * (N * N2) + node_of<N>(d, side ? 0 : N - 1, a1, a2)]
                            : Kp;
     const T prim = T(0.5) * (ng - fE) - sigma_e[f * N2 + ab] * (Kp * up - KE * uE);
-    Au -= S.w[a1] * S.w[a2] * J * norm * (prim - nv);
+    Au -= S.w[a1] * S.w[a2] * J * nrm[d] * (prim - nv);
   }
   return Au;
 }
@@ -191,12 +204,11 @@ __global__ void __launch_bounds__(N * N * N) curved_trace_kernel(CurvedArgs<T> a
     if (idx[d] != (side ? N - 1 : 0)) continue;
     int a1, a2;
     face_coords(d, i, j, k, a1, a2);
-    const T norm = sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
-    const T s = side ? T(1) : T(-1);
+    const T sc = (side ? T(1) : T(-1)) / sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
     T ng = 0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) ng += s * G[d][c] / norm * (G[0][c] * du[0] + G[1][c] * du[1] + G[2][c] * du[2]);
-    a.trace[((int64_t)e * 6 + f) * N2 + a2 * N + a1] = Kp * ng;
+    for (int c = 0; c < 3; ++c) ng += G[d][c] * (G[0][c] * du[0] + G[1][c] * du[1] + G[2][c] * du[2]);
+    a.trace[((int64_t)e * 6 + f) * N2 + a2 * N + a1] = Kp * sc * ng;
   }
 }
 
@@ -275,12 +287,11 @@ __global__ void __launch_bounds__(N * N * N) curved_column_kernel(CurvedArgs<T> 
       if (idx[d] != (side ? N - 1 : 0)) continue;
       int a1, a2;
       face_coords(d, i, j, k, a1, a2);
-      const T norm = sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
-      const T s = side ? T(1) : T(-1);
+      const T sc = (side ? T(1) : T(-1)) / sqrt(G[d][0] * G[d][0] + G[d][1] * G[d][1] + G[d][2] * G[d][2]);
       T ng = 0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) ng += s * G[d][c] / norm * (G[0][c] * du[0] + G[1][c] * du[1] + G[2][c] * du[2]);
-      sTP[f][a2 * N + a1] = Kp * ng;
+      for (int c = 0; c < 3; ++c) ng += G[d][c] * (G[0][c] * du[0] + G[1][c] * du[1] + G[2][c] * du[2]);
+      sTP[f][a2 * N + a1] = Kp * sc * ng;
     }
     __syncthreads();
   }
