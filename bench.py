@@ -388,9 +388,18 @@ def curved_compare(dgg, workloads, torch, stream, steps):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         ms = sum(times) / len(times)
+        d.profile(True)
+        with torch.cuda.stream(stream):
+            u.zero_()
+            d.solve(b, u, TOL)
+        stream.synchronize()
+        prof = d.profile_read()
+        d.profile(False)
+        gm = prof["subdomain_gemm"]
         out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": rep.iterations,
                      "relative_residual": rep.relative_residual, "first_solve_with_setup_s": setup_s,
-                     "device_bytes": d.layout.device_bytes}
+                     "phases_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
+                     "subdomain_gemm_GB/s": gm["bytes"] / max(gm["ms"], 1e-12) / 1e6}
         d.close()
     # apply rates: the operator reads u and the metric (J and 9 G entries per node) and writes A u
     def rate(dom, prec, reps):

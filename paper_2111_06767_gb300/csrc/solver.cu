@@ -275,7 +275,8 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     }
     const bool linearized = linearized_level;
     auto gemm = [&](const T* X, T* Y) {
-      PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * sz + 2 * vec,
+      const double isz = (sizeof(T) == 4 && sw.inv16.get()) ? 2.0 : sz;  // FP16-stored inverses
+      PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * isz + 2 * vec,
                     2.0 * sw.nS * (double)sw.nS * L.E);
       class_gemm<T>(dom, L, X, Y, s);
     };
