@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <mutex>
 #include <set>
+#include <type_traits>
 
 #include "internal.h"
 #include "lines.cuh"
@@ -377,6 +378,245 @@ __global__ void __launch_bounds__(EPB* N* N) apply_line_kernel(const ApplyArgs<T
   apply_line_block<N, T, EPB, true>(A, blockIdx.x);
 }
 
+// ------------------------------------------------------------------ plane-per-thread apply (N = 4, FP32)
+//
+// The line kernel's y- and z-contractions read lines of other threads from shared memory, and at
+// N = 4 in FP32 its shared-memory wavefronts, not HBM, set the pace. For the plain apply at N = 4
+// a thread here owns one plane k of one element (16 points in 4 lines): the x- and y-contractions
+// run in registers and only the z-contractions read the element's other planes, which the four
+// threads of an element read together (broadcast) while the eight elements of a warp sit in
+// distinct banks (68-word element stride). The CTA's elements arrive by a coalesced copy into shared
+// memory; x-neighbours inside the CTA come from there, the others and the y/z neighbours' planes
+// from global memory (L1/L2). The z-neighbours' normal derivatives at the shared faces are summed
+// over the element's four threads with warp shuffles: thread k loads neighbour plane 3 - k, so the
+// thread on the face also holds the neighbour's face values.
+constexpr int kPlaneEPB = 32;     // elements per CTA (128 threads)
+constexpr int kPlaneStride = 68;  // words per element in shared memory
+
+__device__ __forceinline__ void plane_row(const float* p, float (&r)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+__device__ __forceinline__ void plane_row_g(const float* __restrict__ p, float (&r)[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+
+__global__ void __launch_bounds__(kPlaneEPB * 4) apply_plane4_kernel(const ApplyArgs<float> A) {
+  constexpr int N = 4, N3 = 64, NT = kPlaneEPB * 4;
+  constexpr int dO = dtab_off(N), wO = wtab_off(N);
+  using C = CTab<float>;
+  __shared__ __align__(16) float su[kPlaneEPB * kPlaneStride];
+  __shared__ __align__(16) float sv[kPlaneEPB * kPlaneStride];
+  const OpGeom<float>& g = A.g;
+  const float* __restrict__ u = A.u;
+  const int tid = threadIdx.x;
+  const int el = tid >> 2, k = tid & 3;
+  const int E = A.E;
+  const int e0 = blockIdx.x * kPlaneEPB;
+  const int n_el = min(kPlaneEPB, E - e0);
+  const int e = e0 + el;
+  const bool valid = el < n_el;
+  const int ec = valid ? e : E - 1;  // threads past the end compute on a real element, store nothing
+  pdl_launch_dependents();
+  pdl_wait();
+  {
+    const float4* src = reinterpret_cast<const float4*>(u + (int64_t)e0 * N3);
+    for (int q = tid; q < n_el * 16; q += NT)
+      *reinterpret_cast<float4*>(&su[(q >> 4) * kPlaneStride + (q & 15) * 4]) = __ldg(src + q);
+  }
+  const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
+  const int cx = ec % nx, cy = (ec / nx) % ny, cz = ec / nxy;
+  const bool hxm = cx > 0, hxp = cx + 1 < nx, hym = cy > 0, hyp = cy + 1 < ny, hzm = cz > 0, hzp = cz + 1 < g.nz;
+  // y-neighbour traces at the thread's plane: value on the shared face and normal derivative
+  float uym[4], gym[4], uyp[4], gyp[4];
+  {
+    float r[4][4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hym ? ec - nx : ec) * N3 + k * 16 + l * 4, r[l]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uym[i] = r[3][i];
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) a += C::D(dO + 3 * N + l) * r[l][i];
+      gym[i] = g.dxi[1] * a;
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hyp ? ec + nx : ec) * N3 + k * 16 + l * 4, r[l]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uyp[i] = r[0][i];
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) a += C::D(dO + l) * r[l][i];
+      gyp[i] = g.dxi[1] * a;
+    }
+  }
+  // z-neighbour traces on the thread's face plane (k = 0: z-, k = 3: z+), summed over the element's
+  // four threads
+  float uzE[4][4], gzE[4][4];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int nb = side ? (hzp ? ec + nxy : ec) : (hzm ? ec - nxy : ec);
+    const int pl = 3 - k;  // the neighbour plane this thread loads
+    float r[4][4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) plane_row_g(u + (int64_t)nb * N3 + pl * 16 + jj * 4, r[jj]);
+    const float cf = C::D(dO + (side ? 0 : 3 * N) + pl) * g.dxi[2];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float a = cf * r[jj][i];
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (k == (side ? 3 : 0)) {  // the face thread: plane 3 - k is the neighbour's face plane
+          uzE[jj][i] = r[jj][i];
+          gzE[jj][i] = a;
+        }
+      }
+  }
+  __syncthreads();  // the CTA's elements are in shared memory
+  // own plane and the x-neighbour lines of this plane (from shared memory inside the CTA)
+  float U[4][4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) plane_row(&su[el * kPlaneStride + k * 16 + jj * 4], U[jj]);
+  float uxm[4], gxm[4], uxp[4], gxp[4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    float r[4];
+    if (hxm && el > 0) plane_row(&su[(el - 1) * kPlaneStride + k * 16 + jj * 4], r);
+    else plane_row_g(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + k * 16 + jj * 4, r);
+    uxm[jj] = r[3];
+    float a = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) a += C::D(dO + 3 * N + l) * r[l];
+    gxm[jj] = g.dxi[0] * a;
+    if (hxp && el + 1 < n_el) plane_row(&su[(el + 1) * kPlaneStride + k * 16 + jj * 4], r);
+    else plane_row_g(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + k * 16 + jj * 4, r);
+    uxp[jj] = r[0];
+    a = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) a += C::D(dO + l) * r[l];
+    gxp[jj] = g.dxi[0] * a;
+  }
+  // local gradient: x along the thread's lines, y across them, z across the element's planes
+  float vx[4][4], vy[4][4], vz[4][4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float ax = 0.f, ay = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        ax += C::D(dO + i * N + l) * U[jj][l];
+        ay += C::D(dO + jj * N + l) * U[l][i];
+      }
+      vx[jj][i] = g.dxi[0] * ax;
+      vy[jj][i] = g.dxi[1] * ay;
+      vz[jj][i] = 0.f;
+    }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float dk = g.dxi[2] * C::D(dO + k * N + l);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      float r[4];
+      plane_row(&su[el * kPlaneStride + l * 16 + jj * 4], r);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) vz[jj][i] += dk * r[i];
+    }
+  }
+  // faces: lifting into v, primal fluxes into o (Eq. numflux with the ghost states of Eq. bc)
+  float o[4][4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[jj][i] = 0.f;
+  const float wk = C::w(wO + k);
+  {
+    const float smx = g.sigma[0] - g.lift[0], smy = g.sigma[1] - g.lift[1], smz = g.sigma[2] - g.lift[2];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const float Bf = g.Jf[0] * C::w(wO + jj) * wk;
+      vx[jj][0] = face_point(-1.f, U[jj][0], vx[jj][0], uxm[jj], gxm[jj], hxm, g.neumann & 1, g.lift[0], smx, Bf,
+                             o[jj][0]);
+      vx[jj][3] = face_point(1.f, U[jj][3], vx[jj][3], uxp[jj], gxp[jj], hxp, (g.neumann >> 1) & 1, g.lift[0], smx,
+                             Bf, o[jj][3]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float Bf = g.Jf[1] * C::w(wO + i) * wk;
+      vy[0][i] = face_point(-1.f, U[0][i], vy[0][i], uym[i], gym[i], hym, (g.neumann >> 2) & 1, g.lift[1], smy, Bf,
+                            o[0][i]);
+      vy[3][i] = face_point(1.f, U[3][i], vy[3][i], uyp[i], gyp[i], hyp, (g.neumann >> 3) & 1, g.lift[1], smy, Bf,
+                            o[3][i]);
+    }
+    if (k == 0 || k == 3) {
+      const float s = k ? 1.f : -1.f;
+      const bool has = k ? hzp : hzm;
+      const bool neu = (g.neumann >> (k ? 5 : 4)) & 1;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          vz[jj][i] = face_point(s, U[jj][i], vz[jj][i], uzE[jj][i], gzE[jj][i], has, neu, g.lift[2], smz,
+                                 g.Jf[2] * C::w(wO + i) * C::w(wO + jj), o[jj][i]);
+    }
+  }
+  // divergence: z across the planes of the lifted v_z
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj)
+    *reinterpret_cast<float4*>(&sv[el * kPlaneStride + k * 16 + jj * 4]) =
+        make_float4(vz[jj][0], vz[jj][1], vz[jj][2], vz[jj][3]);
+  __syncthreads();
+  float dz[4][4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dz[jj][i] = 0.f;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float dk = g.dxi[2] * C::D(dO + k * N + l);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      float r[4];
+      plane_row(&sv[el * kPlaneStride + l * 16 + jj * 4], r);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dz[jj][i] += dk * r[i];
+    }
+  }
+  if (!valid) return;
+  const int64_t base = (int64_t)ec * N3 + k * 16;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    float val[4], dl[4], bl[4];
+    if (A.diag) plane_row_g(A.diag + base + jj * 4, dl);
+    if (A.b) plane_row_g(A.b + base + jj * 4, bl);
+    const float M0 = g.J * C::w(wO + jj) * wk;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float dx = 0.f, dy = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        dx += C::D(dO + i * N + l) * vx[jj][l];
+        dy += C::D(dO + jj * N + l) * vy[l][i];
+      }
+      float res = -(M0 * C::w(wO + i)) * (g.dxi[0] * dx + g.dxi[1] * dy + dz[jj][i]) + o[jj][i];
+      if (A.diag) res += dl[i] * U[jj][i];
+      val[i] = A.b ? bl[i] - res : res;
+    }
+    *reinterpret_cast<float4*>(A.out + base + jj * 4) = make_float4(val[0], val[1], val[2], val[3]);
+  }
+}
+
 template <int N, typename T, int EPB>
 void launch_apply_epb(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
                       const SubdomainOut& so, int E, cudaStream_t s) {
@@ -400,6 +640,14 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
   constexpr int kSmall = N * N >= 32 ? 1 : (32 + N * N - 1) / (N * N);  // at least one warp per CTA
   constexpr int kBig = S::epb > kSmall ? S::epb : kSmall;
   constexpr int kMid = (kSmall + kBig) / 2;
+  if constexpr (N == 4 && std::is_same<T, float>::value) {
+    if (variant == 4 && !so.rS) {
+      const ApplyArgs<float> A{g, D, w, u, diag, b, out, E, nullptr, 0, 0, nullptr, nullptr, nullptr};
+      launch_pdl(apply_plane4_kernel, dim3((E + kPlaneEPB - 1) / kPlaneEPB), dim3(kPlaneEPB * 4), 0, s, A);
+      return;
+    }
+  }
+  if (variant == 4) variant = 0;  // the plane kernel covers the plain N = 4 FP32 apply only
   if (variant == 0) variant = ((E + kBig - 1) / kBig >= 2 * 152) ? 3 : 1;
   if (variant == 1) launch_apply_epb<N, T, kSmall>(g, D, w, u, diag, b, out, so, E, s);
   else if (variant == 2) launch_apply_epb<N, T, kMid>(g, D, w, u, diag, b, out, so, E, s);

@@ -24,7 +24,19 @@ template <typename T>
 int apply_variant(dg_domain* dom, Level& L, bool fused, const std::function<void(int)>& run, cudaStream_t s) {
   int& v = L.apply_variant[sizeof(T) == 4][fused];
   if (v < 0) {
-    const int pick = autotune({1, dom->N, (int64_t)sizeof(T), L.n[0], L.n[1], L.n[2], fused}, {0, 1, 2, 3}, run, s);
+    // launch shapes of the line kernel; the plane kernel for plain FP32 applies at N = 4
+    std::vector<int> cand{0, 1, 2, 3};
+    if (!fused && dom->N == 4 && sizeof(T) == 4) cand.push_back(4);
+    // DG_APPLY_VARIANT=v pins one candidate (tests of each launch shape)
+    static const int forced = [] {
+      const char* e = std::getenv("DG_APPLY_VARIANT");
+      return e ? std::atoi(e) : -1;
+    }();
+    if (forced >= 0 && std::find(cand.begin(), cand.end(), forced) != cand.end()) {
+      v = forced;
+      return v;
+    }
+    const int pick = autotune({1, dom->N, (int64_t)sizeof(T), L.n[0], L.n[1], L.n[2], fused}, cand, run, s);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     DG_CUDA(cudaStreamIsCapturing(s, &cap));
     if (cap != cudaStreamCaptureStatusNone) return pick;  // not tuned while capturing: ask again later

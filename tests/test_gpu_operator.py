@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import workloads
 from gpu_util import box, rand, rel
 from oracle import dg, mg
 
@@ -110,3 +111,59 @@ def test_krylov_dot_products_deterministic_and_accurate():
     assert np.array_equal(out1, out2)
     exact = np.array([math.fsum(V[k] * w) for k in range(7)])
     assert np.abs(out1 - exact).max() <= 1e-13 * np.abs(V).sum(axis=1).max()
+
+
+_PLANE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[2]); sys.path.insert(0, sys.argv[2] + "/tests")
+import workloads, paper_2111_06767_gb300 as dgg
+from gpu_util import box, rand
+out = {}
+cases = [((3, 2, 1), ()), ((5, 3, 4), ()), ((33, 2, 1), (1, 4)), ((7, 5, 3), (0, 2, 5)), ((1, 1, 1), ())]
+lower, upper = (-1.0, -0.5, 0.0), (1.0, 0.7, 2.5)
+for c, (n, neu) in enumerate(cases):
+    d = dgg.Domain(lower, upper, n, 4, mg_levels=1, overlap=1, neumann=neu)
+    u = rand(300 + c, (n[0] * n[1] * n[2], 4, 4, 4))
+    out[f"apply{c}"] = d.apply_f32(torch.from_numpy(u.ravel()).float().cuda()).double().cpu().numpy()
+d = dgg.Domain(n=(4, 4, 2), N=4, mg_levels=2, overlap=2, precision="mixed", gemm="simt")
+out["vcycle"] = d.vcycle(torch.from_numpy(rand(41, (32, 4, 4, 4)).ravel()).cuda()).cpu().numpy()
+dp = dgg.Domain((-20.0,) * 3, (20.0,) * 3, (4, 3, 2), 4, mg_levels=1, overlap=1, problem="puncture",
+                punctures=workloads.BINARY_PUNCTURES, precision="mixed")
+dp.set_linearization(torch.from_numpy(0.1 * rand(51, (24, 4, 4, 4)).ravel()).cuda())
+out["lin"] = dp.apply_f32(torch.from_numpy(rand(52, (24, 4, 4, 4)).ravel()).float().cuda()).double().cpu().numpy()
+np.savez(sys.argv[1], **out)
+"""
+
+
+@pytest.mark.parametrize("variant", ["4", "1"])
+def test_plane_kernel_matches_oracle(tmp_path, variant):
+    """The plain FP32 apply at N = 4 in its plane-per-thread form (DG_APPLY_VARIANT=4; 1 = a line-kernel
+    shape for comparison), pinned for every apply of the process: operator against the oracle on
+    ragged element counts (33 elements: one CTA of 32 plus one), Neumann faces and a single element,
+    the V-cycle's residual (b - A u) and the linearized puncture operator (+ diag u)."""
+    import os
+    import subprocess
+    import sys
+
+    from oracle import puncture, solve
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "plane.py"
+    script.write_text(_PLANE_SCRIPT)
+    f = tmp_path / "out.npz"
+    subprocess.run([sys.executable, str(script), str(f), root], env=dict(os.environ, DG_APPLY_VARIANT=variant),
+                   check=True, timeout=600)
+    got = np.load(f)
+    cases = [((3, 2, 1), ()), ((5, 3, 4), ()), ((33, 2, 1), (1, 4)), ((7, 5, 3), (0, 2, 5)), ((1, 1, 1), ())]
+    lower, upper = (-1.0, -0.5, 0.0), (1.0, 0.7, 2.5)
+    for c, (n, neu) in enumerate(cases):
+        grid = dg.BoxGrid(lower, upper, n, 4, 1.5, tuple(fc in neu for fc in range(6)))
+        u = rand(300 + c, (grid.n_elements, 4, 4, 4))
+        assert rel(got[f"apply{c}"], dg.apply(grid.graph(), u)) < 2e-5, (variant, n)
+    pr = solve.Problem(box((4, 4, 2), 4), mg_levels=2)
+    assert rel(got["vcycle"], pr.vcycle(rand(41, (32, 4, 4, 4)))) < 1e-4
+    gp = box((4, 3, 2), 4, lower=(-20.0,) * 3, upper=(20.0,) * 3)
+    pp = solve.PunctureProblem(gp, workloads.BINARY_PUNCTURES, mg_levels=1)
+    ul, v = 0.1 * rand(51, (24, 4, 4, 4)), rand(52, (24, 4, 4, 4))
+    ref = pp.apply(v) + pp.mass * puncture.source_deriv(ul, pp.alpha, pp.beta) * v
+    assert rel(got["lin"], ref) < 2e-5
