@@ -378,17 +378,18 @@ __global__ void __launch_bounds__(EPB* N* N) apply_line_kernel(const ApplyArgs<T
   apply_line_block<N, T, EPB, true>(A, blockIdx.x);
 }
 
-// ------------------------------------------------------------------ plane-per-thread apply (N = 4, FP32)
+// ------------------------------------------------------------------ slice-per-thread apply (N = 4, FP32)
 //
 // The line kernel's y- and z-contractions read lines of other threads from shared memory, and at
 // N = 4 in FP32 its shared-memory wavefronts, not HBM, set the pace. For the plain apply at N = 4
-// a thread here owns one plane k of one element (16 points in 4 lines): the x- and y-contractions
-// run in registers and only the z-contractions read the element's other planes, which the four
-// threads of an element read together (broadcast) while the eight elements of a warp sit in
-// distinct banks (68-word element stride). The CTA's elements arrive by a coalesced copy into shared
-// memory; x-neighbours inside the CTA come from there, the others and the y/z neighbours' planes
-// from global memory (L1/L2). The z-neighbours' normal derivatives at the shared faces are summed
-// over the element's four threads with warp shuffles: thread k loads neighbour plane 3 - k, so the
+// a thread here owns one x-z slice (fixed y index q: the four x-lines of the four z-planes, 16
+// points) of one element: the x- and z-contractions run in registers and only the y-contractions
+// read the element's other slices from shared memory, where the four threads of an element read
+// the same addresses (broadcast) and the eight elements of a warp sit in distinct banks (68-word
+// element stride). The four threads of an element load their slices as one contiguous 64-byte
+// run per plane, for the element itself and for every neighbour. x-neighbours inside the CTA are
+// read back from shared memory; the y-neighbours' normal derivatives at the shared faces are summed
+// over the element's four threads with warp shuffles: thread q loads neighbour slice 3 - q, so the
 // thread on the face also holds the neighbour's face values.
 constexpr int kPlaneEPB = 32;     // elements per CTA (128 threads)
 constexpr int kPlaneStride = 68;  // words per element in shared memory
@@ -408,7 +409,7 @@ __device__ __forceinline__ void plane_row_g(const float* __restrict__ p, float (
   r[3] = v.w;
 }
 
-__global__ void __launch_bounds__(kPlaneEPB * 4) apply_plane4_kernel(const ApplyArgs<float> A) {
+__global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const ApplyArgs<float> A) {
   constexpr int N = 4, N3 = 64, NT = kPlaneEPB * 4;
   constexpr int dO = dtab_off(N), wO = wtab_off(N);
   using C = CTab<float>;
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kPlaneEPB * 4) apply_plane4_kernel(const Apply
   const OpGeom<float>& g = A.g;
   const float* __restrict__ u = A.u;
   const int tid = threadIdx.x;
-  const int el = tid >> 2, k = tid & 3;
+  const int el = tid >> 2, q = tid & 3;  // element of the CTA, y index of the thread's slice
   const int E = A.E;
   const int e0 = blockIdx.x * kPlaneEPB;
   const int n_el = min(kPlaneEPB, E - e0);
@@ -426,194 +427,194 @@ __global__ void __launch_bounds__(kPlaneEPB * 4) apply_plane4_kernel(const Apply
   const int ec = valid ? e : E - 1;  // threads past the end compute on a real element, store nothing
   pdl_launch_dependents();
   pdl_wait();
-  {
-    const float4* src = reinterpret_cast<const float4*>(u + (int64_t)e0 * N3);
-    for (int q = tid; q < n_el * 16; q += NT)
-      *reinterpret_cast<float4*>(&su[(q >> 4) * kPlaneStride + (q & 15) * 4]) = __ldg(src + q);
-  }
   const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
   const int cx = ec % nx, cy = (ec / nx) % ny, cz = ec / nxy;
   const bool hxm = cx > 0, hxp = cx + 1 < nx, hym = cy > 0, hyp = cy + 1 < ny, hzm = cz > 0, hzp = cz + 1 < g.nz;
-  // y-neighbour traces at the thread's plane: value on the shared face and normal derivative
-  float uym[4], gym[4], uyp[4], gyp[4];
+  // own slice: U[kk][i] = u(i, q, kk)
+  float U[4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) plane_row_g(u + (int64_t)ec * N3 + kk * 16 + q * 4, U[kk]);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    *reinterpret_cast<float4*>(&su[el * kPlaneStride + kk * 16 + q * 4]) =
+        make_float4(U[kk][0], U[kk][1], U[kk][2], U[kk][3]);
+  // z-neighbour traces on the slice's face rows (kk = 0: z-, kk = 3: z+), in the thread
+  float uzm[4], gzm[4], uzp[4], gzp[4];
   {
     float r[4][4];
 #pragma unroll
-    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hym ? ec - nx : ec) * N3 + k * 16 + l * 4, r[l]);
+    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hzm ? ec - nxy : ec) * N3 + l * 16 + q * 4, r[l]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      uym[i] = r[3][i];
+      uzm[i] = r[3][i];
       float a = 0.f;
 #pragma unroll
       for (int l = 0; l < 4; ++l) a += C::D(dO + 3 * N + l) * r[l][i];
-      gym[i] = g.dxi[1] * a;
+      gzm[i] = g.dxi[2] * a;
     }
 #pragma unroll
-    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hyp ? ec + nx : ec) * N3 + k * 16 + l * 4, r[l]);
+    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hzp ? ec + nxy : ec) * N3 + l * 16 + q * 4, r[l]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      uyp[i] = r[0][i];
+      uzp[i] = r[0][i];
       float a = 0.f;
 #pragma unroll
       for (int l = 0; l < 4; ++l) a += C::D(dO + l) * r[l][i];
-      gyp[i] = g.dxi[1] * a;
+      gzp[i] = g.dxi[2] * a;
     }
   }
-  // z-neighbour traces on the thread's face plane (k = 0: z-, k = 3: z+), summed over the element's
+  // y-neighbour traces on the element's y faces (q = 0: y-, q = 3: y+), summed over the element's
   // four threads
-  float uzE[4][4], gzE[4][4];
+  float uyE[4][4], gyE[4][4];
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    const int nb = side ? (hzp ? ec + nxy : ec) : (hzm ? ec - nxy : ec);
-    const int pl = 3 - k;  // the neighbour plane this thread loads
+    const int nb = side ? (hyp ? ec + nx : ec) : (hym ? ec - nx : ec);
+    const int sl = 3 - q;  // the neighbour slice this thread loads
     float r[4][4];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) plane_row_g(u + (int64_t)nb * N3 + pl * 16 + jj * 4, r[jj]);
-    const float cf = C::D(dO + (side ? 0 : 3 * N) + pl) * g.dxi[2];
+    for (int kk = 0; kk < 4; ++kk) plane_row_g(u + (int64_t)nb * N3 + kk * 16 + sl * 4, r[kk]);
+    const float cf = C::D(dO + (side ? 0 : 3 * N) + sl) * g.dxi[1];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj)
+    for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        float a = cf * r[jj][i];
+        float a = cf * r[kk][i];
         a += __shfl_xor_sync(0xffffffffu, a, 1);
         a += __shfl_xor_sync(0xffffffffu, a, 2);
-        if (k == (side ? 3 : 0)) {  // the face thread: plane 3 - k is the neighbour's face plane
-          uzE[jj][i] = r[jj][i];
-          gzE[jj][i] = a;
+        if (q == (side ? 3 : 0)) {  // the face thread: slice 3 - q is the neighbour's face slice
+          uyE[kk][i] = r[kk][i];
+          gyE[kk][i] = a;
         }
       }
   }
-  __syncthreads();  // the CTA's elements are in shared memory
-  // own plane and the x-neighbour lines of this plane (from shared memory inside the CTA)
-  float U[4][4];
-#pragma unroll
-  for (int jj = 0; jj < 4; ++jj) plane_row(&su[el * kPlaneStride + k * 16 + jj * 4], U[jj]);
+  __syncthreads();  // the CTA's slices are in shared memory
+  // x-neighbour lines of this slice (from shared memory inside the CTA)
   float uxm[4], gxm[4], uxp[4], gxp[4];
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
+  for (int kk = 0; kk < 4; ++kk) {
     float r[4];
-    if (hxm && el > 0) plane_row(&su[(el - 1) * kPlaneStride + k * 16 + jj * 4], r);
-    else plane_row_g(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + k * 16 + jj * 4, r);
-    uxm[jj] = r[3];
+    if (hxm && el > 0) plane_row(&su[(el - 1) * kPlaneStride + kk * 16 + q * 4], r);
+    else plane_row_g(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + kk * 16 + q * 4, r);
+    uxm[kk] = r[3];
     float a = 0.f;
 #pragma unroll
     for (int l = 0; l < 4; ++l) a += C::D(dO + 3 * N + l) * r[l];
-    gxm[jj] = g.dxi[0] * a;
-    if (hxp && el + 1 < n_el) plane_row(&su[(el + 1) * kPlaneStride + k * 16 + jj * 4], r);
-    else plane_row_g(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + k * 16 + jj * 4, r);
-    uxp[jj] = r[0];
+    gxm[kk] = g.dxi[0] * a;
+    if (hxp && el + 1 < n_el) plane_row(&su[(el + 1) * kPlaneStride + kk * 16 + q * 4], r);
+    else plane_row_g(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + kk * 16 + q * 4, r);
+    uxp[kk] = r[0];
     a = 0.f;
 #pragma unroll
     for (int l = 0; l < 4; ++l) a += C::D(dO + l) * r[l];
-    gxp[jj] = g.dxi[0] * a;
+    gxp[kk] = g.dxi[0] * a;
   }
-  // local gradient: x along the thread's lines, y across them, z across the element's planes
+  // local gradient: x along the thread's lines, z across its planes, y across the element's slices
   float vx[4][4], vy[4][4], vz[4][4];
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj)
+  for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      float ax = 0.f, ay = 0.f;
+      float ax = 0.f, az = 0.f;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
-        ax += C::D(dO + i * N + l) * U[jj][l];
-        ay += C::D(dO + jj * N + l) * U[l][i];
+        ax += C::D(dO + i * N + l) * U[kk][l];
+        az += C::D(dO + kk * N + l) * U[l][i];
       }
-      vx[jj][i] = g.dxi[0] * ax;
-      vy[jj][i] = g.dxi[1] * ay;
-      vz[jj][i] = 0.f;
+      vx[kk][i] = g.dxi[0] * ax;
+      vz[kk][i] = g.dxi[2] * az;
+      vy[kk][i] = 0.f;
     }
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
-    const float dk = g.dxi[2] * C::D(dO + k * N + l);
+    const float dq = g.dxi[1] * C::D(dO + q * N + l);
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int kk = 0; kk < 4; ++kk) {
       float r[4];
-      plane_row(&su[el * kPlaneStride + l * 16 + jj * 4], r);
+      plane_row(&su[el * kPlaneStride + kk * 16 + l * 4], r);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) vz[jj][i] += dk * r[i];
+      for (int i = 0; i < 4; ++i) vy[kk][i] += dq * r[i];
     }
   }
   // faces: lifting into v, primal fluxes into o (Eq. numflux with the ghost states of Eq. bc)
   float o[4][4];
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj)
+  for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) o[jj][i] = 0.f;
-  const float wk = C::w(wO + k);
+    for (int i = 0; i < 4; ++i) o[kk][i] = 0.f;
+  const float wq = C::w(wO + q);
   {
     const float smx = g.sigma[0] - g.lift[0], smy = g.sigma[1] - g.lift[1], smz = g.sigma[2] - g.lift[2];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const float Bf = g.Jf[0] * C::w(wO + jj) * wk;
-      vx[jj][0] = face_point(-1.f, U[jj][0], vx[jj][0], uxm[jj], gxm[jj], hxm, g.neumann & 1, g.lift[0], smx, Bf,
-                             o[jj][0]);
-      vx[jj][3] = face_point(1.f, U[jj][3], vx[jj][3], uxp[jj], gxp[jj], hxp, (g.neumann >> 1) & 1, g.lift[0], smx,
-                             Bf, o[jj][3]);
+    for (int kk = 0; kk < 4; ++kk) {
+      const float Bf = g.Jf[0] * wq * C::w(wO + kk);
+      vx[kk][0] = face_point(-1.f, U[kk][0], vx[kk][0], uxm[kk], gxm[kk], hxm, g.neumann & 1, g.lift[0], smx, Bf,
+                             o[kk][0]);
+      vx[kk][3] = face_point(1.f, U[kk][3], vx[kk][3], uxp[kk], gxp[kk], hxp, (g.neumann >> 1) & 1, g.lift[0], smx,
+                             Bf, o[kk][3]);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const float Bf = g.Jf[1] * C::w(wO + i) * wk;
-      vy[0][i] = face_point(-1.f, U[0][i], vy[0][i], uym[i], gym[i], hym, (g.neumann >> 2) & 1, g.lift[1], smy, Bf,
+      const float Bf = g.Jf[2] * C::w(wO + i) * wq;
+      vz[0][i] = face_point(-1.f, U[0][i], vz[0][i], uzm[i], gzm[i], hzm, (g.neumann >> 4) & 1, g.lift[2], smz, Bf,
                             o[0][i]);
-      vy[3][i] = face_point(1.f, U[3][i], vy[3][i], uyp[i], gyp[i], hyp, (g.neumann >> 3) & 1, g.lift[1], smy, Bf,
+      vz[3][i] = face_point(1.f, U[3][i], vz[3][i], uzp[i], gzp[i], hzp, (g.neumann >> 5) & 1, g.lift[2], smz, Bf,
                             o[3][i]);
     }
-    if (k == 0 || k == 3) {
-      const float s = k ? 1.f : -1.f;
-      const bool has = k ? hzp : hzm;
-      const bool neu = (g.neumann >> (k ? 5 : 4)) & 1;
+    if (q == 0 || q == 3) {
+      const float s = q ? 1.f : -1.f;
+      const bool has = q ? hyp : hym;
+      const bool neu = (g.neumann >> (q ? 3 : 2)) & 1;
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj)
+      for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          vz[jj][i] = face_point(s, U[jj][i], vz[jj][i], uzE[jj][i], gzE[jj][i], has, neu, g.lift[2], smz,
-                                 g.Jf[2] * C::w(wO + i) * C::w(wO + jj), o[jj][i]);
+          vy[kk][i] = face_point(s, U[kk][i], vy[kk][i], uyE[kk][i], gyE[kk][i], has, neu, g.lift[1], smy,
+                                 g.Jf[1] * C::w(wO + i) * C::w(wO + kk), o[kk][i]);
     }
   }
-  // divergence: z across the planes of the lifted v_z
+  // divergence: y across the slices of the lifted v_y
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj)
-    *reinterpret_cast<float4*>(&sv[el * kPlaneStride + k * 16 + jj * 4]) =
-        make_float4(vz[jj][0], vz[jj][1], vz[jj][2], vz[jj][3]);
+  for (int kk = 0; kk < 4; ++kk)
+    *reinterpret_cast<float4*>(&sv[el * kPlaneStride + kk * 16 + q * 4]) =
+        make_float4(vy[kk][0], vy[kk][1], vy[kk][2], vy[kk][3]);
   __syncthreads();
-  float dz[4][4];
+  float dy[4][4];
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj)
+  for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) dz[jj][i] = 0.f;
+    for (int i = 0; i < 4; ++i) dy[kk][i] = 0.f;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
-    const float dk = g.dxi[2] * C::D(dO + k * N + l);
+    const float dq = g.dxi[1] * C::D(dO + q * N + l);
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int kk = 0; kk < 4; ++kk) {
       float r[4];
-      plane_row(&sv[el * kPlaneStride + l * 16 + jj * 4], r);
+      plane_row(&sv[el * kPlaneStride + kk * 16 + l * 4], r);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) dz[jj][i] += dk * r[i];
+      for (int i = 0; i < 4; ++i) dy[kk][i] += dq * r[i];
     }
   }
   if (!valid) return;
-  const int64_t base = (int64_t)ec * N3 + k * 16;
+  const int64_t base = (int64_t)ec * N3 + q * 4;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
+  for (int kk = 0; kk < 4; ++kk) {
     float val[4], dl[4], bl[4];
-    if (A.diag) plane_row_g(A.diag + base + jj * 4, dl);
-    if (A.b) plane_row_g(A.b + base + jj * 4, bl);
-    const float M0 = g.J * C::w(wO + jj) * wk;
+    if (A.diag) plane_row_g(A.diag + base + kk * 16, dl);
+    if (A.b) plane_row_g(A.b + base + kk * 16, bl);
+    const float M0 = g.J * wq * C::w(wO + kk);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      float dx = 0.f, dy = 0.f;
+      float dx = 0.f, dz = 0.f;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
-        dx += C::D(dO + i * N + l) * vx[jj][l];
-        dy += C::D(dO + jj * N + l) * vy[l][i];
+        dx += C::D(dO + i * N + l) * vx[kk][l];
+        dz += C::D(dO + kk * N + l) * vz[l][i];
       }
-      float res = -(M0 * C::w(wO + i)) * (g.dxi[0] * dx + g.dxi[1] * dy + dz[jj][i]) + o[jj][i];
-      if (A.diag) res += dl[i] * U[jj][i];
+      float res = -(M0 * C::w(wO + i)) * (g.dxi[0] * dx + dy[kk][i] + g.dxi[2] * dz) + o[kk][i];
+      if (A.diag) res += dl[i] * U[kk][i];
       val[i] = A.b ? bl[i] - res : res;
     }
-    *reinterpret_cast<float4*>(A.out + base + jj * 4) = make_float4(val[0], val[1], val[2], val[3]);
+    *reinterpret_cast<float4*>(A.out + base + kk * 16) = make_float4(val[0], val[1], val[2], val[3]);
   }
 }
 
