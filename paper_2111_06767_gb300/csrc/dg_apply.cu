@@ -383,14 +383,14 @@ __global__ void __launch_bounds__(EPB* N* N) apply_line_kernel(const ApplyArgs<T
 // The line kernel's y- and z-contractions read lines of other threads from shared memory, and at
 // N = 4 in FP32 its shared-memory wavefronts, not HBM, set the pace. For the plain apply at N = 4
 // a thread here owns one x-z slice (fixed y index q: the four x-lines of the four z-planes, 16
-// points) of one element: the x- and z-contractions run in registers and only the y-contractions
-// read the element's other slices from shared memory, where the four threads of an element read
-// the same addresses (broadcast) and the eight elements of a warp sit in distinct banks (68-word
-// element stride). The four threads of an element load their slices as one contiguous 64-byte
-// run per plane, for the element itself and for every neighbour. x-neighbours inside the CTA are
-// read back from shared memory; the y-neighbours' normal derivatives at the shared faces are summed
-// over the element's four threads with warp shuffles: thread q loads neighbour slice 3 - q, so the
-// thread on the face also holds the neighbour's face values.
+// points) of one element: the x- and z-contractions run in registers and the y-contractions take
+// the other three slices of the element from the neighbouring lanes with warp shuffles (the four
+// threads of an element are consecutive lanes). The four threads of an element load their slices
+// as one contiguous 64-byte run per plane, for the element itself and for every neighbour;
+// x-neighbours inside the CTA are read back from shared memory (68-word element stride, distinct
+// banks); the y-neighbours' normal derivatives at the shared faces are summed over the element's
+// four threads with shuffles as well: thread q loads neighbour slice 3 - q, so the thread on the
+// face also holds the neighbour's face values.
 constexpr int kPlaneEPB = 32;     // elements per CTA (128 threads)
 constexpr int kPlaneStride = 68;  // words per element in shared memory
 
@@ -414,7 +414,6 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
   constexpr int dO = dtab_off(N), wO = wtab_off(N);
   using C = CTab<float>;
   __shared__ __align__(16) float su[kPlaneEPB * kPlaneStride];
-  __shared__ __align__(16) float sv[kPlaneEPB * kPlaneStride];
   const OpGeom<float>& g = A.g;
   const float* __restrict__ u = A.u;
   const int tid = threadIdx.x;
@@ -524,17 +523,25 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
       vz[kk][i] = g.dxi[2] * az;
       vy[kk][i] = 0.f;
     }
+  // row q of Dhat (times 2/h_y) in partner order: Dy[m] multiplies the slice of thread q ^ m
+  float Dy[4];
 #pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    const float dq = g.dxi[1] * C::D(dO + q * N + l);
+  for (int m = 0; m < 4; ++m) {
+    float d = 0.f;
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      float r[4];
-      plane_row(&su[el * kPlaneStride + kk * 16 + l * 4], r);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) vy[kk][i] += dq * r[i];
-    }
+    for (int qq = 0; qq < 4; ++qq)  // compile-time constant-memory addresses, selected per lane
+      if (qq == q) d = C::D(dO + qq * N + (qq ^ m));
+    Dy[m] = g.dxi[1] * d;
   }
+  // y across the element's slices: the other three threads' values by warp shuffles
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float x = U[kk][i];
+      vy[kk][i] = Dy[0] * x + Dy[1] * __shfl_xor_sync(0xffffffffu, x, 1) + Dy[2] * __shfl_xor_sync(0xffffffffu, x, 2) +
+                  Dy[3] * __shfl_xor_sync(0xffffffffu, x, 3);
+    }
   // faces: lifting into v, primal fluxes into o (Eq. numflux with the ghost states of Eq. bc)
   float o[4][4];
 #pragma unroll
@@ -572,28 +579,16 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
                                  g.Jf[1] * C::w(wO + i) * C::w(wO + kk), o[kk][i]);
     }
   }
-  // divergence: y across the slices of the lifted v_y
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk)
-    *reinterpret_cast<float4*>(&sv[el * kPlaneStride + kk * 16 + q * 4]) =
-        make_float4(vy[kk][0], vy[kk][1], vy[kk][2], vy[kk][3]);
-  __syncthreads();
+  // divergence: y across the slices of the lifted v_y, by warp shuffles
   float dy[4][4];
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) dy[kk][i] = 0.f;
-#pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    const float dq = g.dxi[1] * C::D(dO + q * N + l);
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      float r[4];
-      plane_row(&sv[el * kPlaneStride + kk * 16 + l * 4], r);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) dy[kk][i] += dq * r[i];
+    for (int i = 0; i < 4; ++i) {
+      const float x = vy[kk][i];
+      dy[kk][i] = Dy[0] * x + Dy[1] * __shfl_xor_sync(0xffffffffu, x, 1) + Dy[2] * __shfl_xor_sync(0xffffffffu, x, 2) +
+                  Dy[3] * __shfl_xor_sync(0xffffffffu, x, 3);
     }
-  }
   if (!valid) return;
   const int64_t base = (int64_t)ec * N3 + q * 4;
 #pragma unroll
