@@ -618,6 +618,18 @@ def run_ours(args):
         "fp32_hbm_frac": 8.0 * g32 / hbm, "fp64_hbm_frac": 16.0 * g64 / hbm,
         "fp64_alu_bound_gdofs": 1.2e12 / (12 * 4 + 12) / 1e9}
     big.close()
+    # the sweep over N at about the same size (u + A u far above L2): GDOF/s and the fraction of the
+    # HBM copy rate counting u and A u (8 B/DOF in FP32, 16 in FP64)
+    if args.apply_sweep:
+        sweep = {}
+        for Ns, ns in ((4, 96), (5, 77), (6, 64), (7, 55), (8, 48), (9, 43)):
+            dm = dgg.Domain(n=(ns,) * 3, N=Ns, penalty=1.5, precision="mixed", mg_levels=1, overlap=1, stream=stream)
+            r64, r32 = apply_rate(dm, "fp64", 3)[0], apply_rate(dm, "fp32", 5)[0]
+            sweep[f"N{Ns}_{ns}cubed"] = {"dof": dm.n_dof, "fp32_gdofs": r32, "fp32_hbm_frac": 8.0 * r32 / hbm,
+                                         "fp64_gdofs": r64, "fp64_hbm_frac": 16.0 * r64 / hbm,
+                                         "fp64_flop_rate_tflops": r64 * (12 * Ns + 12) / 1e3}
+            dm.close()
+        apply["sweep"] = sweep
 
     # ---- roofline of the dominant kernel phase of the timed solves
     dom_phase = max(prof, key=lambda k: prof[k]["ms"])
@@ -717,6 +729,8 @@ def main():
                     help="prefix of the batched stream also solved in plain FP64 for the mixed/FP64 ratio")
     ap.add_argument("--puncture-steps", type=int, default=2,
                     help="timed solves of the 16^3 puncture workload per subdomain solver (0: skip)")
+    ap.add_argument("--no-apply-sweep", dest="apply_sweep", action="store_false",
+                    help="skip the DG-apply sweep over N = 4..9 at about 56M DOF")
     ap.add_argument("--curved-steps", type=int, default=3,
                     help="timed mixed solves of the warped-mesh workload (0: skip the curved leg)")
     args = ap.parse_args()
