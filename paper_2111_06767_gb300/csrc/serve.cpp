@@ -26,6 +26,7 @@ struct Job {
   uint64_t ticket = 0;
   dg_request req{};
   std::vector<double> f;
+  std::vector<double> xyz, coef;  // copies of per-node geometry / coefficient (curved domains)
   size_t bytes = 0;
   double submit_time = 0, admit_time = 0, finish_time = 0;
   dg_status status = DG_PENDING;
@@ -64,8 +65,16 @@ size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations, bool l
       classes = (size_t)std::min(n[0], 5) * std::min(n[1], 5) * std::min(n[2], 5);
     }
     classes = std::min(classes, E);
-    build_peak = std::max(build_peak, classes * nS * nS * 8);  // FP64 build, freed after inversion
-    total += classes * ld * ld * fb;                            // stored inverses
+    if (d.node_xyz || d.coef) {
+      // every subdomain has its own inverse, compact; MIXED keeps FP16 copies (FP32 with "simt"),
+      // built in the smoother's precision; plus the nodal metric, face-node penalty and traces
+      const size_t store = mixed ? (d.subdomain_gemm == DG_GEMM_SIMT ? 4 : 2) : 8;
+      build_peak = std::max(build_peak, E * nS * nS * (mixed ? 4 : 8));
+      total += E * nS * nS * store + ndof * (11 * 12 + 8) + E * 6 * N * N * 24;
+    } else {
+      build_peak = std::max(build_peak, classes * nS * nS * 8);  // FP64 build, freed after inversion
+      total += classes * ld * ld * fb;                            // stored inverses
+    }
     total += 2 * E * ld * fb + 3 * ndof * fb + 4 * E * 4;       // r_S, du_S, b, u, r, tables
     if ((d.mg_levels && l + 1 == d.mg_levels) || (n[0] % 2 && n[1] % 2 && n[2] % 2)) break;
     for (int i = 0; i < 3; ++i)
@@ -205,7 +214,6 @@ dg_status elliptic_serve_submit(dg_server* srv, const dg_request* req, uint64_t*
   const dg_domain_desc& d = req->domain;
   if (d.N < 2 || d.N > DG_MAX_N || d.n[0] < 1 || d.n[1] < 1 || d.n[2] < 1) return DG_ERR_INVALID_ARG;
   if (d.problem == DG_PROBLEM_POISSON && !req->f_host) return DG_ERR_INVALID_ARG;
-  if (d.node_xyz || d.coef) return DG_ERR_INVALID_ARG;  // per-node geometry or coefficients are not copied
   const int max_it = req->opts.max_iterations > 0 ? req->opts.max_iterations : 200;
   if (req->opts.subdomain_solver != 0 && req->opts.subdomain_solver != 1) return DG_ERR_INVALID_ARG;
   const size_t bytes = dg::estimate_domain_bytes(d, max_it, req->opts.subdomain_solver == 1);
@@ -223,6 +231,20 @@ dg_status elliptic_serve_submit(dg_server* srv, const dg_request* req, uint64_t*
     }
   }
   job->req.f_host = nullptr;
+  if (d.node_xyz || d.coef) {
+    // per-node geometry and coefficient are copied as the source is; the queued descriptor points at
+    // the copies, which live as long as the job
+    const size_t ndof = (size_t)d.n[0] * d.n[1] * d.n[2] * d.N * d.N * d.N;
+    try {
+      if (d.node_xyz) job->xyz.assign(d.node_xyz, d.node_xyz + 3 * ndof);
+      if (d.coef) job->coef.assign(d.coef, d.coef + ndof);
+    } catch (...) {
+      delete job;
+      return DG_ERR_OOM;
+    }
+    job->req.domain.node_xyz = d.node_xyz ? job->xyz.data() : nullptr;
+    job->req.domain.coef = d.coef ? job->coef.data() : nullptr;
+  }
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stopping || bytes > srv->budget) {

@@ -95,3 +95,47 @@ def test_queue_errors():
             busy += 1
     assert busy >= 3
     srv.close()
+
+
+def test_curved_coefficient_and_neumann_requests_in_the_mix():
+    """Requests with curved elements (node coordinates), a variable coefficient and Neumann faces are
+    served beside plain ones; the server copies the per-node arrays at submission, and every result
+    equals the same request solved alone."""
+    warp = lambda X, Y, Z: (X + 0.1 * (1 - X**2) * Y, Y + 0.12 * (1 - Y**2) * Z * X, Z + 0.1 * (1 - Z**2) * (X + Y))
+    specs = [dict(n=(4, 4, 4), N=4, mapping=warp), dict(n=(3, 3, 3), N=5, coef=True),
+             dict(n=(4, 4, 4), N=4, neumann=(0, 1)), dict(n=(2, 2, 2), N=6),
+             dict(n=(2, 3, 2), N=4, mapping=warp, coef=True, neumann=(4,))]
+    srv = dgg.Server(max_active=3, n_streams=3)
+    jobs = []
+    for i, sp in enumerate(specs):
+        grid = box(sp["n"], sp["N"])
+        x, y, z = grid.coordinates()
+        xyz = warp(x, y, z) if sp.get("mapping") else None
+        px, py, pz = xyz if xyz else (x, y, z)
+        coef = 1.0 + 0.5 * px**2 + 0.2 * np.tanh(py * pz) if sp.get("coef") else None
+        kw = dict(precision="fp64", overlap=2, neumann=sp.get("neumann", ()), node_xyz=xyz, coef=coef)
+        desc = dgg.make_desc((-1.0,) * 3, (1.0,) * 3, sp["n"], sp["N"], **kw)
+        f = workloads.gaussian_source(20 + i)(px, py, pz).ravel()
+        jobs.append((srv.submit(desc, f, tol=1e-10), sp, kw, f))
+        del desc  # the server holds its own copies
+    results = {}
+    t0 = time.time()
+    while len(results) < len(jobs) and time.time() - t0 < 300:
+        for t, sp, kw, f in jobs:
+            if t in results:
+                continue
+            u = np.empty(int(np.prod(sp["n"])) * sp["N"] ** 3)
+            st, res = srv.poll(t, u)
+            if st != _native.DG_PENDING:
+                results[t] = (st, res.report.relative_residual, u)
+        time.sleep(0.01)
+    assert len(results) == len(jobs)
+    for t, sp, kw, f in jobs:
+        st, relres, u = results[t]
+        assert st == _native.DG_OK and relres <= 1e-10, sp
+        d = dgg.Domain((-1.0,) * 3, (1.0,) * 3, sp["n"], sp["N"], **kw)
+        b = d.rhs(torch.from_numpy(f).cuda())
+        ua = torch.zeros_like(b)
+        d.solve(b, ua, 1e-10, opts=dgg.solve_opts(relative_to_b=True))
+        assert rel(u, ua.cpu().numpy()) < 1e-12, sp
+    srv.close()
