@@ -41,7 +41,8 @@ typedef enum dg_status {
   DG_ERR_BREAKDOWN = -5,      /* non-finite residual or Krylov breakdown without convergence */
   DG_ERR_TIMEOUT = -6,        /* a bounded device wait gave up */
   DG_ERR_BUSY = -7,           /* serving queue full: retry later */
-  DG_ERR_NOT_FOUND = -8       /* unknown serving ticket */
+  DG_ERR_NOT_FOUND = -8,      /* unknown serving ticket */
+  DG_ERR_CANCELLED = -9       /* served request cancelled before it finished */
 } dg_status;
 
 enum { DG_MAX_N = 10, DG_MAX_LEVELS = 8, DG_MAX_PUNCTURES = 4 };
@@ -314,6 +315,11 @@ dg_status elliptic_serve_submit(struct dg_server* srv, const dg_request* req, ui
  * with the report, times and (if out->u_host is set) the solution copied out. A finished ticket
  * is released by the poll that returns it. */
 dg_status elliptic_serve_poll(struct dg_server* srv, uint64_t ticket, dg_result* out);
+/* Cancel a request: one still waiting leaves the queue; one running stops at its next Krylov
+ * iteration (the solve checks between iterations, never inside a kernel). Its poll then returns
+ * DG_ERR_CANCELLED. A request that has already finished keeps its result. DG_ERR_NOT_FOUND for an
+ * unknown or already released ticket. */
+dg_status elliptic_serve_cancel(struct dg_server* srv, uint64_t ticket);
 /* Seconds on the server's clock (for latency bookkeeping). */
 double elliptic_serve_clock(const struct dg_server* srv);
 /* Stop accepting, finish what is admitted, join the workers and free everything. NULL-safe. */

@@ -281,6 +281,10 @@ class Server:
         st = _lib.elliptic_serve_poll(self._h, C.c_uint64(ticket), C.byref(res))
         return st, res
 
+    def cancel(self, ticket):
+        """Cancel a waiting or running request (its poll then returns DG_ERR_CANCELLED)."""
+        return _lib.elliptic_serve_cancel(self._h, C.c_uint64(ticket))
+
     def clock(self):
         return _lib.elliptic_serve_clock(self._h)
 

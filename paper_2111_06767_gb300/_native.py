@@ -10,9 +10,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdg_elliptic.so")
 
 DG_OK, DG_PENDING = 0, 1
+DG_ERR_CANCELLED = -9
 STATUS_NAMES = {0: "DG_OK", 1: "DG_PENDING", -1: "DG_ERR_INVALID_ARG", -2: "DG_ERR_OOM", -3: "DG_ERR_CUDA",
                 -4: "DG_ERR_NOT_CONVERGED", -5: "DG_ERR_BREAKDOWN", -6: "DG_ERR_TIMEOUT", -7: "DG_ERR_BUSY",
-                -8: "DG_ERR_NOT_FOUND"}
+                -8: "DG_ERR_NOT_FOUND", -9: "DG_ERR_CANCELLED"}
 DG_MAX_N, DG_MAX_LEVELS, DG_MAX_PUNCTURES = 10, 8, 4
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 PROBLEM_POISSON, PROBLEM_PUNCTURE = 0, 1
@@ -105,6 +106,7 @@ SIGNATURES = {
     "elliptic_serve_create": (C.c_int, [C.POINTER(dg_serve_desc), C.POINTER(_vp)]),
     "elliptic_serve_submit": (C.c_int, [_vp, C.POINTER(dg_request), C.POINTER(C.c_uint64)]),
     "elliptic_serve_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(dg_result)]),
+    "elliptic_serve_cancel": (C.c_int, [_vp, C.c_uint64]),
     "elliptic_serve_clock": (C.c_double, [_vp]),
     "elliptic_serve_destroy": (None, [_vp]),
 }

@@ -2,6 +2,8 @@
 // workspace. Host-side definitions shared by the setup, solver and C-ABI translation units.
 #pragma once
 
+#include <atomic>
+
 #include <vector_types.h>
 
 #include "internal.h"
@@ -133,6 +135,7 @@ struct dg_domain {
   int subdomain_iterations = 3;
   dg::Profiler prof;
   int subdomain_solver = 0;  // linearized finest-level subdomain problems: 0 GMRES, 1 per-subdomain inverses
+  const std::atomic<bool>* cancel = nullptr;  // set by a serving worker: stop between Krylov iterations
   bool linv_current = false; // per-subdomain inverses built for the current linearization
   bool use_tc = false;       // subdomain GEMM on tcgen05 tensor cores (MIXED)
   bool coarse_fused = false; // fused cooperative smoother on coarse levels (DG_COARSE_FUSED=1 turns it on)

@@ -6,6 +6,7 @@
 // and publish the result; admission happens whenever a worker and enough budget free up, so
 // requests that arrive while others run join the device work as capacity allows. poll() hands a
 // finished result back exactly once.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -27,6 +28,7 @@ struct Job {
   dg_request req{};
   std::vector<double> f;
   std::vector<double> xyz, coef;  // copies of per-node geometry / coefficient (curved domains)
+  std::atomic<bool> cancel{false};
   size_t bytes = 0;
   double submit_time = 0, admit_time = 0, finish_time = 0;
   dg_status status = DG_PENDING;
@@ -151,7 +153,9 @@ void dg_server::run(int wid) {
         if (st == DG_OK) {
           dg_solve_opts o = job->req.opts;
           o.relative_to_b = job->req.domain.problem == DG_PROBLEM_POISSON ? 1 : 0;
+          dom->cancel = &job->cancel;
           st = elliptic_solve(dom, b, u, job->req.tol, &o, &job->report);
+          dom->cancel = nullptr;
         }
         job->u.resize(lay.n_dof);
         if (cudaMemcpyAsync(job->u.data(), u, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -287,6 +291,26 @@ dg_status elliptic_serve_poll(dg_server* srv, uint64_t ticket, dg_result* out) {
   }
   delete job;
   return st;
+}
+
+dg_status elliptic_serve_cancel(dg_server* srv, uint64_t ticket) {
+  if (!srv) return DG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->jobs.find(ticket);
+  if (it == srv->jobs.end()) return DG_ERR_NOT_FOUND;
+  Job* job = it->second;
+  if (job->status != DG_PENDING) return DG_OK;  // finished: the result stands
+  job->cancel.store(true);
+  for (auto w = srv->waiting.begin(); w != srv->waiting.end(); ++w) {
+    if (*w != job) continue;
+    // never admitted: leave the queue now
+    srv->waiting.erase(w);
+    job->status = DG_ERR_CANCELLED;
+    job->report.status = DG_ERR_CANCELLED;
+    job->finish_time = clock_now() - srv->t0;
+    break;
+  }
+  return DG_OK;
 }
 
 double elliptic_serve_clock(const dg_server* srv) { return srv ? clock_now() - srv->t0 : 0.0; }

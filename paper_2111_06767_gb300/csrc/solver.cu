@@ -553,6 +553,7 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
   int k = 0;
   std::vector<double> hh(2 * (max_it + 2) + 1);
   for (int j = 0; j < max_it; ++j) {
+    if (dom->cancel && dom->cancel->load(std::memory_order_relaxed)) { R.status = DG_ERR_CANCELLED; break; }
     ensure_workspace(dom, j + 1);  // may move V and Z (contents kept)
     double* V = dom->V.get();
     double* Z = dom->Zb.get();
@@ -643,6 +644,7 @@ LinearResult fcg(dg_domain* dom, const double* b, double* x, double tol, double 
   if (!std::isfinite(beta)) { R.status = DG_ERR_BREAKDOWN; return R; }
   double res = beta, pq_old = 0.0;
   for (int k = 0; k < max_it && res > tol * ref && res > 0.0; ++k) {
+    if (dom->cancel && dom->cancel->load(std::memory_order_relaxed)) { R.status = DG_ERR_CANCELLED; break; }
     precondition(dom, pmode, r, z, s);
     if (k == 0) {
       DG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -805,7 +807,7 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
       LinearResult L = o.krylov == 1 ? fcg(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false)
                                      : fgmres(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false);
       R.iterations += L.iterations;
-      if (L.status == DG_ERR_BREAKDOWN) { R.status = L.status; break; }
+      if (L.status == DG_ERR_BREAKDOWN || L.status == DG_ERR_CANCELLED) { R.status = L.status; break; }
       double lam = 1.0, rn_new = 0.0;
       for (int bt = 0; bt <= 10; ++bt) {
         DG_CUDA(cudaMemcpyAsync(dom->ut.get(), u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));

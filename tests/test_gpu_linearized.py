@@ -114,3 +114,22 @@ def test_newton_with_per_subdomain_inverses_matches_oracle(precision):
         its = sum(info["iterations"] for info in rep_ref["linear_iterations"])
         assert rep.newton_steps == rep_ref["steps"]
         assert abs(rep.iterations - its) <= rep.newton_steps
+
+
+def test_per_subdomain_inverses_that_do_not_fit_report_oom():
+    """36^3 elements, N = 6, overlap 5 (n_S = 1296): the per-subdomain linearized inverses would need
+    46,656 x 1296^2 x 4 B = 313 GB, more than the device holds. The linearization reports
+    DG_ERR_OOM (an allocation that fails, no fault), and the domain keeps working with the default
+    subdomain solver."""
+    d = dgg.Domain((-20.0,) * 3, (20.0,) * 3, (36, 36, 36), 6, precision="mixed", mg_levels=1, overlap=5,
+                   problem="puncture", punctures=P)
+    u = torch.zeros(d.n_dof, dtype=torch.float64, device="cuda")
+    d.set_subdomain_solver("inverse")
+    with pytest.raises(dgg.NativeError) as info:
+        d.set_linearization(u)
+    assert info.value.status == -2  # DG_ERR_OOM
+    d.set_subdomain_solver("gmres", 3)
+    d.set_linearization(u)
+    b = torch.ones_like(u)
+    out = d.schwarz_smooth(0, b, torch.zeros_like(u), 1)
+    assert torch.isfinite(out).all() and float(out.abs().max()) > 0

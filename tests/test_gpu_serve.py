@@ -139,3 +139,35 @@ def test_curved_coefficient_and_neumann_requests_in_the_mix():
         d.solve(b, ua, 1e-10, opts=dgg.solve_opts(relative_to_b=True))
         assert rel(u, ua.cpu().numpy()) < 1e-12, sp
     srv.close()
+
+
+def test_cancel_waiting_and_running_requests():
+    """With one worker: a long FP64 request is cancelled while it runs (the solve stops at its next
+    Krylov iteration), a queued one is cancelled before admission, and the remaining request is
+    served as if alone; tickets that were never issued report NOT_FOUND."""
+    srv = dgg.Server(max_active=1, n_streams=1)
+    long_desc, long_f = _request("poisson", 8, 8, 30)  # FP64 8^3, N = 8: a few hundred ms
+    short_desc, short_f = _request("poisson", 2, 4, 31)
+    t_long = srv.submit(long_desc, long_f, tol=1e-10)
+    t_queued = srv.submit(short_desc, short_f, tol=1e-10)
+    t_kept = srv.submit(short_desc, short_f, tol=1e-10)
+    assert srv.cancel(t_queued) == 0
+    time.sleep(0.15)  # the long request is admitted at once and runs for several hundred ms
+    assert srv.cancel(t_long) == 0
+    status = {}
+    t0 = time.time()
+    while len(status) < 3 and time.time() - t0 < 120:
+        for t in (t_long, t_queued, t_kept):
+            if t in status:
+                continue
+            u = np.empty(2**3 * 4**3) if t == t_kept else None
+            st, res = srv.poll(t, u)
+            if st != _native.DG_PENDING:
+                status[t] = (st, u, res.report.iterations)
+        time.sleep(0.01)
+    assert status[t_queued][0] == _native.DG_ERR_CANCELLED
+    assert status[t_long][0] == _native.DG_ERR_CANCELLED
+    assert status[t_kept][0] == _native.DG_OK
+    assert rel(status[t_kept][1], _alone(short_desc, short_f, 1e-10)) < 1e-12
+    assert srv.cancel(10**9) == -8 and srv.poll(10**9)[0] == -8
+    srv.close()
