@@ -391,17 +391,17 @@ __global__ void __launch_bounds__(EPB* N* N) apply_line_kernel(const ApplyArgs<T
 // banks); the y-neighbours' normal derivatives at the shared faces are summed over the element's
 // four threads with shuffles as well: thread q loads neighbour slice 3 - q, so the thread on the
 // face also holds the neighbour's face values.
-constexpr int kPlaneEPB = 32;     // elements per CTA (128 threads)
-constexpr int kPlaneStride = 68;  // words per element in shared memory
+constexpr int kSliceEPB = 32;     // elements per CTA (128 threads)
+constexpr int kSliceStride = 68;  // words per element in shared memory
 
-__device__ __forceinline__ void plane_row(const float* p, float (&r)[4]) {
+__device__ __forceinline__ void row4(const float* p, float (&r)[4]) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   r[0] = v.x;
   r[1] = v.y;
   r[2] = v.z;
   r[3] = v.w;
 }
-__device__ __forceinline__ void plane_row_g(const float* __restrict__ p, float (&r)[4]) {
+__device__ __forceinline__ void row4_g(const float* __restrict__ p, float (&r)[4]) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
   r[0] = v.x;
   r[1] = v.y;
@@ -409,18 +409,18 @@ __device__ __forceinline__ void plane_row_g(const float* __restrict__ p, float (
   r[3] = v.w;
 }
 
-__global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const ApplyArgs<float> A) {
-  constexpr int N = 4, N3 = 64, NT = kPlaneEPB * 4;
+__global__ void __launch_bounds__(kSliceEPB * 4, 4) apply_slice4_kernel(const ApplyArgs<float> A) {
+  constexpr int N = 4, N3 = 64;
   constexpr int dO = dtab_off(N), wO = wtab_off(N);
   using C = CTab<float>;
-  __shared__ __align__(16) float su[kPlaneEPB * kPlaneStride];
+  __shared__ __align__(16) float su[kSliceEPB * kSliceStride];
   const OpGeom<float>& g = A.g;
   const float* __restrict__ u = A.u;
   const int tid = threadIdx.x;
   const int el = tid >> 2, q = tid & 3;  // element of the CTA, y index of the thread's slice
   const int E = A.E;
-  const int e0 = blockIdx.x * kPlaneEPB;
-  const int n_el = min(kPlaneEPB, E - e0);
+  const int e0 = blockIdx.x * kSliceEPB;
+  const int n_el = min(kSliceEPB, E - e0);
   const int e = e0 + el;
   const bool valid = el < n_el;
   const int ec = valid ? e : E - 1;  // threads past the end compute on a real element, store nothing
@@ -432,17 +432,17 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
   // own slice: U[kk][i] = u(i, q, kk)
   float U[4][4];
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) plane_row_g(u + (int64_t)ec * N3 + kk * 16 + q * 4, U[kk]);
+  for (int kk = 0; kk < 4; ++kk) row4_g(u + (int64_t)ec * N3 + kk * 16 + q * 4, U[kk]);
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk)
-    *reinterpret_cast<float4*>(&su[el * kPlaneStride + kk * 16 + q * 4]) =
+    *reinterpret_cast<float4*>(&su[el * kSliceStride + kk * 16 + q * 4]) =
         make_float4(U[kk][0], U[kk][1], U[kk][2], U[kk][3]);
   // z-neighbour traces on the slice's face rows (kk = 0: z-, kk = 3: z+), in the thread
   float uzm[4], gzm[4], uzp[4], gzp[4];
   {
     float r[4][4];
 #pragma unroll
-    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hzm ? ec - nxy : ec) * N3 + l * 16 + q * 4, r[l]);
+    for (int l = 0; l < 4; ++l) row4_g(u + (int64_t)(hzm ? ec - nxy : ec) * N3 + l * 16 + q * 4, r[l]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       uzm[i] = r[3][i];
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
       gzm[i] = g.dxi[2] * a;
     }
 #pragma unroll
-    for (int l = 0; l < 4; ++l) plane_row_g(u + (int64_t)(hzp ? ec + nxy : ec) * N3 + l * 16 + q * 4, r[l]);
+    for (int l = 0; l < 4; ++l) row4_g(u + (int64_t)(hzp ? ec + nxy : ec) * N3 + l * 16 + q * 4, r[l]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       uzp[i] = r[0][i];
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
     const int sl = 3 - q;  // the neighbour slice this thread loads
     float r[4][4];
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) plane_row_g(u + (int64_t)nb * N3 + kk * 16 + sl * 4, r[kk]);
+    for (int kk = 0; kk < 4; ++kk) row4_g(u + (int64_t)nb * N3 + kk * 16 + sl * 4, r[kk]);
     const float cf = C::D(dO + (side ? 0 : 3 * N) + sl) * g.dxi[1];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)
@@ -492,15 +492,15 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     float r[4];
-    if (hxm && el > 0) plane_row(&su[(el - 1) * kPlaneStride + kk * 16 + q * 4], r);
-    else plane_row_g(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + kk * 16 + q * 4, r);
+    if (hxm && el > 0) row4(&su[(el - 1) * kSliceStride + kk * 16 + q * 4], r);
+    else row4_g(u + (int64_t)(hxm ? ec - 1 : ec) * N3 + kk * 16 + q * 4, r);
     uxm[kk] = r[3];
     float a = 0.f;
 #pragma unroll
     for (int l = 0; l < 4; ++l) a += C::D(dO + 3 * N + l) * r[l];
     gxm[kk] = g.dxi[0] * a;
-    if (hxp && el + 1 < n_el) plane_row(&su[(el + 1) * kPlaneStride + kk * 16 + q * 4], r);
-    else plane_row_g(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + kk * 16 + q * 4, r);
+    if (hxp && el + 1 < n_el) row4(&su[(el + 1) * kSliceStride + kk * 16 + q * 4], r);
+    else row4_g(u + (int64_t)(hxp ? ec + 1 : ec) * N3 + kk * 16 + q * 4, r);
     uxp[kk] = r[0];
     a = 0.f;
 #pragma unroll
@@ -594,8 +594,8 @@ __global__ void __launch_bounds__(kPlaneEPB * 4, 4) apply_plane4_kernel(const Ap
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     float val[4], dl[4], bl[4];
-    if (A.diag) plane_row_g(A.diag + base + kk * 16, dl);
-    if (A.b) plane_row_g(A.b + base + kk * 16, bl);
+    if (A.diag) row4_g(A.diag + base + kk * 16, dl);
+    if (A.b) row4_g(A.b + base + kk * 16, bl);
     const float M0 = g.J * wq * C::w(wO + kk);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -639,7 +639,7 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
   if constexpr (N == 4 && std::is_same<T, float>::value) {
     if (variant == 4 && !so.rS) {
       const ApplyArgs<float> A{g, D, w, u, diag, b, out, E, nullptr, 0, 0, nullptr, nullptr, nullptr};
-      launch_pdl(apply_plane4_kernel, dim3((E + kPlaneEPB - 1) / kPlaneEPB), dim3(kPlaneEPB * 4), 0, s, A);
+      launch_pdl(apply_slice4_kernel, dim3((E + kSliceEPB - 1) / kSliceEPB), dim3(kSliceEPB * 4), 0, s, A);
       return;
     }
   }
