@@ -107,9 +107,13 @@ __device__ __forceinline__ void scatter_element(const SubdomainGeom& g, const T*
     const T* sh = sh0 + (size_t)p * 7;
     auto du = [&](int64_t i) { return L2ONLY ? __ldcg(duS + i) : duS[i]; };
     T acc = sh[0] * du((int64_t)s_col[0] * ld + __ldg(inv + s_inv[0] + p));
+    // the neighbour across face f covers this point only within N_overlap layers of that face
+    const int c[3] = {p % g.N, (p / g.N) % g.N, p / (g.N * g.N)};
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       if (s_col[1 + f] < 0) continue;
+      const int cd = c[f >> 1];
+      if (((f & 1) ? g.N - 1 - cd : cd) >= g.ov) continue;
       const int row = __ldg(inv + s_inv[1 + f] + p);
       if (row >= 0) acc += sh[1 + f] * du((int64_t)s_col[1 + f] * ld + row);
     }
