@@ -4,12 +4,14 @@
 // timed ones, and the fastest is kept; it replaces hand-picked launch heuristics and has no
 // counterpart in the paper), the stream of this thread's allocations, and the switch for
 // programmatic dependent launch.
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <map>
 #include <mutex>
 #include <set>
+#include <string>
 
 #include "internal.h"
 
@@ -20,6 +22,15 @@ std::mutex g_tune_mu;
 std::map<std::vector<int64_t>, int> g_tuned;
 
 thread_local cudaStream_t tl_alloc_stream = nullptr;
+
+// DG_TUNE_LOG=1: one line on stderr per tuned shape with the candidate kept and every candidate's time.
+bool tune_log() {
+  static const bool on = [] {
+    const char* v = std::getenv("DG_TUNE_LOG");
+    return v && std::strcmp(v, "1") == 0;
+  }();
+  return on;
+}
 
 bool tuning_enabled() {
   const char* v = std::getenv("DG_AUTOTUNE");
@@ -82,6 +93,7 @@ int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates
   }
   int best = candidates[0];
   float best_ms = std::numeric_limits<float>::infinity();
+  std::string timings;
   try {
     for (int c : candidates) {
       run(c);  // warm-up (first launch of a kernel pays for module loading)
@@ -91,6 +103,7 @@ int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates
       DG_CUDA(cudaEventSynchronize(b));
       float ms = 0.0f;
       DG_CUDA(cudaEventElapsedTime(&ms, a, b));
+      timings += " " + std::to_string(c) + ":" + std::to_string(ms / 3.0f * 1e3f);
       if (ms < best_ms) {
         best_ms = ms;
         best = c;
@@ -104,6 +117,12 @@ int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (tune_log()) {
+    std::string line = "dg autotune key";
+    for (int64_t v : key) line += " " + std::to_string(v);
+    line += ": picked " + std::to_string(best) + "; us per launch" + timings + "\n";
+    std::fputs(line.c_str(), stderr);
+  }
   return g_tuned.emplace(k, best).first->second;
 }
 

@@ -209,6 +209,15 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
       // split-K factor: the default (0) first, then every split the shape allows
       std::vector<int> cand{0};
       for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(sp);
+      // DG_GEMM_SPLIT=k pins one candidate (tests and measurements of each launch shape); read
+      // when a level first runs its GEMM, so a process can set it per domain
+      const char* e = std::getenv("DG_GEMM_SPLIT");
+      const int forced = e ? std::atoi(e) : -1;
+      if (forced >= 0 && std::find(cand.begin(), cand.end(), forced) != cand.end()) {
+        L.gemm_split = forced;
+        run(forced);
+        return;
+      }
       const int pick = autotune({2, sw.n_classes, sw.ld, sw.n_tiles_tc, L.E}, cand, run, s);
       cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
       DG_CUDA(cudaStreamIsCapturing(s, &cap));
