@@ -25,6 +25,7 @@ paper's order and notation, so it can be checked against the paper by eye:
 
 Parity status: the DG operator, transfers, Schwarz weights, FGMRES and Newton are pinned by
 the `-m "not gpu"` tests (closed forms, invariants, dense direct solves, manufactured
-solutions). The puncture physics values (alpha, beta) are parity unpinned beyond their
-closed-form limits: the paper prints no values for them.
+solutions). The puncture fields (alpha, beta), for which the paper prints no values, are pinned
+by the Bowen-York invariants (traceless, divergence-free curvature whose surface integrals give
+the punctures' linear and angular momenta) and the closed form of 1/alpha.
 """

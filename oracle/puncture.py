@@ -9,8 +9,10 @@ curvature:
     beta    = alpha^7 A_ij A^ij / 8
 
 and the equation  -Laplace(u) + S(u) = 0  with  S(u) = -beta (1 + alpha (1 + u))^-7,
-S'(u) = 7 alpha beta (1 + alpha (1 + u))^-8.  Parity unpinned for the values of alpha and
-beta (no printed values); pinned only by their closed-form limits.
+S'(u) = 7 alpha beta (1 + alpha (1 + u))^-8.  The paper prints no values for alpha and beta;
+they are pinned by physics instead: the curvature beta is built from is traceless and
+divergence-free and carries, through its surface integrals, the linear and orbital angular
+momenta of the punctures, and 1/alpha is checked against its closed form.
 """
 from __future__ import annotations
 

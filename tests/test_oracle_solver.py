@@ -350,23 +350,28 @@ def test_line_search_backtracks_on_overshoot():
 
 # ---------------------------------------------------------------- puncture data
 
+def _bowen_york_abar(X, punctures):
+    """Conformal traceless extrinsic curvature of Bowen-York punctures without spin, summed over the
+    punctures, at points X (..., 3)."""
+    out = np.zeros(X.shape[:-1] + (3, 3))
+    for q in punctures:
+        dx = X - np.asarray(q.position)
+        r = np.linalg.norm(dx, axis=-1)
+        l = dx / r[..., None]
+        P = np.asarray(q.momentum)
+        Pl = l @ P
+        out += 1.5 / r[..., None, None] ** 2 * (np.einsum("i,...j->...ij", P, l) + np.einsum("...i,j->...ij", l, P)
+                                                - (np.eye(3) - np.einsum("...i,...j->...ij", l, l)) * Pl[..., None, None])
+    return out
+
+
 def test_bowen_york_curvature_traceless_and_divergence_free():
     p = workloads.BINARY_PUNCTURES
     pts = np.array([[0.3, 0.7, -1.1], [5.0, -2.0, 1.0]])
     eps = 1e-4
 
     def abar(X):
-        x, y, z = X[..., 0], X[..., 1], X[..., 2]
-        out = np.zeros(X.shape[:-1] + (3, 3))
-        for q in p:
-            dx = X - np.asarray(q.position)
-            r = np.linalg.norm(dx, axis=-1)
-            l = dx / r[..., None]
-            P = np.asarray(q.momentum)
-            Pl = l @ P
-            out += 1.5 / r[..., None, None] ** 2 * (np.einsum("i,...j->...ij", P, l) + np.einsum("...i,j->...ij", l, P)
-                                                    - (np.eye(3) - np.einsum("...i,...j->...ij", l, l)) * Pl[..., None, None])
-        return out
+        return _bowen_york_abar(X, p)
 
     A = abar(pts)
     assert np.abs(np.trace(A, axis1=-2, axis2=-1)).max() < 1e-15
@@ -381,3 +386,37 @@ def test_bowen_york_curvature_traceless_and_divergence_free():
     assert np.allclose(beta, alpha**7 * np.einsum("...ij,...ij->...", A, A) / 8, rtol=1e-14)
     r = [np.linalg.norm(pts - np.asarray(q.position), axis=-1) for q in p]
     assert np.allclose(1 / alpha, 0.5 / (2 * r[0]) + 0.5 / (2 * r[1]), rtol=1e-15)
+
+
+def test_bowen_york_adm_momenta():
+    """The curvature carries the momenta it is built from: the surface integrals
+    P^i = (1/8 pi) oint A^ij n_j dA and J_i = (1/8 pi) oint eps_ijk x^j A^kl n_l dA over a sphere give
+    the linear momentum of the punctures inside it and their orbital angular momentum C x P (the
+    3/2 normalisation, which tracelessness and zero divergence leave free, is fixed by this).
+    Gauss-Legendre in cos(theta) x uniform in phi; the integrands are smooth on these spheres."""
+    p = workloads.BINARY_PUNCTURES
+    ct, wt = np.polynomial.legendre.leggauss(48)
+    ph = np.arange(96) * (2 * np.pi / 96)
+    st = np.sqrt(1 - ct**2)
+    n = np.stack([st[:, None] * np.cos(ph)[None, :], st[:, None] * np.sin(ph)[None, :],
+                  np.broadcast_to(ct[:, None], (48, 96))], axis=-1)
+    dOmega = wt[:, None] * np.full(96, 2 * np.pi / 96)[None, :]
+
+    def integrals(center, R):
+        X = np.asarray(center) + R * n
+        A = _bowen_york_abar(X, p)
+        An = np.einsum("...ij,...j->...i", A, n)
+        P = np.einsum("ab,abi->i", dOmega, An) * R**2 / (8 * np.pi)
+        J = np.einsum("ab,abi->i", dOmega, np.cross(X, An)) * R**2 / (8 * np.pi)
+        return P, J
+
+    # a sphere around each puncture alone: its own momentum
+    for q in p:
+        P, _ = integrals(q.position, 1.0)
+        assert np.allclose(P, q.momentum, atol=1e-12)
+    # a sphere around both: total momentum and orbital angular momentum sum_n C_n x P_n
+    P, J = integrals((0.0, 0.0, 0.0), 10.0)
+    assert np.allclose(P, sum(np.asarray(q.momentum) for q in p), atol=1e-12)
+    J_ref = sum(np.cross(q.position, q.momentum) for q in p)
+    assert np.allclose(J, J_ref, atol=1e-12)
+    assert abs(J_ref[2]) > 0.1  # the binary orbits: a nonzero reference
