@@ -18,8 +18,6 @@
 // Missing neighbours keep their slots as padding (identity rows and columns in A_S, zero data),
 // so every subdomain has n_S = N^3 + 6 N_ov N^2.
 #include <limits>
-#include <map>
-#include <mutex>
 
 #include "internal.h"
 #include "pdl.cuh"
@@ -497,81 +495,86 @@ void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4*
 // diagonal linearization term) is solved by GMRES from du_S = 0 for a fixed number of iterations,
 // right-preconditioned by the explicit inverse of the Poisson subdomain matrix A_S (the
 // Laplacian approximation). With z = A_S^-1 v, (A_S + D_S) z = v + D_S z, so every iteration is
-// one class GEMM plus per-subdomain vector work. One CTA per subdomain column.
+// one class GEMM plus per-subdomain vector work. One warp per subdomain column (8 per CTA): the
+// reductions are warp shuffles in a fixed order, with no CTA barrier, and every subdomain of a
+// level is resident at once.
 
+constexpr int kSubWarps = 8;  // subdomain columns (warps) per CTA
+
+// Sum over the warp's lanes in a fixed order, returned to every lane.
 template <typename T>
-__device__ __forceinline__ T block_sum(T v, T* red) {
+__device__ __forceinline__ T warp_total(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  T t = 0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-  return t;
+  return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // V_0 = r_S / ||r_S|| per column; beta[col] = ||r_S||
 template <typename T>
-__global__ void sub_normalize_kernel(int nS, const T* __restrict__ rS, T* __restrict__ V0, T* __restrict__ beta) {
-  __shared__ T red[32];
-  const int col = blockIdx.x;
+__global__ void __launch_bounds__(32 * kSubWarps)
+    sub_normalize_kernel(int E, int nS, const T* __restrict__ rS, T* __restrict__ V0, T* __restrict__ beta) {
+  const int col = blockIdx.x * kSubWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (col >= E) return;  // whole warps
   const T* r = rS + (size_t)col * nS;
   T acc = 0;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) acc += r[i] * r[i];
-  const T nrm = sqrt(block_sum(acc, red));
+  for (int i = lane; i < nS; i += 32) acc += r[i] * r[i];
+  const T nrm = sqrt(warp_total(acc));
   const T inv = nrm > T(0) ? T(1) / nrm : T(0);
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) V0[(size_t)col * nS + i] = r[i] * inv;
-  if (threadIdx.x == 0) beta[col] = nrm;
+  for (int i = lane; i < nS; i += 32) V0[(size_t)col * nS + i] = r[i] * inv;
+  if (lane == 0) beta[col] = nrm;
 }
 
 // Arnoldi step j: w = V_j + D Z_j, modified Gram-Schmidt against V_0..V_j, V_{j+1} = w / ||w||.
-// H is [col][m+1][m]; V and Z are blocks of E*nS values per basis index.
+// H is [col][m+1][m]; V and Z are blocks of E*nS values per basis index. w is built in place in
+// V_{j+1}; every lane reads back only the entries it wrote.
 template <typename T>
-__global__ void sub_arnoldi_kernel(int nS, int64_t stride, int j, int m, const T* __restrict__ D, T* __restrict__ V,
-                                   const T* __restrict__ Z, T* __restrict__ H) {
-  extern __shared__ unsigned char smem_raw[];
-  T* w = reinterpret_cast<T*>(smem_raw);
-  __shared__ T red[32];
-  const int col = blockIdx.x;
+__global__ void __launch_bounds__(32 * kSubWarps)
+    sub_arnoldi_kernel(int E, int nS, int64_t stride, int j, int m, const T* __restrict__ D, T* V,
+                       const T* __restrict__ Z, T* __restrict__ H) {
+  const int col = blockIdx.x * kSubWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (col >= E) return;  // whole warps
   const size_t off = (size_t)col * nS;
   const T* vj = V + (size_t)j * stride + off;
   const T* zj = Z + (size_t)j * stride + off;
+  T* w = V + (size_t)(j + 1) * stride + off;
   T acc0 = 0;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) {
-    w[i] = vj[i] + D[off + i] * zj[i];
-    acc0 += w[i] * w[i];
+  for (int i = lane; i < nS; i += 32) {
+    const T x = vj[i] + D[off + i] * zj[i];
+    w[i] = x;
+    acc0 += x * x;
   }
-  const T w0 = sqrt(block_sum(acc0, red));  // ||w|| before orthogonalisation
+  const T w0 = sqrt(warp_total(acc0));  // ||w|| before orthogonalisation
   T* h = H + (size_t)col * (m + 1) * m;
   for (int i = 0; i <= j; ++i) {
     const T* vi = V + (size_t)i * stride + off;
     T acc = 0;
-    for (int t = threadIdx.x; t < nS; t += blockDim.x) acc += w[t] * vi[t];
-    const T hij = block_sum(acc, red);
-    for (int t = threadIdx.x; t < nS; t += blockDim.x) w[t] -= hij * vi[t];
-    if (threadIdx.x == 0) h[i * m + j] = hij;
-    __syncthreads();
+    for (int t = lane; t < nS; t += 32) acc += w[t] * vi[t];
+    const T hij = warp_total(acc);
+    for (int t = lane; t < nS; t += 32) w[t] -= hij * vi[t];
+    if (lane == 0) h[i * m + j] = hij;
   }
   T acc = 0;
-  for (int t = threadIdx.x; t < nS; t += blockDim.x) acc += w[t] * w[t];
-  T hn = sqrt(block_sum(acc, red));
+  for (int t = lane; t < nS; t += 32) acc += w[t] * w[t];
+  T hn = sqrt(warp_total(acc));
   // what is left after orthogonalisation at the level of the cancellation error is rounding noise,
   // not a new direction: treat it as a (happy) breakdown so that the least-squares step ignores it
   if (hn <= T(64) * std::numeric_limits<T>::epsilon() * w0) hn = T(0);
-  if (threadIdx.x == 0) h[(j + 1) * m + j] = hn;
+  if (lane == 0) h[(j + 1) * m + j] = hn;
   const T inv = hn > T(0) ? T(1) / hn : T(0);
-  T* vn = V + (size_t)(j + 1) * stride + off;
-  for (int t = threadIdx.x; t < nS; t += blockDim.x) vn[t] = w[t] * inv;
+  for (int t = lane; t < nS; t += 32) w[t] *= inv;
 }
 
-// y = argmin || beta e1 - H y || (Givens, in registers of thread 0), then du_S = sum_j y_j Z_j.
+// y = argmin || beta e1 - H y || (Givens, by lane 0 of the column's warp), then du_S = sum_j y_j Z_j.
 template <typename T>
-__global__ void sub_lsq_combine_kernel(int nS, int64_t stride, int m, const T* __restrict__ beta,
-                                       const T* __restrict__ H, const T* __restrict__ Z, T* __restrict__ duS) {
-  __shared__ T y[16];
-  const int col = blockIdx.x;
-  if (threadIdx.x == 0) {
+__global__ void __launch_bounds__(32 * kSubWarps)
+    sub_lsq_combine_kernel(int E, int nS, int64_t stride, int m, const T* __restrict__ beta,
+                           const T* __restrict__ H, const T* __restrict__ Z, T* __restrict__ duS) {
+  __shared__ T ys[kSubWarps][16];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = blockIdx.x * kSubWarps + wid;
+  if (col >= E) return;  // whole warps
+  T* y = ys[wid];
+  if (lane == 0) {
     T R[17][16], g[17];
     const T* h = H + (size_t)col * (m + 1) * m;
     for (int i = 0; i <= m; ++i) {
@@ -602,9 +605,9 @@ __global__ void sub_lsq_combine_kernel(int nS, int64_t stride, int m, const T* _
       y[i] = acc / R[i][i];
     }
   }
-  __syncthreads();
+  __syncwarp();
   const size_t off = (size_t)col * nS;
-  for (int t = threadIdx.x; t < nS; t += blockDim.x) {
+  for (int t = lane; t < nS; t += 32) {
     T acc = 0;
     for (int c = 0; c < m; ++c) acc += y[c] * Z[(size_t)c * stride + off + t];
     duS[off + t] = acc;
@@ -613,30 +616,22 @@ __global__ void sub_lsq_combine_kernel(int nS, int64_t stride, int m, const T* _
 
 template <typename T>
 void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream_t s) {
-  sub_normalize_kernel<T><<<E, 256, 0, s>>>(nS, rS, V0, beta);
+  if (E == 0) return;
+  sub_normalize_kernel<T><<<(E + kSubWarps - 1) / kSubWarps, 32 * kSubWarps, 0, s>>>(E, nS, rS, V0, beta);
   DG_LAUNCHED(1);
 }
 template <typename T>
 void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* Z, T* H, cudaStream_t s) {
-  const size_t smem = nS * sizeof(T);
-  if (smem > 48 * 1024) {
-    // the attribute is per device and may be raised by several serving threads at once
-    static std::mutex mu;
-    static std::map<int, size_t> attr_set;  // largest dynamic shared memory enabled per device
-    int dev = 0;
-    DG_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    if (smem > attr_set[dev]) {
-      DG_CUDA(cudaFuncSetAttribute(sub_arnoldi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_set[dev] = smem;
-    }
-  }
-  sub_arnoldi_kernel<T><<<E, 256, smem, s>>>(nS, (int64_t)E * nS, j, m, D, V, Z, H);
+  if (E == 0) return;
+  sub_arnoldi_kernel<T><<<(E + kSubWarps - 1) / kSubWarps, 32 * kSubWarps, 0, s>>>(E, nS, (int64_t)E * nS, j, m, D, V,
+                                                                                  Z, H);
   DG_LAUNCHED(1);
 }
 template <typename T>
 void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s) {
-  sub_lsq_combine_kernel<T><<<E, 256, 0, s>>>(nS, (int64_t)E * nS, m, beta, H, Z, duS);
+  if (E == 0) return;
+  sub_lsq_combine_kernel<T><<<(E + kSubWarps - 1) / kSubWarps, 32 * kSubWarps, 0, s>>>(E, nS, (int64_t)E * nS, m, beta,
+                                                                                      H, Z, duS);
   DG_LAUNCHED(1);
 }
 template void launch_sub_normalize<double>(int, int, const double*, double*, double*, cudaStream_t);

@@ -321,13 +321,21 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
       T* beta = W.gH.get() + (size_t)L.E * (m + 1) * m;
       launch_gather_tab<T>(sw.geom, lin_diag<T>(dom), sw.elem_of_col.get(), sw.xform_of_elem.get(),
                            dom->orient_map.get(), W.gD.get(), s);
-      PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, (double)blk * sz * (4.0 * m + 3.0), 6.0 * blk * m);
-      launch_sub_normalize<T>(L.E, ld, W.rS.get(), W.gV.get(), beta, s);
+      // the per-subdomain vector kernels count as Krylov work, the preconditioner GEMMs as GEMM
+      {
+        PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, 2.0 * blk * sz, 2.0 * blk);
+        launch_sub_normalize<T>(L.E, ld, W.rS.get(), W.gV.get(), beta, s);
+      }
       for (int j = 0; j < m; ++j) {
         gemm(W.gV.get() + j * blk, W.gZ.get() + j * blk);
+        // read V_j, D, Z_j and V_0..V_j, write V_{j+1}
+        PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, (double)blk * sz * (j + 5.0), 4.0 * blk * (j + 2.0));
         launch_sub_arnoldi<T>(L.E, ld, j, m, W.gD.get(), W.gV.get(), W.gZ.get(), W.gH.get(), s);
       }
-      launch_sub_lsq_combine<T>(L.E, ld, m, beta, W.gH.get(), W.gZ.get(), W.duS.get(), s);
+      {
+        PhaseScope ps(dom->prof, DG_PHASE_KRYLOV, s, (double)blk * sz * (m + 1.0), 2.0 * blk * m);
+        launch_sub_lsq_combine<T>(L.E, ld, m, beta, W.gH.get(), W.gZ.get(), W.duS.get(), s);
+      }
     }
     {
       PhaseScope ps(dom->prof, DG_PHASE_SCATTER, s, vec + 2.0 * L.ndof * sz, 0.0);
