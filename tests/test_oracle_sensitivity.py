@@ -1,0 +1,120 @@
+"""The oracle's pins are sensitive: each case below plants one plausible mistake in the oracle
+(monkeypatched, on the CPU, for the duration of the case) and checks that a pin of
+test_oracle_lgl / test_oracle_dg / test_oracle_solver then fails. A pin that still passed with
+the mistake in place would not be pinning that part of the oracle."""
+import numpy as np
+import pytest
+
+import test_oracle_dg as tdg
+import test_oracle_lgl as tlgl
+import test_oracle_solver as tsol
+from oracle import dg, lgl, mg, puncture, schwarz
+
+_FAIL = (AssertionError, np.linalg.LinAlgError)
+
+
+def _fails(pin, *args):
+    with pytest.raises(_FAIL):
+        pin(*args)
+
+
+def test_pins_pass_without_a_planted_mistake():
+    """The same pins, unpatched, pass (so the failures below come from the plants)."""
+    tlgl.test_diff_matrix_exact_on_polynomials(5)
+    tlgl.test_weights_sum_and_endpoints(5)
+    tlgl.test_closed_form_nodes()
+    tdg.test_polynomial_consistency()
+    tdg.test_strong_form_equals_sipg_bilinear_form((2, 2, 1), 3)
+    tsol.test_overlap_width_values()
+    tsol.test_smoothstep_and_weight_function_closed_forms()
+    tsol.test_face_neighbour_weight_is_product_away_from_edges()
+    tsol.test_prolongation_exact_on_coarse_polynomials((2, 2, 2))
+    tsol.test_restriction_is_transpose_of_prolongation()
+    tsol.test_bowen_york_curvature_traceless_and_divergence_free()
+
+
+def test_transposed_differentiation_matrix_is_caught(monkeypatch):
+    orig = lgl.diff_matrix
+    monkeypatch.setattr(lgl, "diff_matrix", lambda N: orig(N).T.copy())
+    _fails(tlgl.test_diff_matrix_exact_on_polynomials, 5)
+    _fails(tdg.test_polynomial_consistency)
+
+
+def test_uniform_quadrature_weights_are_caught(monkeypatch):
+    # (A u = M (-Laplace u) holds for any diagonal M, so the operator pins cannot see the weights;
+    # the quadrature pins do)
+    monkeypatch.setattr(lgl, "lgl_weights", lambda N: np.full(N, 2.0 / N))
+    _fails(tlgl.test_weights_sum_and_endpoints, 5)
+    _fails(tlgl.test_quadrature_exact_to_degree_2N_minus_3, 5)
+
+
+def test_equispaced_nodes_are_caught(monkeypatch):
+    monkeypatch.setattr(lgl, "lgl_nodes", lambda N: np.linspace(-1.0, 1.0, N))
+    _fails(tlgl.test_closed_form_nodes)
+
+
+def test_trace_from_the_opposite_face_is_caught(monkeypatch):
+    orig = dg._face
+    monkeypatch.setattr(dg, "_face", lambda a, d, side, N: orig(a, d, 1 - side, N))
+    _fails(tdg.test_strong_form_equals_sipg_bilinear_form, (2, 2, 1), 3)
+
+
+def test_lift_onto_the_opposite_face_is_caught(monkeypatch):
+    orig = dg._lift_to_volume
+    monkeypatch.setattr(dg, "_lift_to_volume", lambda fv, d, side, N: orig(fv, d, 1 - side, N))
+    _fails(tdg.test_strong_form_equals_sipg_bilinear_form, (2, 2, 1), 3)
+
+
+def test_overlap_width_one_layer_short_is_caught(monkeypatch):
+    monkeypatch.setattr(schwarz, "overlap_width",
+                        lambda N, ov: 1.0 + lgl.lgl_nodes(N)[ov - 1] if ov < N else 2.0)
+    _fails(tsol.test_overlap_width_values)
+
+
+def test_cubic_smoothstep_is_caught(monkeypatch):
+    def cubic(x):
+        x = np.asarray(x, dtype=np.float64)
+        t = 0.5 * (x + 1.0)
+        return np.where(np.abs(x) <= 1.0, 2.0 * (3 * t**2 - 2 * t**3) - 1.0, np.sign(x))
+
+    monkeypatch.setattr(schwarz, "phi", cubic)
+    _fails(tsol.test_smoothstep_and_weight_function_closed_forms)
+
+
+def test_weights_kept_by_the_own_subdomain_are_caught(monkeypatch):
+    def own_only(N, overlap, has_lo, has_hi):
+        sh = np.zeros((N, N, N, 7))
+        sh[..., 0] = 1.0
+        return sh
+
+    monkeypatch.setattr(schwarz, "weight_shares", own_only)
+    _fails(tsol.test_face_neighbour_weight_is_product_away_from_edges)
+
+
+def test_swapped_child_halves_in_prolongation_are_caught(monkeypatch):
+    orig = mg._interp
+
+    def swapped(N):
+        I = orig(N)
+        return {0: I[1], 1: I[0], None: I[None]}
+
+    monkeypatch.setattr(mg, "_interp", swapped)
+    _fails(tsol.test_prolongation_exact_on_coarse_polynomials, (2, 2, 2))
+
+
+def test_scaled_restriction_is_caught(monkeypatch):
+    orig = mg.restrict
+    monkeypatch.setattr(mg, "restrict", lambda fine, coarse, rf: 0.125 * orig(fine, coarse, rf))
+    _fails(tsol.test_restriction_is_transpose_of_prolongation)
+
+
+def test_bowen_york_normalisation_is_caught(monkeypatch):
+    """beta built from a curvature with prefactor 1 instead of 3/2 (beta scales with its square)."""
+    orig = puncture.alpha_beta
+
+    def wrong(x, y, z, punctures):
+        a, b = orig(x, y, z, punctures)
+        return a, b * (1.0 / 1.5) ** 2
+
+    monkeypatch.setattr(puncture, "alpha_beta", wrong)
+    _fails(tsol.test_bowen_york_curvature_traceless_and_divergence_free)
