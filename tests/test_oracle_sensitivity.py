@@ -1,14 +1,15 @@
 """The oracle's pins are sensitive: each case below plants one plausible mistake in the oracle
 (monkeypatched, on the CPU, for the duration of the case) and checks that a pin of
-test_oracle_lgl / test_oracle_dg / test_oracle_solver then fails. A pin that still passed with
+test_oracle_lgl / test_oracle_dg / test_oracle_solver / test_oracle_curved then fails. A pin that still passed with
 the mistake in place would not be pinning that part of the oracle."""
 import numpy as np
 import pytest
 
+import test_oracle_curved as tcur
 import test_oracle_dg as tdg
 import test_oracle_lgl as tlgl
 import test_oracle_solver as tsol
-from oracle import dg, lgl, mg, puncture, schwarz
+from oracle import curved, dg, lgl, mg, puncture, schwarz
 
 _FAIL = (AssertionError, np.linalg.LinAlgError)
 
@@ -118,3 +119,31 @@ def test_bowen_york_normalisation_is_caught(monkeypatch):
 
     monkeypatch.setattr(puncture, "alpha_beta", wrong)
     _fails(tsol.test_bowen_york_curvature_traceless_and_divergence_free)
+
+
+# ---------------------------------------------------------------- curved elements
+
+
+def test_curved_pins_pass_without_a_planted_mistake():
+    tcur.test_rigid_motion_leaves_operator_unchanged()
+    tcur.test_identity_map_reduces_to_affine_operator((2, 2, 1), 4, (False,) * 6)
+
+
+def test_transposed_inverse_jacobian_is_caught(monkeypatch):
+    """G^j_i = dxi^j/dx^i stored as dxi^i/dx^j: invisible on axis-aligned boxes, not under rotation."""
+    orig = curved.metric
+
+    def transposed(N, x, y, z):
+        J, G = orig(N, x, y, z)
+        return J, np.swapaxes(G, 1, 2).copy()
+
+    monkeypatch.setattr(curved, "metric", transposed)
+    tcur.test_identity_map_reduces_to_affine_operator((2, 2, 1), 4, (False,) * 6)
+    _fails(tcur.test_rigid_motion_leaves_operator_unchanged)
+
+
+def test_face_size_without_its_factor_two_is_caught(monkeypatch):
+    """h = 1 / |G^d| instead of 2 / |G^d| doubles the penalty against the affine operator."""
+    orig = curved.face_size
+    monkeypatch.setattr(curved, "face_size", lambda N, J, G, d, side: 0.5 * orig(N, J, G, d, side))
+    _fails(tcur.test_identity_map_reduces_to_affine_operator, (2, 2, 1), 4, (False,) * 6)
