@@ -33,3 +33,24 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_do_no_work():
     out = _run({"RANK": "1"})
     assert out.stdout.strip() == ""
+
+
+def test_gemm_traffic_comes_from_the_committed_summary_while_the_kernel_is_unchanged(monkeypatch, tmp_path):
+    """roofline.traffic is read from the ncu summary under profiles/ only while the GEMM sources
+    hash to the digest recorded there; a changed kernel (other digest) or a missing summary gives
+    null instead of stale counters."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    with open(bench.TRAFFIC_PROFILE) as f:
+        recorded = [l.split(": ", 1)[1].strip() for l in f if l.startswith("- gemm_sources_sha256: ")]
+    t = bench.gemm_traffic_per_launch()
+    if recorded and recorded[0] == bench.gemm_sources_digest():
+        assert t is not None and t > 0
+    else:
+        assert t is None
+    monkeypatch.setattr(bench, "gemm_sources_digest", lambda: "0" * 64)
+    assert bench.gemm_traffic_per_launch() is None
+    monkeypatch.undo()
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(tmp_path / "missing.md"))
+    assert bench.gemm_traffic_per_launch() is None
