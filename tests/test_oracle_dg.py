@@ -227,3 +227,52 @@ def test_mixed_boundaries_manufactured_p_convergence():
         errs.append(math.sqrt(np.mean((u - ue.ravel()) ** 2)))
     assert errs[0] / errs[1] > 20 and errs[1] / errs[2] > 0.9 * errs[0] / errs[1]
     assert errs[2] < 1e-5
+
+
+def _sipg_1d(n, N, h, C):
+    """Textbook 1-D symmetric interior-penalty matrix on n elements of width h with LGL quadrature
+    and homogeneous Dirichlet ends: sum_K int w' u' - sum_F ({n w'}[u] + {n u'}[w] - sigma [w][u]),
+    sigma = C N^2 / h inside, and at an end (mirror ghost) the consistency terms with the interior
+    derivative and the penalty doubled. Written from the 1-D weak form, not from the 3-D code."""
+    w = lgl.lgl_weights(N)
+    D = (2.0 / h) * lgl.diff_matrix(N)
+    A = np.zeros((n * N, n * N))
+    sig = C * N**2 / h
+    blk = lambda e: slice(e * N, (e + 1) * N)
+    for e in range(n):
+        A[blk(e), blk(e)] += D.T @ np.diag(0.5 * h * w) @ D
+    # interior faces: element e (node N-1) | element e+1 (node 0), normal +x
+    for e in range(n - 1):
+        rows = np.zeros((2, n * N))  # jump [u] = u_e(N-1) - u_{e+1}(0), average of u'
+        rows[0, e * N + N - 1] = 1.0
+        rows[0, (e + 1) * N] = -1.0
+        rows[1, blk(e)] = 0.5 * D[N - 1]
+        rows[1, blk(e + 1)] = 0.5 * D[0]
+        jump, avg = rows[0], rows[1]
+        A += -np.outer(avg, jump) - np.outer(jump, avg) + sig * np.outer(jump, jump)
+    # Dirichlet ends: outward normal -1 at node 0 of element 0, +1 at node N-1 of element n-1
+    for node, nrm, dl in ((0, -1.0, D[0]), ((n - 1) * N + N - 1, 1.0, D[N - 1])):
+        e = 0 if nrm < 0 else n - 1
+        val = np.zeros(n * N)
+        val[node] = 1.0
+        der = np.zeros(n * N)
+        der[blk(e)] = nrm * dl
+        A += -np.outer(der, val) - np.outer(val, der) + 2.0 * sig * np.outer(val, val)
+    return A
+
+
+@pytest.mark.parametrize("n,N", [(1, 3), (3, 4), (4, 6)])
+def test_one_dimensional_reduction(n, N):
+    """One element across y and z with homogeneous Neumann faces there and a field constant in y and
+    z: the operator is the textbook 1-D SIPG matrix in x times the y and z mass weights."""
+    C = 1.5
+    grid = _box((n, 1, 1), N, C, lower=(-1.0, 0.0, -0.5), upper=(2.0, 0.8, 1.5),
+                neumann=(False, False, True, True, True, True))
+    hx, hy, hz = 3.0 / n, 0.8, 2.0
+    ux = workloads.uniform_vector(7, n * N).reshape(n, N)
+    u = np.broadcast_to(ux[:, None, None, :], (n, N, N, N)).copy()  # [e, k, j, i]
+    Au = dg.apply(grid.graph(), u)
+    A1 = _sipg_1d(n, N, hx, C) @ ux.ravel()
+    w = lgl.lgl_weights(N)
+    ref = A1.reshape(n, 1, 1, N) * (0.5 * hz * w)[None, :, None, None] * (0.5 * hy * w)[None, None, :, None]
+    assert np.abs(Au - ref).max() <= 1e-12 * np.abs(ref).max()
