@@ -147,3 +147,97 @@ def test_face_size_without_its_factor_two_is_caught(monkeypatch):
     orig = curved.face_size
     monkeypatch.setattr(curved, "face_size", lambda N, J, G, d, side: 0.5 * orig(N, J, G, d, side))
     _fails(tcur.test_identity_map_reduces_to_affine_operator, (2, 2, 1), 4, (False,) * 6)
+
+
+# ---------------------------------------------------------------- V-cycle step order, subdomain GMRES
+
+
+def _vcycle_planted(mistake):
+    """The V-cycle of Sec. III.C.3 with one planted mistake."""
+
+    def vcycle(levels, smoothers, b0, presmooth=3, postsmooth=3, operators=None):
+        L = len(levels)
+        if operators is None:
+            graphs = [g.graph() for g in levels]
+            operators = [lambda u, gr=gr: dg.apply(gr, u) for gr in graphs]
+        b, u = [None] * L, [None] * L
+        b[0] = b0
+        for l in range(L - 1):
+            u[l] = smoothers[l](b[l], np.zeros_like(b[l]), presmooth)
+            r = b[l] - operators[l](u[l])
+            b[l + 1] = mg.restrict(levels[l], levels[l + 1], r)
+        start = b[L - 1].copy() if mistake == "coarse_guess_b" else np.zeros_like(b[L - 1])
+        u[L - 1] = smoothers[L - 1](b[L - 1], start, presmooth)
+        if mistake != "no_coarse_postsmooth":
+            u[L - 1] = smoothers[L - 1](b[L - 1], u[L - 1], postsmooth)
+        for l in range(L - 2, -1, -1):
+            if mistake == "smooth_before_correction":
+                u[l] = smoothers[l](b[l], u[l], postsmooth)
+                u[l] = u[l] + mg.prolongate(levels[l], levels[l + 1], u[l + 1])
+            else:
+                u[l] = u[l] + mg.prolongate(levels[l], levels[l + 1], u[l + 1])
+                u[l] = smoothers[l](b[l], u[l], postsmooth)
+        return u[0]
+
+    return vcycle
+
+
+def test_vcycle_pin_passes_with_the_unplanted_copy(monkeypatch):
+    monkeypatch.setattr(mg, "vcycle", _vcycle_planted(None))
+    tsol.test_vcycle_equals_multigrid_error_propagation_operator((8, 2, 2), 3, 3, 3)
+
+
+# (a wrong coarse initial guess decays as S_c^(pre + post); with 3 + 3 steps on a two-element coarse
+# level it falls below rounding, so that plant runs with 2 + 1 steps)
+@pytest.mark.parametrize("mistake,case", [("no_coarse_postsmooth", ((4, 2, 2), 2, 3, 3)),
+                                          ("coarse_guess_b", ((8, 2, 2), 3, 2, 1)),
+                                          ("smooth_before_correction", ((4, 2, 2), 2, 3, 3))])
+def test_vcycle_step_order_mistakes_are_caught(monkeypatch, mistake, case):
+    monkeypatch.setattr(mg, "vcycle", _vcycle_planted(mistake))
+    _fails(tsol.test_vcycle_equals_multigrid_error_propagation_operator, *case)
+
+
+def test_left_preconditioned_subdomain_gmres_is_caught(monkeypatch):
+    """GMRES minimising ||M (r - A z)|| (left preconditioning) instead of ||r - A z||."""
+
+    def left(op, prec, r, iterations):
+        Mop = lambda z: prec(op(z))
+        Mr = prec(r)
+        beta = np.linalg.norm(Mr)
+        V = [Mr / beta]
+        H = np.zeros((iterations + 1, iterations))
+        for j in range(iterations):
+            w = Mop(V[j])
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j])
+        e1 = np.zeros(iterations + 1)
+        e1[0] = beta
+        y = np.linalg.lstsq(H, e1, rcond=None)[0]
+        return np.stack(V[:iterations], axis=1) @ y
+
+    monkeypatch.setattr(schwarz, "_gmres_right", left)
+    _fails(tsol.test_truncated_subdomain_gmres_is_the_krylov_least_squares_minimiser)
+
+
+def test_galerkin_instead_of_least_squares_subdomain_step_is_caught(monkeypatch):
+    """The square Hessenberg system (FOM, a Galerkin condition) solved in place of the least-squares
+    problem of GMRES."""
+    orig_lstsq = np.linalg.lstsq
+
+    def fom(op, prec, r, iterations):
+        def square(H, e1, rcond=None):
+            k = H.shape[1]
+            return (np.linalg.solve(H[:k, :k], e1[:k]),)
+
+        np.linalg.lstsq = square
+        try:
+            return schwarz.__dict__["_gmres_right_orig"](op, prec, r, iterations)
+        finally:
+            np.linalg.lstsq = orig_lstsq
+
+    monkeypatch.setitem(schwarz.__dict__, "_gmres_right_orig", schwarz._gmres_right)
+    monkeypatch.setattr(schwarz, "_gmres_right", fom)
+    _fails(tsol.test_truncated_subdomain_gmres_is_the_krylov_least_squares_minimiser)

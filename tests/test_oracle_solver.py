@@ -420,3 +420,86 @@ def test_bowen_york_adm_momenta():
     J_ref = sum(np.cross(q.position, q.momentum) for q in p)
     assert np.allclose(J, J_ref, atol=1e-12)
     assert abs(J_ref[2]) > 0.1  # the binary orbits: a nonzero reference
+
+
+# ---------------------------------------------------------------- V-cycle and subdomain GMRES, in closed form
+
+def _schwarz_matrix(level: schwarz.SchwarzLevel) -> np.ndarray:
+    """M^-1 = sum_S R_S^T W_S A_S^-1 R_S (Eqs. schwarz_subd_problem, schwarz_weighting) as a dense
+    matrix, from each subdomain's point list, weights and dense A_S."""
+    n = level.grid.n_elements * level.N**3
+    Minv = np.zeros((n, n))
+    for e, sd in enumerate(level.subdomains):
+        g = sd["glob"]
+        Minv[np.ix_(g, g)] += sd["weight"][:, None] * np.linalg.inv(level.subdomain_matrix(e))
+    return Minv
+
+
+def _prolongation_matrix(fine, coarse) -> np.ndarray:
+    N = fine.N
+    nc = coarse.n_elements * N**3
+    eye = np.eye(nc).reshape(nc, coarse.n_elements, N, N, N)
+    return mg.prolongate(fine, coarse, eye).reshape(nc, -1).T.copy()
+
+
+@pytest.mark.parametrize("n,levels,pre,post", [((4, 2, 2), 2, 3, 3), ((8, 2, 2), 3, 3, 3), ((8, 2, 2), 3, 2, 1)])
+def test_vcycle_equals_multigrid_error_propagation_operator(n, levels, pre, post):
+    """Sec. III.C.3 as error propagation (Hackbusch, Multi-Grid Methods, Sec. 2.4/7.1): with the
+    Schwarz iteration matrix S_l = I - M_l^-1 A_l, a V-cycle from zero initial guesses is the linear
+    map B_l with I - B_l A_l = S_l^post (I - P_l B_{l+1} R_l A_l) S_l^pre, and on the coarsest level
+    (presmoothing then postsmoothing from zero) I - B_c A_c = S_c^(pre + post). Evaluated with dense
+    matrices, independently of the oracle's sequential step list. The coarsest level has two or more
+    elements, so that its Schwarz step is not an exact solve (a dropped coarse postsmooth shows).
+    Also pins the multi-step smoother: k steps from u give S^k u + (I - S^k) A^-1 b."""
+    N = 2
+    grid = _box(n, N)
+    pr = solve.Problem(grid, mg_levels=levels, overlap=1, presmooth=pre, postsmooth=post)
+    L = len(pr.levels)
+    assert L == levels and pr.levels[-1].n_elements >= 2
+    A = [dg.assemble(g) for g in pr.graphs]
+    Ainv = [np.linalg.inv(a) for a in A]
+    S = [np.eye(a.shape[0]) - _schwarz_matrix(s) @ a for s, a in zip(pr.schwarz, A)]
+    P = [_prolongation_matrix(pr.levels[l], pr.levels[l + 1]) for l in range(L - 1)]
+    mp = np.linalg.matrix_power
+    B = (np.eye(A[-1].shape[0]) - mp(S[-1], pre + post)) @ Ainv[-1]
+    for l in range(L - 2, -1, -1):
+        I = np.eye(A[l].shape[0])
+        B = (I - mp(S[l], post) @ (I - P[l] @ B @ P[l].T @ A[l]) @ mp(S[l], pre)) @ Ainv[l]
+    for seed in (41, 42):
+        r = workloads.uniform_vector(seed, A[0].shape[0]).reshape(-1, N, N, N)
+        z = pr.vcycle(r).ravel()
+        want = B @ r.ravel()
+        assert np.linalg.norm(z - want) <= 1e-12 * np.linalg.norm(want)
+    # the smoother itself: k Schwarz steps of the stationary iteration
+    b = workloads.uniform_vector(43, A[0].shape[0]).reshape(-1, N, N, N)
+    u0 = workloads.uniform_vector(44, A[0].shape[0]).reshape(-1, N, N, N)
+    for k in (1, 3):
+        got = pr.schwarz[0].smooth(b, u0, k).ravel()
+        Sk = mp(S[0], k)
+        want = Sk @ u0.ravel() + (np.eye(A[0].shape[0]) - Sk) @ (Ainv[0] @ b.ravel())
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_truncated_subdomain_gmres_is_the_krylov_least_squares_minimiser():
+    """Sec. III.E's subdomain solver: m right-preconditioned GMRES iterations from zero (Saad,
+    Iterative Methods, Sec. 9.3.2) return z = M y with y the minimiser of ||r - A M y|| over the
+    Krylov space K_m(A M, r) = span{r, (A M) r, ..., (A M)^(m-1) r}. Built here from the monomial
+    basis and a dense least-squares solve on a linearized subdomain operator A_S + D_S with the
+    Poisson inverse as M, for m = 1, 2, 3 (none converged: the residual stays well above zero)."""
+    grid = _box((3, 2, 2), 3)
+    lv = schwarz.SchwarzLevel(grid, 2)
+    e = 4  # an interior-ish element with four face neighbours
+    A_S = lv.subdomain_matrix(e)
+    nS = A_S.shape[0]
+    D = 40.0 * workloads.uniform_vector(45, nS, 0.0, 1.0)  # strong diagonal: M is far from exact
+    op = lambda z: A_S @ z + D * z
+    Minv = np.linalg.inv(A_S)
+    r = workloads.uniform_vector(46, nS)
+    AM = (A_S + np.diag(D)) @ Minv
+    for m in (1, 2, 3):
+        W = np.stack([np.linalg.matrix_power(AM, i) @ r for i in range(m)], axis=1)
+        c = np.linalg.lstsq(AM @ W, r, rcond=None)[0]
+        want = Minv @ (W @ c)
+        got = schwarz._gmres_right(op, lambda v: Minv @ v, r, m)
+        assert np.linalg.norm(r - op(want)) >= 1e-3 * np.linalg.norm(r)
+        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want), m
