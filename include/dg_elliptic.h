@@ -213,7 +213,8 @@ dg_status dg_dot(struct dg_domain* dom, int32_t m, const double* V, int64_t ld, 
  * the process exits. m above DG_NOALLOC_MAX_VECTORS is rejected with DG_ERR_INVALID_ARG; the
  * message is available from dg_last_error(NULL). The call allocates nothing and calls no
  * allocating routine. The first call on a device (with that device current) looks up the array's
- * device address, so make that first call before any stream capture. All calls share the one
+ * device address, so make that first call before any stream capture; the address is kept until the
+ * process exits, so the device must not be reset (cudaDeviceReset) after it. All calls share the one
  * array: calls that overlap on the GPU (concurrent streams) race and must be serialised by the
  * caller. V, w, out are device pointers; stream as elsewhere (NULL: legacy default stream). */
 enum { DG_NOALLOC_MAX_VECTORS = 64 };
@@ -242,6 +243,30 @@ dg_status dg_puncture_fields(const struct dg_domain* dom, double* alpha, double*
  * FP64 residual recomputed at exit meets the tolerance. */
 dg_status elliptic_solve(struct dg_domain* dom, const double* b, double* u, double tol, const dg_solve_opts* opts,
                          dg_solve_report* report);
+/* elliptic_solve runs a linear FGMRES solve with the multigrid preconditioner (opts->precondition 2,
+ * per-phase profiling off) as ONE CUDA graph from the second solve on a domain with the same
+ * tolerance and kernels: the Hessenberg column, its Givens rotations and the stopping test of
+ * Sec. III.B are computed on the device, and the Arnoldi loop is a conditional WHILE node, so an
+ * iteration needs no host round trip (the first such solve runs host-driven and tunes the launch
+ * shapes). A captured solve holds at most 40 Arnoldi columns; a solve that needs more continues
+ * host-driven from the graph's iterate (a restart). Setting DG_SOLVE_GRAPH=0 in the environment
+ * keeps every solve host-driven. */
+
+/* Many independent linear solves (POISSON problems on distinct domains) as one CUDA graph: each
+ * solve is one branch of the graph (b and u copied in, FGMRES with the multigrid preconditioner as
+ * above, u copied out), so one launch runs them all concurrently on the device. create captures
+ * the graph (it first runs every kernel shape of each domain once, untimed, on the domain's
+ * stream, and synchronises); run launches it on `stream` and waits for it, filling count
+ * reports. b[i] and u[i] are device pointers of domain i's n_dof values, fixed for the life of the
+ * batch (u[i] holds the initial guess before each run and the solution after it); the domains
+ * must outlive the batch and must not be used by other calls while a run is in flight. opts as for
+ * elliptic_solve with krylov 0 and precondition 2 (NULL: defaults). Errors of create and run are
+ * described by dg_last_error(NULL). Not in the paper, whose solves run one at a time. */
+typedef struct dg_batch dg_batch;
+dg_status elliptic_batch_create(struct dg_domain* const* domains, const double* const* b, double* const* u,
+                                int32_t count, double tol, const dg_solve_opts* opts, struct dg_batch** out);
+dg_status elliptic_batch_run(struct dg_batch* batch, void* stream, dg_solve_report* reports);
+void elliptic_batch_destroy(struct dg_batch* batch);
 
 /* ---------------------------------------------------------------------------------------------
  * Per-phase kernel timing: CUDA events around every launch of a phase on the stream it runs on.

@@ -23,15 +23,22 @@ void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relax
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 void puncture_residual_api(dg_domain* dom, const double* u, const double* b, double* r, cudaStream_t s);
-const char* noalloc_last_error();
 void puncture_linearize_api(dg_domain* dom, const double* u, cudaStream_t s);
 void subdomain_solver_api(dg_domain* dom, int solver, int iterations, cudaStream_t s);
+
+namespace {
+// The last error of a call that has no domain handle to hold it (a failed dg_domain_create, any
+// dg_dot_noalloc call), per thread: every such call overwrites it, so dg_last_error(NULL) always
+// describes the latest of them.
+thread_local std::string g_null_handle_error;
+}  // namespace
+
+void set_null_handle_error(const std::string& msg) { g_null_handle_error = msg; }
+const char* null_handle_error() { return g_null_handle_error.c_str(); }
 
 }  // namespace dg
 
 namespace {
-
-thread_local std::string g_create_error;
 
 template <typename F>
 dg_status guarded(dg_domain* dom, F&& f) {
@@ -63,12 +70,17 @@ void check_level(const dg_domain* dom, int level) {
 extern "C" {
 
 dg_status dg_domain_create(const dg_domain_desc* desc, void* cuda_stream, dg_domain** out) {
-  if (!desc || !out) return DG_ERR_INVALID_ARG;
+  if (!desc || !out) {
+    dg::set_null_handle_error("dg_domain_create: null descriptor or output pointer");
+    return DG_ERR_INVALID_ARG;
+  }
   *out = nullptr;
+  dg::set_null_handle_error("");
   dg_domain* dom = nullptr;
   try {
     dom = new dg_domain();
   } catch (...) {
+    dg::set_null_handle_error("dg_domain_create: host allocation failed");
     return DG_ERR_OOM;
   }
   dom->desc = *desc;
@@ -79,7 +91,7 @@ dg_status dg_domain_create(const dg_domain_desc* desc, void* cuda_stream, dg_dom
     dom->bytes = dg::domain_device_bytes(dom);
   });
   if (st != DG_OK) {
-    g_create_error = dom->err;
+    dg::set_null_handle_error(dom->err);
     dg_domain_destroy(dom);
     return st;
   }
@@ -99,10 +111,7 @@ void dg_domain_destroy(dg_domain* dom) {
 }
 
 const char* dg_last_error(const dg_domain* dom) {
-  if (!dom) {
-    const char* na = dg::noalloc_last_error();
-    return na[0] ? na : g_create_error.c_str();
-  }
+  if (!dom) return dg::null_handle_error();
   return dom->err.c_str();
 }
 
@@ -321,6 +330,51 @@ dg_status elliptic_solve(dg_domain* dom, const double* b, double* u, double tol,
   if (result != DG_OK) dom->err = "solve ended with status " + std::to_string((int)result);
   return result;
 }
+
+dg_status elliptic_batch_create(dg_domain* const* domains, const double* const* b, double* const* u, int32_t count,
+                                double tol, const dg_solve_opts* opts, dg_batch** out) {
+  if (!domains || !b || !u || !out || count < 1) {
+    dg::set_null_handle_error("elliptic_batch_create: null argument or count < 1");
+    return DG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  dg_solve_opts o{};
+  o.max_iterations = 200;
+  o.precondition = 2;
+  o.linear_tol = 1e-4;
+  o.max_newton_steps = 20;
+  o.subdomain_iterations = 3;
+  if (opts) o = *opts;
+  try {
+    dg::AllocStreamScope scope(domains[0] ? domains[0]->stream : nullptr);
+    *out = dg::batch_create(domains, b, u, count, tol, o);
+    dg::set_null_handle_error("");
+    return DG_OK;
+  } catch (const dg::Error& e) {
+    dg::set_null_handle_error(e.message);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    dg::set_null_handle_error("host allocation failed");
+    return DG_ERR_OOM;
+  } catch (const std::exception& e) {
+    dg::set_null_handle_error(e.what());
+    return DG_ERR_INVALID_ARG;
+  }
+}
+
+dg_status elliptic_batch_run(dg_batch* batch, void* stream, dg_solve_report* reports) {
+  if (!batch) return DG_ERR_INVALID_ARG;
+  try {
+    dg::batch_run(batch, (cudaStream_t)stream, reports);
+    dg::set_null_handle_error("");
+    return DG_OK;
+  } catch (const dg::Error& e) {
+    dg::set_null_handle_error(e.message);
+    return e.status;
+  }
+}
+
+void elliptic_batch_destroy(dg_batch* batch) { dg::batch_destroy(batch); }
 
 int64_t dg_kernel_launches(void) { return dg::launches_total(); }
 

@@ -8,9 +8,11 @@
 // its per-block partial sums in a fixed file-scope device array instead of a domain workspace.
 //
 // The array is ordinary module memory: every GPU that loads this library holds its
-// DG_NOALLOC_PARTIALS doubles until the process exits. In host code its name is only a host-side
-// stand-in, so its device address is looked up with cudaGetSymbolAddress once per device, with
-// that device current, on that device's first call.
+// 304 x DG_NOALLOC_MAX_VECTORS doubles until the process exits. In host code its name is only a
+// host-side stand-in, so its device address is looked up with cudaGetSymbolAddress once per device,
+// with that device current, on that device's first call, and kept for the life of the process: a
+// cudaDeviceReset after that first call would leave the kept address pointing into a destroyed
+// context, so callers of this entry point must not reset the device.
 #include <mutex>
 
 #include "internal.h"
@@ -25,18 +27,13 @@ static __device__ __align__(256) double g_noalloc_partials[kPartials];
 
 std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {};
-thread_local std::string g_noalloc_error;
 
 dg_status noalloc_fail(dg_status st, const std::string& msg) {
-  g_noalloc_error = msg;
+  dg::set_null_handle_error(msg);
   return st;
 }
 
 }  // namespace
-
-namespace dg {
-const char* noalloc_last_error() { return g_noalloc_error.c_str(); }
-}  // namespace dg
 
 extern "C" dg_status dg_dot_noalloc(int64_t n, int32_t m, const double* V, int64_t ld, const double* w, double* out,
                                     void* stream) {
@@ -76,6 +73,6 @@ extern "C" dg_status dg_dot_noalloc(int64_t n, int32_t m, const double* V, int64
   } catch (const dg::Error& err) {
     return noalloc_fail(err.status, err.message);
   }
-  g_noalloc_error.clear();
+  dg::set_null_handle_error("");
   return DG_OK;
 }
