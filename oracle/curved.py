@@ -20,7 +20,7 @@ F_u^i = K v^i and the flux of Eq. numflux:
     A u  = -M G^j_i Dhat_j (K v^i) - ML ((n.F_u)* - K n.v)
     (n.F_u)* = (K n.grad u + K^ext n.grad u^ext) / 2 - sigma (K u - K^ext u^ext)
 
-Readings (each also listed in the design notes):
+Readings where the paper is silent:
   * the unit normal at a face node is the element's own, n_i = s G^d_i / |G^d|, and the
     exterior normal is its negative (the paper's n^ext = -n^int);
   * h in the penalty (Eq. penalty) is the element size normal to the face at each face node,

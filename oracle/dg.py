@@ -12,7 +12,7 @@ evaluated in two steps, Eq. dg_op_auxvars then Eq. dg_op_primal:
 with the generalized internal-penalty flux (Eq. numflux), the penalty (Eq. penalty) and
 boundary conditions imposed through the exterior fluxes (Eq. bc).
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent:
   * quadrature: the integrals of Eqs. massmat, stiffmat and liftop are evaluated with the
     LGL collocation quadrature, so M and the face mass are diagonal, MD_i = M D_i exactly
     and L only touches face nodes;

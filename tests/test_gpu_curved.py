@@ -121,6 +121,8 @@ def test_curved_vcycle_matches_oracle(n, N, levels):
 
 
 def test_curved_solve_matches_direct_solution():
+    """At a 1e-10 residual the FP64 solution on this warped mesh is 5.2e-10 from the direct solution
+    (measured): the solve runs to 1e-11, where the 1e-10 solution parity holds."""
     n, N = (2, 2, 2), 5
     g = mapped(n, N, sheared_warp, neumann=(2,))
     pr = solve.Problem(g)
@@ -128,16 +130,16 @@ def test_curved_solve_matches_direct_solution():
     f = workloads.gaussian_source(2)(x, y, z)
     b_ref = dg.rhs(pr.graphs[0], f)
     direct = np.linalg.solve(dg.assemble(pr.graphs[0]), b_ref.ravel())
-    _, info = pr.solve_linear(b_ref, tol=1e-10)
+    _, info11 = pr.solve_linear(b_ref, tol=1e-11)
     for precision in ("fp64", "mixed"):
         d = domain(g, (2,), precision=precision)
         b = d.rhs(dev(f))
         u = torch.zeros_like(b)
-        rep = d.solve(b, u, tol=1e-10)
-        assert rep.relative_residual <= 1e-10
-        assert rel(u.cpu().numpy(), direct) < 1e-9, precision
+        rep = d.solve(b, u, tol=1e-11)
+        assert rep.relative_residual <= 1e-11
+        assert rel(u.cpu().numpy(), direct) < 1e-10, precision
         if precision == "fp64":
-            assert abs(rep.iterations - info["iterations"]) <= 1
+            assert abs(rep.iterations - info11["iterations"]) <= 1
 
 
 def test_manufactured_solution_on_a_warped_mesh():
@@ -172,7 +174,7 @@ def test_curved_arguments_are_checked():
 
 def test_curved_8x8x8_N8_workload():
     """The Gaussian workload's size on a warped mesh (262,144 DOF, 512 subdomain inverses of
-    1280^2 per precision): mixed and FP64 reach 1e-10 and agree to 1e-9; the oracle's operator
+    1280^2 per precision): mixed and FP64 reach 1e-10 and agree to 1e-10; the oracle's operator
     confirms the residual."""
     n, N = (8, 8, 8), 8
     g = mapped(n, N, warp)
@@ -187,7 +189,7 @@ def test_curved_8x8x8_N8_workload():
         assert rep.relative_residual <= 1e-10
         sols[precision] = (u.cpu().numpy(), rep.iterations, b.cpu().numpy())
         d.close()
-    assert rel(sols["mixed"][0], sols["fp64"][0]) < 1e-9
+    assert rel(sols["mixed"][0], sols["fp64"][0]) < 1e-10
     gr = g.graph()
     uh = sols["fp64"][0].reshape(-1, N, N, N)
     res = dg.rhs(gr, f) - dg.apply(gr, uh)
@@ -245,7 +247,7 @@ def test_variable_coefficient_solves():
             u = torch.zeros_like(b)
             rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(krylov=krylov))
             assert rep.relative_residual <= 1e-10
-            assert rel(u.cpu().numpy(), direct) < 1e-9, (precision, krylov)
+            assert rel(u.cpu().numpy(), direct) < 1e-10, (precision, krylov)
 
 
 def test_variable_coefficient_manufactured_solution():
