@@ -751,24 +751,27 @@ __device__ __forceinline__ void coarse_gemm_unit(const float* __restrict__ invm,
 
 template <int N, int EPB>
 __global__ void __launch_bounds__(EPB* N* N) coarse_smooth_kernel(const CoarseArgs a) {
-  const unsigned G = gridDim.x;
+  // a wait of an earlier launch gave up and the host has not read the flag yet: skip the work
+  // (its inputs are incomplete) instead of waiting again
+  if (*reinterpret_cast<volatile int*>(a.err) != 0) return;
+  const unsigned G = gridDim.x + (unsigned)a.stall;
   const int E = a.ap.E;
   const int nblk = (E + EPB - 1) / EPB;
   for (int it = 0; it < a.iterations; ++it) {
     if (it == 0 && a.u_zero) {
-      for (int col = blockIdx.x; col < E; col += G)
+      for (int col = blockIdx.x; col < E; col += gridDim.x)
         gather_column<float, false>(a.sg, a.ap.b, a.elem_of_col, a.ap.orient, a.map, a.ap.rS, col);
     } else {
-      for (int blk = blockIdx.x; blk < nblk; blk += G) {
+      for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
         __syncthreads();  // the previous group is done with the shared blocks
         apply_line_block<N, float, EPB, false, true>(a.ap, blk);
       }
     }
     if (!grid_barrier(a.bar, G, a.err)) return;
-    for (int un = blockIdx.x; un < a.n_units; un += G)
+    for (int un = blockIdx.x; un < a.n_units; un += gridDim.x)
       coarse_gemm_unit(a.invm, a.sg.ld, a.ap.rS, a.duS, a.units[un], a.alpha);
     if (!grid_barrier(a.bar, G, a.err)) return;
-    for (int e = blockIdx.x; e < E; e += G)
+    for (int e = blockIdx.x; e < E; e += gridDim.x)
       scatter_element<float, float, false, true>(a.sg, a.duS, a.ap.col_of_elem, a.ap.orient, a.ap.inv, a.shares,
                                                  const_cast<float*>(a.ap.u), e);
     if (it + 1 < a.iterations && !grid_barrier(a.bar, G, a.err)) return;

@@ -1,0 +1,89 @@
+"""Failure statuses of elliptic_solve, each made on the host or by a bounded device wait that is
+made to run out, and the domain's recovery afterwards (the next solve on the same domain reaches
+the dense direct solution).
+
+* DG_ERR_NOT_CONVERGED: the Krylov iteration cap is reached before the tolerance.
+* DG_ERR_BREAKDOWN: a NaN placed in b on the host makes the initial residual non-finite.
+* DG_ERR_TIMEOUT: with DG_TEST_BARRIER_STALL=1 the fused coarse-level smoother's grid barriers wait
+  for one CTA more than the launch has, so the generation flag they poll is never advanced; every
+  wait gives up after its poll limit (well under a second), raises the domain's error flag and
+  returns. Nothing faults or hangs: the waits are bounded and later launches skip their work until
+  the host has read the flag.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import box, rel
+from oracle import dg, solve
+
+pytestmark = pytest.mark.gpu
+
+dgg = pytest.importorskip("paper_2111_06767_gb300")
+nat = dgg._native
+STATUS = {v: k for k, v in nat.STATUS_NAMES.items()}
+
+
+def _sine_problem(n, N):
+    grid = box(n, N)
+    x, y, z = grid.coordinates()
+    f = workloads.sine_source_3d(x, y, z)
+    pr = solve.Problem(grid)
+    ud = np.linalg.solve(dg.assemble(pr.graphs[0]), dg.rhs(pr.graphs[0], f).ravel())
+    return f, ud
+
+
+def _recovers(d, f, ud):
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    u = torch.zeros_like(b)
+    rep = d.solve(b, u, tol=1e-10)
+    assert rep.status == STATUS["DG_OK"] and rep.relative_residual <= 1e-10
+    assert rel(u.cpu().numpy(), ud) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_not_converged_when_the_iteration_cap_is_reached(precision):
+    n, N = (2, 2, 2), 6
+    f, ud = _sine_problem(n, N)
+    d = dgg.Domain(n=n, N=N, precision=precision)
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    u = torch.zeros_like(b)
+    rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(max_iterations=2), check_status=False)
+    assert rep.status == STATUS["DG_ERR_NOT_CONVERGED"]
+    assert rep.iterations == 2 and rep.relative_residual > 1e-10
+    with pytest.raises(nat.NativeError, match="DG_ERR_NOT_CONVERGED"):
+        d.solve(b, torch.zeros_like(b), tol=1e-10, opts=dgg.solve_opts(max_iterations=2))
+    _recovers(d, f, ud)
+
+
+@pytest.mark.parametrize("krylov", ["fgmres", "fcg"])
+def test_breakdown_on_a_non_finite_right_hand_side(krylov):
+    n, N = (2, 2, 2), 6
+    f, ud = _sine_problem(n, N)
+    d = dgg.Domain(n=n, N=N, precision="mixed")
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    bad = b.clone()
+    bad[17] = float("nan")  # planted on the host side of the call, before the solve
+    u = torch.zeros_like(b)
+    rep = d.solve(bad, u, tol=1e-10, opts=dgg.solve_opts(krylov=krylov), check_status=False)
+    assert rep.status == STATUS["DG_ERR_BREAKDOWN"]
+    _recovers(d, f, ud)
+
+
+def test_timeout_when_a_device_wait_runs_out(monkeypatch):
+    n, N = (4, 4, 4), 4  # 64 and 8 elements: both levels use the fused coarse smoother
+    f, ud = _sine_problem(n, N)
+    monkeypatch.setenv("DG_COARSE_FUSED", "1")
+    d = dgg.Domain(n=n, N=N, precision="mixed", mg_levels=2, gemm="simt")
+    b = d.rhs(torch.from_numpy(f.ravel()).cuda())
+    monkeypatch.setenv("DG_TEST_BARRIER_STALL", "1")
+    u = torch.zeros_like(b)
+    rep = d.solve(b, u, tol=1e-10, opts=dgg.solve_opts(max_iterations=3), check_status=False)
+    assert rep.status == STATUS["DG_ERR_TIMEOUT"]
+    assert rep.seconds < 30.0
+    monkeypatch.delenv("DG_TEST_BARRIER_STALL")
+    # the flag was read and cleared by the failed solve: the same domain (its V-cycle graph is
+    # captured again without the stall) solves to the direct solution
+    _recovers(d, f, ud)
+    _recovers(d, f, ud)
