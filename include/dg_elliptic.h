@@ -243,6 +243,16 @@ dg_status dg_puncture_fields(const struct dg_domain* dom, double* alpha, double*
  * FP64 residual recomputed at exit meets the tolerance. */
 dg_status elliptic_solve(struct dg_domain* dom, const double* b, double* u, double tol, const dg_solve_opts* opts,
                          dg_solve_report* report);
+/* The same solve with HOST buffers, for callers that keep their data in host memory: f_host holds
+ * the nodal source f (n_dof values; POISSON: b = M f, Eq. dg_op_primal; PUNCTURE: ignored, may be
+ * NULL), u_host the initial guess on entry and the solution on exit. The call copies f and u to
+ * library-owned device buffers of the domain (allocated on the first call), solves as
+ * elliptic_solve does and copies u back, all on the domain's stream; it returns when u_host holds
+ * the result. Page-locked host buffers (cudaHostAlloc, cudaHostRegister) make the copies
+ * asynchronous DMA transfers; pageable ones are staged by the driver. */
+dg_status elliptic_solve_host(struct dg_domain* dom, const double* f_host, double* u_host, double tol,
+                              const dg_solve_opts* opts, dg_solve_report* report);
+
 /* elliptic_solve runs a linear FGMRES solve with the multigrid preconditioner (opts->precondition 2,
  * per-phase profiling off) as ONE CUDA graph from the second solve on a domain with the same
  * tolerance and kernels: the Hessenberg column, its Givens rotations and the stopping test of
@@ -259,7 +269,8 @@ dg_status elliptic_solve(struct dg_domain* dom, const double* b, double* u, doub
  * stream, and synchronises); run launches it on `stream` and waits for it, filling count
  * reports. b[i] and u[i] are device pointers of domain i's n_dof values, fixed for the life of the
  * batch (u[i] holds the initial guess before each run and the solution after it); the domains
- * must outlive the batch and must not be used by other calls while a run is in flight. opts as for
+ * must outlive every run of the batch and must not be used by other calls while a run is in flight
+ * (destroying the batch does not touch them, so it may come after them). opts as for
  * elliptic_solve with krylov 0 and precondition 2 (NULL: defaults). Errors of create and run are
  * described by dg_last_error(NULL). Not in the paper, whose solves run one at a time. */
 typedef struct dg_batch dg_batch;

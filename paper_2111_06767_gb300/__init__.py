@@ -16,7 +16,7 @@ from ._native import NativeError, check
 
 _lib = nat.load()
 
-__all__ = ["Domain", "Server", "solve_opts", "NativeError", "lib"]
+__all__ = ["Domain", "Batch", "Server", "solve_opts", "NativeError", "lib"]
 
 
 def lib():
@@ -235,6 +235,29 @@ class Domain:
         return {name: {"launches": int(a.launches), "ms": a.milliseconds, "bytes": a.bytes, "flops": a.flops}
                 for name, a in zip(nat.PHASES, arr)}
 
+    def solve_host(self, f_host, u_host, tol=1e-10, opts=None, check_status=True):
+        """elliptic_solve_host: f_host, u_host are contiguous float64 host arrays (numpy, or CPU
+        tensors; pinned ones make the copies DMA transfers); u_host is overwritten with the solution."""
+        import numpy as np
+
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                assert a.device.type == "cpu" and a.dtype == torch.float64 and a.is_contiguous()
+                return C.c_void_p(a.data_ptr())
+            assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+            return C.c_void_p(a.ctypes.data)
+
+        rep = nat.dg_solve_report()
+        o = opts if opts is not None else solve_opts()
+        st = _lib.elliptic_solve_host(self._h, hp(f_host), hp(u_host), tol, C.byref(o), C.byref(rep))
+        if check_status and st != nat.DG_OK:
+            msg = _lib.dg_last_error(self._h)
+            raise NativeError(st, msg.decode() if msg else "")
+        return SolveReport(rep.status, rep.iterations, rep.newton_steps, rep.line_search_steps, rep.initial_residual,
+                           rep.final_residual, rep.relative_residual, rep.seconds)
+
     def solve(self, b, u, tol=1e-10, opts=None, check_status=True):
         """Run elliptic_solve on the domain's stream (synchronises it with torch's current stream)."""
         torch.cuda.current_stream().synchronize()
@@ -246,6 +269,49 @@ class Domain:
             raise NativeError(st, msg.decode() if msg else "")
         return SolveReport(rep.status, rep.iterations, rep.newton_steps, rep.line_search_steps, rep.initial_residual,
                            rep.final_residual, rep.relative_residual, rep.seconds)
+
+
+class Batch:
+    """Many independent linear solves captured as one CUDA graph (elliptic_batch_*): `domains`,
+    `bs` and `us` are equal-length sequences of Domain objects and their FP64 CUDA right-hand sides
+    and solution vectors (fixed for the life of the batch; us hold the initial guesses)."""
+
+    def __init__(self, domains, bs, us, tol=1e-10, opts=None):
+        n = len(domains)
+        self._keep = (list(domains), list(bs), list(us))
+        arr = lambda xs: (C.c_void_p * n)(*[x for x in xs])
+        self._d = arr([d._h.value for d in domains])
+        self._b = arr([_ptr(b).value for b in bs])
+        self._u = arr([_ptr(u).value for u in us])
+        self.count = n
+        self._h = C.c_void_p()
+        o = opts if opts is not None else solve_opts()
+        torch.cuda.current_stream().synchronize()
+        st = _lib.elliptic_batch_create(self._d, self._b, self._u, n, tol, C.byref(o), C.byref(self._h))
+        if st != nat.DG_OK:
+            msg = _lib.dg_last_error(None)
+            raise NativeError(st, msg.decode() if msg else "")
+
+    def run(self, stream=None):
+        """Launch every solve (one graph launch) and wait; returns one SolveReport per solve."""
+        reps = (nat.dg_solve_report * self.count)()
+        st = _lib.elliptic_batch_run(self._h, _stream(stream), reps)
+        if st != nat.DG_OK:
+            msg = _lib.dg_last_error(None)
+            raise NativeError(st, msg.decode() if msg else "")
+        return [SolveReport(r.status, r.iterations, r.newton_steps, r.line_search_steps, r.initial_residual,
+                            r.final_residual, r.relative_residual, r.seconds) for r in reps]
+
+    def close(self):
+        if self._h:
+            _lib.elliptic_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

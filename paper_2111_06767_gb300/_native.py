@@ -100,6 +100,12 @@ SIGNATURES = {
     "dg_layout_coordinates_host": (C.c_int, [C.POINTER(dg_domain_desc), C.POINTER(C.c_double),
                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "elliptic_solve": (C.c_int, [_vp, _vp, _vp, C.c_double, C.POINTER(dg_solve_opts), C.POINTER(dg_solve_report)]),
+    "elliptic_solve_host": (C.c_int, [_vp, _vp, _vp, C.c_double, C.POINTER(dg_solve_opts),
+                                      C.POINTER(dg_solve_report)]),
+    "elliptic_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _i32, C.c_double,
+                                        C.POINTER(dg_solve_opts), C.POINTER(_vp)]),
+    "elliptic_batch_run": (C.c_int, [_vp, _vp, C.POINTER(dg_solve_report)]),
+    "elliptic_batch_destroy": (None, [_vp]),
     "dg_kernel_launches": (C.c_int64, []),
     "dg_profile_enable": (C.c_int, [_vp, _i32]),
     "dg_profile_read": (C.c_int, [_vp, C.POINTER(dg_phase_stats)]),

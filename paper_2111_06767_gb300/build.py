@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libdg_elliptic.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["lgl.cpp", "dg_apply.cu", "schwarz.cu", "mg.cu", "blas.cu", "puncture.cu", "setup.cu", "solver.cu",
            "capi.cu", "serve.cpp", "noalloc.cu", "tc_gemm.cu", "autotune.cu",
-           "lin_inverse.cu", "curved.cu"]
+           "lin_inverse.cu", "curved.cu", "krylov_dev.cu"]
 
 
 def nvcc() -> str:

@@ -23,7 +23,14 @@ std::map<std::vector<int64_t>, int> g_tuned;
 
 thread_local cudaStream_t tl_alloc_stream = nullptr;
 
-// DG_TUNE_LOG=1: one line on stderr per tuned shape with the candidate kept and every candidate's time.
+bool tuning_enabled() {
+  const char* v = std::getenv("DG_AUTOTUNE");
+  return !(v && std::strcmp(v, "0") == 0);
+}
+}  // namespace
+
+// DG_TUNE_LOG=1: one line on stderr per tuned shape with the candidate kept and every candidate's
+// time, and one per captured whole-solve graph.
 bool tune_log() {
   static const bool on = [] {
     const char* v = std::getenv("DG_TUNE_LOG");
@@ -31,12 +38,6 @@ bool tune_log() {
   }();
   return on;
 }
-
-bool tuning_enabled() {
-  const char* v = std::getenv("DG_AUTOTUNE");
-  return !(v && std::strcmp(v, "0") == 0);
-}
-}  // namespace
 
 cudaStream_t alloc_stream() { return tl_alloc_stream; }
 

@@ -331,6 +331,41 @@ dg_status elliptic_solve(dg_domain* dom, const double* b, double* u, double tol,
   return result;
 }
 
+dg_status elliptic_solve_host(dg_domain* dom, const double* f_host, double* u_host, double tol,
+                              const dg_solve_opts* opts, dg_solve_report* report) {
+  if (!dom) return DG_ERR_INVALID_ARG;
+  dg_status st = guarded(dom, [&] {
+    DG_REQUIRE(u_host != nullptr, "u_host must be a host pointer");
+    DG_REQUIRE(f_host != nullptr || dom->desc.problem == DG_PROBLEM_PUNCTURE, "f_host must be a host pointer");
+    const int64_t n = dom->levels[0].ndof;
+    if (!dom->host_f.get()) {
+      dom->host_f.alloc(n);
+      dom->host_b.alloc(n);
+      dom->host_u.alloc(n);
+    }
+    cudaStream_t s = dom->stream;
+    DG_CUDA(cudaMemcpyAsync(dom->host_u.get(), u_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    if (f_host) {
+      DG_CUDA(cudaMemcpyAsync(dom->host_f.get(), f_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      dg::launch_scale_mul(n, dom->mass.get(), dom->host_f.get(), dom->host_b.get(), s);
+    }
+  });
+  if (st != DG_OK) {
+    if (report) report->status = st;
+    return st;
+  }
+  const dg_status result = elliptic_solve(dom, f_host ? dom->host_b.get() : nullptr, dom->host_u.get(), tol, opts,
+                                          report);
+  st = guarded(dom, [&] {
+    DG_CUDA(cudaMemcpyAsync(u_host, dom->host_u.get(), sizeof(double) * dom->levels[0].ndof, cudaMemcpyDeviceToHost,
+                            dom->stream));
+    DG_CUDA(cudaStreamSynchronize(dom->stream));
+  });
+  if (st != DG_OK) return st;
+  if (result != DG_OK) dom->err = "solve ended with status " + std::to_string((int)result);
+  return result;
+}
+
 dg_status elliptic_batch_create(dg_domain* const* domains, const double* const* b, double* const* u, int32_t count,
                                 double tol, const dg_solve_opts* opts, dg_batch** out) {
   if (!domains || !b || !u || !out || count < 1) {

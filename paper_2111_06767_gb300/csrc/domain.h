@@ -35,6 +35,8 @@ struct SchwarzLevel {
   int n_tiles = 0;
   DevBuf<int4> tiles_tc;           // tensor-core GEMM tiles: 128 rows x 64 columns
   int n_tiles_tc = 0;
+  DevBuf<int4> tiles_tc256;        // tensor-core GEMM tiles: 128 rows x 256 columns (one read of a
+  int n_tiles_tc256 = 0;           //   128-row slab of the inverse per class of at most 256 columns)
   DevBuf<int4> units;              // fused coarse smoother GEMM units: 16 rows x all columns of a class
   int n_units = 0;
   DevBuf<unsigned> bar;            // fused coarse smoother barrier state
@@ -139,6 +141,8 @@ struct dg_domain {
   bool linv_current = false; // per-subdomain inverses built for the current linearization
   bool use_tc = false;       // subdomain GEMM on tcgen05 tensor cores (MIXED)
   bool coarse_fused = false; // fused cooperative smoother on coarse levels (DG_COARSE_FUSED=1 turns it on)
+  int barrier_stall = 0;     // DG_TEST_BARRIER_STALL=1 (read when a solve starts): the fused smoother's
+                             // barriers wait for one CTA more than launched, so every wait runs out
   dg::DevBuf<int> err_flag;       // set by device code whose bounded wait gave up
   // the V-cycle replayed as one CUDA graph (fixed input/output buffers; captured on the second use)
   bool graphs = true;
@@ -146,13 +150,30 @@ struct dg_domain {
   cudaGraphExec_t vgraph = nullptr;
   bool vgraph_lin = false;
   bool vgraph_prof = false;
+  int vgraph_stall = 0;
   int64_t vgraph_kernels = 0;  // kernels in the captured graph (counted again at every replay)
   int vgraph_m = -1;
   int vgraph_sub = -1;
   dg::DevBuf<double> vin64, vout64;
   cudaStream_t gstream = nullptr;  // private stream the graph is captured on and replayed in
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  // A whole FGMRES solve as one CUDA graph (device-resident Hessenberg/Givens, the Arnoldi loop a
+  // conditional WHILE node): built when a solve with the same key has run once host-driven.
+  cudaGraphExec_t sgraph = nullptr;
+  std::vector<int64_t> sgraph_key, skey_seen;
+  int kr_cap = 0;
+  int64_t sgraph_body_kernels = 0, sgraph_fixed_kernels = 0;  // kernels per loop body / outside it
+  dg::DevBuf<dg::KrylovState> kst;
+  dg::DevBuf<double> kbuf;            // H, rotations, g, y, inner products, norms of the captured solve
+  dg::DevBuf<double> kb, kx, zfix;    // the graph's fixed b and x, and the operator input Z_j
+  cudaStream_t gstream2 = nullptr;    // second capture stream (the loop body)
+  int* cancel_host = nullptr;         // mapped pinned flag the rotation kernel reads (serving cancel)
+  dg::DevBuf<double> host_f, host_b, host_u;  // device copies for elliptic_solve_host
+  int* cancel_dev = nullptr;
   ~dg_domain() {
+    if (sgraph) cudaGraphExecDestroy(sgraph);
+    if (gstream2) cudaStreamDestroy(gstream2);
+    if (cancel_host) cudaFreeHost(cancel_host);
     if (vgraph) cudaGraphExecDestroy(vgraph);
     if (gev_in) cudaEventDestroy(gev_in);
     if (gev_out) cudaEventDestroy(gev_out);
@@ -163,6 +184,10 @@ struct dg_domain {
 namespace dg {
 
 void domain_setup(dg_domain* dom);
+dg_batch* batch_create(dg_domain* const* doms, const double* const* b, double* const* u, int count, double tol,
+                       const dg_solve_opts& o);
+void batch_run(dg_batch* bt, cudaStream_t s, dg_solve_report* reps);
+void batch_destroy(dg_batch* bt);
 void profile_read(dg_domain* dom, dg_phase_stats* out);
 void ensure_schwarz(dg_domain* dom, int level);
 size_t domain_device_bytes(const dg_domain* dom);

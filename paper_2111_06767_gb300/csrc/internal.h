@@ -34,6 +34,10 @@ int64_t launches_total();
     ::dg::count_launches(k);                \
     DG_CUDA(cudaGetLastError());            \
   } while (0)
+// Message of the latest call on this thread that had no domain handle (dg_domain_create that
+// failed, dg_dot_noalloc); dg_last_error(NULL) returns it.
+void set_null_handle_error(const std::string& msg);
+const char* null_handle_error();
 #define DG_REQUIRE(cond, msg)                                  \
   do {                                                         \
     if (!(cond)) ::dg::fail(DG_ERR_INVALID_ARG, (msg));        \
@@ -210,15 +214,19 @@ struct CoarseArgs {
   int* err;                  // set if a barrier wait gave up
   int iterations;
   int u_zero;                // first step gathers b (u = 0)
+  int stall;                 // extra arrivals every barrier waits for: 0, or 1 to make every wait run out
+                             // (the generation flag is then never advanced; the timeout test's switch)
 };
 bool coarse_smooth_available(int N);
 void launch_coarse_smooth(int N, const CoarseArgs& a, cudaStream_t s);
 
 // Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
 bool tc_gemm_available();
-// split: K split across a cluster of 1, 2, 4 or 8 CTAs; 0 picks it from the tile count.
+// split: K split across a cluster of 1, 2, 4 or 8 CTAs; 0 picks it from the tile count. bn: tile
+// width, 64 or 256 (d_tiles must list tiles of that width).
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split = 0);
+                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split = 0,
+                          int bn = 64);
 // Splits the tensor-core GEMM accepts for this shape (each CTA keeps >= 4 K chunks).
 std::vector<int> tc_gemm_splits(int ld);
 
@@ -226,6 +234,7 @@ std::vector<int> tc_gemm_splits(int ld);
 // candidate (run(c) launches it once on stream s) and keep the fastest; later calls return the
 // kept choice. candidates[0] is the heuristic default, used alone when DG_AUTOTUNE=0 or while s is
 // being captured into a graph.
+bool tune_log();  // DG_TUNE_LOG=1
 int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates,
              const std::function<void(int)>& run, cudaStream_t s);
 
@@ -308,6 +317,41 @@ void launch_subtract_combination(int64_t n, int m, const double* V, int64_t ld, 
 // x += sum_k y[k] Z[k*ld + i]
 void launch_add_combination(int64_t n, int m, const double* Z, int64_t ld, const double* y, double* x, cudaStream_t s);
 int multidot_partial_blocks();
+
+// Device-resident flexible GMRES (krylov_dev.cu): the state of one solve, in device memory.
+enum { KR_RUNNING = 0, KR_CONVERGED = 1, KR_BREAKDOWN = 2, KR_CAP = 3, KR_CANCELLED = 4 };
+struct KrylovState {
+  int j;           // column the running iteration computes (V_j, Z_j)
+  int k;           // completed columns
+  int status;      // KR_*
+  int max_it;      // columns allowed (input)
+  int rel_to_b;    // tolerance relative to ||b|| (input) instead of ||b - A x0||
+  int runs;        // loop bodies executed (Arnoldi iterations attempted)
+  double tol;      // relative tolerance (input)
+  double tol_abs;  // absolute threshold on the residual estimate
+  double beta;     // ||b - A x0||
+  double scale;    // factor of the next basis vector: 1 / beta, then 1 / h_{j+1,j}
+  double est;      // latest residual estimate |g_k|
+};
+void launch_kr_start(KrylovState* st, double tol, int max_it, bool rel_to_b, const double* nrm2, double* g,
+                     cudaGraphConditionalHandle loop, cudaStream_t s);
+void launch_kr_report(const KrylovState* st, const double* nrm2, double* out, cudaStream_t s);
+void launch_kr_scale_into_v(int64_t n, const double* x, const KrylovState* st, double* V, int64_t ld, cudaStream_t s);
+template <typename T>
+void launch_kr_load_v(int64_t n, const double* V, int64_t ld, const KrylovState* st, T* out, cudaStream_t s);
+template <typename T>
+void launch_kr_store_z(int64_t n, const T* z, const KrylovState* st, double* Z, int64_t ld, double* zfix,
+                       cudaStream_t s);
+void launch_kr_multidot(int64_t n, int cap, const double* V, int64_t ld, const double* w, const KrylovState* st,
+                        double* partial, double* out, cudaStream_t s);
+void launch_kr_sub_comb(int64_t n, const double* V, int64_t ld, const double* h, const KrylovState* st, double* w,
+                        cudaStream_t s);
+void launch_kr_givens(KrylovState* st, double* H, int ldh, double* cs, double* sn, double* g, const double* h1,
+                      const double* h2, const double* nrm2, const volatile int* cancel,
+                      cudaGraphConditionalHandle loop, cudaStream_t s);
+void launch_kr_trisolve(const KrylovState* st, const double* H, int ldh, const double* g, double* y, cudaStream_t s);
+void launch_kr_add_comb(int64_t n, const double* Z, int64_t ld, const double* y, const KrylovState* st, double* x,
+                        cudaStream_t s);
 
 // Puncture source terms.
 void launch_puncture_fields(int64_t n, const double* x, const double* y, const double* z, int np,

@@ -2,10 +2,18 @@
 //
 // submit() copies a request into library memory and queues it. Worker threads (one per
 // concurrently running solve, each with its own CUDA stream) admit the oldest waiting request
-// whose estimated device footprint fits the remaining memory budget, build its domain, solve it
-// and publish the result; admission happens whenever a worker and enough budget free up, so
+// whose estimated device footprint fits the remaining memory budget, take a domain for it, solve
+// it and publish the result; admission happens whenever a worker and enough budget free up, so
 // requests that arrive while others run join the device work as capacity allows. poll() hands a
 // finished result back exactly once.
+//
+// Domains stay on the device between requests: a finished request's domain (its multigrid
+// hierarchy, explicit subdomain inverses, Krylov and multigrid work vectors and captured graphs)
+// is kept in an idle pool keyed by its descriptor, and the next request with the same descriptor
+// reuses it instead of building a new one (the paper's amortisation of the explicit inverses over
+// many solves, Sec. III.E). Idle domains count against the memory budget and are released, least
+// recently used first, when a request that needs new memory would not fit otherwise. Requests with
+// per-node geometry or coefficients are not pooled.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -94,9 +102,18 @@ size_t estimate_domain_bytes(const dg_domain_desc& d, int max_iterations, bool l
 
 }  // namespace dg
 
+struct PooledDomain {
+  dg_domain* dom = nullptr;
+  size_t bytes = 0;
+  uint64_t last_use = 0;
+};
+
 struct dg_server {
   dg_serve_desc desc{};
   std::mutex mu;
+  std::unordered_map<std::string, std::vector<PooledDomain>> idle;  // key: descriptor bytes
+  size_t idle_bytes = 0;
+  uint64_t use_clock = 0;
   std::condition_variable cv_work, cv_done;
   std::deque<Job*> waiting;
   std::unordered_map<uint64_t, Job*> jobs;
@@ -108,19 +125,79 @@ struct dg_server {
   double t0 = clock_now();
 
   void run(int wid);
+  // With mu held: an idle domain for this key (removed from the pool), or nullptr.
+  dg_domain* take_idle(const std::string& key, size_t* bytes);
+  // With mu held: move least recently used idle domains into `out` until `need` more bytes fit.
+  void evict_for(size_t need, std::vector<dg_domain*>& out);
 };
+
+namespace {
+// Pool key: the descriptor's bytes, or "" (not pooled) for per-node geometry or coefficients.
+std::string pool_key(const dg_domain_desc& d) {
+  if (d.node_xyz || d.coef) return std::string();
+  dg_domain_desc k = d;
+  k.node_xyz = nullptr;
+  k.coef = nullptr;
+  return std::string(reinterpret_cast<const char*>(&k), sizeof(k));
+}
+}  // namespace
+
+dg_domain* dg_server::take_idle(const std::string& key, size_t* bytes) {
+  if (key.empty()) return nullptr;
+  auto it = idle.find(key);
+  if (it == idle.end() || it->second.empty()) return nullptr;
+  PooledDomain p = it->second.back();
+  it->second.pop_back();
+  idle_bytes -= p.bytes;
+  *bytes = p.bytes;
+  return p.dom;
+}
+
+void dg_server::evict_for(size_t need, std::vector<dg_domain*>& out) {
+  while (in_use + idle_bytes + need > budget && idle_bytes > 0) {
+    std::vector<PooledDomain>* oldest = nullptr;
+    size_t pos = 0;
+    for (auto& kv : idle)
+      for (size_t i = 0; i < kv.second.size(); ++i)
+        if (!oldest || kv.second[i].last_use < (*oldest)[pos].last_use) {
+          oldest = &kv.second;
+          pos = i;
+        }
+    if (!oldest) break;
+    idle_bytes -= (*oldest)[pos].bytes;
+    out.push_back((*oldest)[pos].dom);
+    oldest->erase(oldest->begin() + pos);
+  }
+}
 
 void dg_server::run(int wid) {
   cudaStream_t s = streams[wid % streams.size()];
   for (;;) {
     Job* job = nullptr;
+    dg_domain* dom = nullptr;
+    std::string key;
+    std::vector<dg_domain*> evicted;
     {
       std::unique_lock<std::mutex> lk(mu);
       for (;;) {
         if (stopping && waiting.empty()) return;
         for (auto it = waiting.begin(); it != waiting.end(); ++it) {
-          if (in_use + (*it)->bytes <= budget) {
+          const std::string k = pool_key((*it)->req.domain);
+          size_t pooled = 0;
+          dg_domain* d = take_idle(k, &pooled);
+          if (d) {  // an idle domain of this shape: no new memory
             job = *it;
+            dom = d;
+            key = k;
+            job->bytes = pooled;
+            waiting.erase(it);
+            break;
+          }
+          if (in_use + (*it)->bytes > budget) continue;
+          evict_for((*it)->bytes, evicted);
+          if (in_use + idle_bytes + (*it)->bytes <= budget) {
+            job = *it;
+            key = k;
             waiting.erase(it);
             break;
           }
@@ -131,48 +208,46 @@ void dg_server::run(int wid) {
       in_use += job->bytes;
       job->admit_time = clock_now() - t0;
     }
-    dg_domain* dom = nullptr;
-    dg_status st = dg_domain_create(&job->req.domain, s, &dom);
+    for (dg_domain* d : evicted) dg_domain_destroy(d);
+    dg_status st = DG_OK;
+    if (dom) {
+      dom->stream = s;  // idle: all of its earlier work is complete
+    } else {
+      st = dg_domain_create(&job->req.domain, s, &dom);
+    }
     if (st == DG_OK) {
       dg_layout lay;
       dg_domain_layout(dom, &lay);
-      double *u = nullptr, *b = nullptr, *f = nullptr;
-      const size_t nb = sizeof(double) * lay.n_dof;
-      if (cudaMallocAsync((void**)&u, nb, s) != cudaSuccess || cudaMallocAsync((void**)&b, nb, s) != cudaSuccess ||
-          cudaMallocAsync((void**)&f, nb, s) != cudaSuccess) {
-        (void)cudaGetLastError();
+      try {
+        job->u.assign(lay.n_dof, 0.0);
+      } catch (...) {
         st = DG_ERR_OOM;
-      } else {
-        cudaMemsetAsync(u, 0, nb, s);
-        if (job->req.domain.problem == DG_PROBLEM_POISSON) {
-          cudaMemcpyAsync(f, job->f.data(), nb, cudaMemcpyHostToDevice, s);
-          st = dg_rhs(dom, f, b, s);
-        } else {
-          cudaMemsetAsync(b, 0, nb, s);
-        }
-        if (st == DG_OK) {
-          dg_solve_opts o = job->req.opts;
-          o.relative_to_b = job->req.domain.problem == DG_PROBLEM_POISSON ? 1 : 0;
-          dom->cancel = &job->cancel;
-          st = elliptic_solve(dom, b, u, job->req.tol, &o, &job->report);
-          dom->cancel = nullptr;
-        }
-        job->u.resize(lay.n_dof);
-        if (cudaMemcpyAsync(job->u.data(), u, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-          (void)cudaGetLastError();
-          if (st == DG_OK) st = DG_ERR_CUDA;
-        }
       }
-      if (u) cudaFreeAsync(u, s);
-      if (b) cudaFreeAsync(b, s);
-      if (f) cudaFreeAsync(f, s);
-      cudaStreamSynchronize(s);
+      if (st == DG_OK) {
+        dg_solve_opts o = job->req.opts;
+        o.relative_to_b = job->req.domain.problem == DG_PROBLEM_POISSON ? 1 : 0;
+        dom->cancel = &job->cancel;
+        st = elliptic_solve_host(dom, job->req.domain.problem == DG_PROBLEM_POISSON ? job->f.data() : nullptr,
+                                 job->u.data(), job->req.tol, &o, &job->report);
+        dom->cancel = nullptr;
+      }
+      if (cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (st == DG_OK) st = DG_ERR_CUDA;
+      }
+    }
+    const bool keep = dom && !key.empty() && (st == DG_OK || st == DG_ERR_NOT_CONVERGED || st == DG_ERR_CANCELLED);
+    if (dom && !keep) {
       dg_domain_destroy(dom);
+      dom = nullptr;
     }
     {
       std::lock_guard<std::mutex> lk(mu);
       in_use -= job->bytes;
+      if (keep) {
+        idle[key].push_back(PooledDomain{dom, job->bytes, ++use_clock});
+        idle_bytes += job->bytes;
+      }
       job->status = st;
       job->report.status = st;
       job->finish_time = clock_now() - t0;
@@ -323,6 +398,8 @@ void elliptic_serve_destroy(dg_server* srv) {
   }
   srv->cv_work.notify_all();
   for (auto& t : srv->workers) t.join();
+  for (auto& kv : srv->idle)
+    for (auto& p : kv.second) dg_domain_destroy(p.dom);
   for (auto& kv : srv->jobs) delete kv.second;
   for (auto s : srv->streams) cudaStreamDestroy(s);
   delete srv;

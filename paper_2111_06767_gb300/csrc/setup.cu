@@ -215,6 +215,13 @@ void classify_schwarz(dg_domain* dom, Level& L) {
         tiles_tc.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
   sw.n_tiles_tc = (int)tiles_tc.size();
   upload(sw.tiles_tc, tiles_tc, s);
+  std::vector<int4> tiles_tc256;
+  for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
+    for (int r0 = 0; r0 < sw.ld; r0 += 128)
+      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 256)
+        tiles_tc256.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
+  sw.n_tiles_tc256 = (int)tiles_tc256.size();
+  upload(sw.tiles_tc256, tiles_tc256, s);
   std::vector<int4> units;
   for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 16) units.push_back(make_int4(c, r0, sw.class_first[c], sw.class_count[c]));
@@ -667,6 +674,7 @@ size_t domain_device_bytes(const dg_domain* dom) {
     b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.class_of_col.bytes() + sw.xform_of_elem.bytes() +
          sw.inv64.bytes() +
          sw.inv32.bytes() + sw.inv16.bytes() + sw.inv16_scale.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() +
+         sw.tiles_tc256.bytes() +
          sw.units.bytes() + sw.bar.bytes();
     for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
                     &L.w64.gH, &L.w64.linA, &L.w64.linv})

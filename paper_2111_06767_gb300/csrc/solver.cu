@@ -4,6 +4,9 @@
 // (k+1) x k Hessenberg matrix and its Givens rotations, read back once per Krylov iteration.
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
 #include <type_traits>
 
 #include "domain.h"
@@ -27,6 +30,10 @@ int apply_variant(dg_domain* dom, Level& L, bool fused, const std::function<void
     // launch shapes of the line kernel; the plane kernel for plain FP32 applies at N = 4
     std::vector<int> cand{0, 1, 2, 3};
     if (!fused && dom->N == 4 && sizeof(T) == 4) cand.push_back(4);
+    if (!fused && dom->N >= 4 && sizeof(T) == 4) {  // the block-of-lines kernel, two launch shapes
+      cand.push_back(5);
+      cand.push_back(6);
+    }
     // DG_APPLY_VARIANT=v pins one candidate (tests of each launch shape)
     static const int forced = [] {
       const char* e = std::getenv("DG_APPLY_VARIANT");
@@ -201,14 +208,21 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
     return;
   }
   if (dom->use_tc) {
-    auto run = [&](int split) {
-      launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, sw.tiles_tc.get(), sw.n_tiles_tc,
-                           dom->err_flag.get(), (float)sw.inv_scale, s, split);
+    // launch shape: split-K factor (low 4 bits; 0 = chosen from the tile count) and tile width
+    // (kWide: 256 columns, else 64)
+    constexpr int kWide = 16;
+    auto run = [&](int shape) {
+      const bool wide = (shape & kWide) != 0;
+      launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E,
+                           wide ? sw.tiles_tc256.get() : sw.tiles_tc.get(), wide ? sw.n_tiles_tc256 : sw.n_tiles_tc,
+                           dom->err_flag.get(), (float)sw.inv_scale, s, shape & 15, wide ? 256 : 64);
     };
     if (L.gemm_split < 0) {
-      // split-K factor: the default (0) first, then every split the shape allows
+      // the default (0) first, then every split the shape allows, at both tile widths
       std::vector<int> cand{0};
       for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(sp);
+      cand.push_back(kWide);
+      for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(kWide | sp);
       // DG_GEMM_SPLIT=k pins one candidate (tests and measurements of each launch shape); read
       // when a level first runs its GEMM, so a process can set it per domain
       const char* e = std::getenv("DG_GEMM_SPLIT");
@@ -218,7 +232,7 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
         run(forced);
         return;
       }
-      const int pick = autotune({2, sw.n_classes, sw.ld, sw.n_tiles_tc, L.E}, cand, run, s);
+      const int pick = autotune({3, sw.n_classes, sw.ld, sw.n_tiles_tc, sw.n_tiles_tc256, L.E}, cand, run, s);
       cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
       DG_CUDA(cudaStreamIsCapturing(s, &cap));
       if (cap != cudaStreamCaptureStatusNone) {
@@ -268,6 +282,7 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
       a.err = dom->err_flag.get();
       a.iterations = iterations;
       a.u_zero = u_is_zero ? 1 : 0;
+      a.stall = dom->barrier_stall;
       const double vec = (double)L.E * sw.nS * 4.0, nS = sw.nS;
       PhaseScope ps(dom->prof, DG_PHASE_COARSE_SMOOTH, s,
                     iterations * ((double)sw.n_classes * nS * nS * 4.0 + 2 * vec + 4.0 * 4.0 * L.ndof),
@@ -400,8 +415,8 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
   const int m = dom->subdomain_iterations;
   const int sub = dom->subdomain_solver;
   const bool prof = dom->prof.on;
-  if (dom->vgraph &&
-      (dom->vgraph_lin != lin || dom->vgraph_m != m || dom->vgraph_sub != sub || dom->vgraph_prof != prof)) {
+  if (dom->vgraph && (dom->vgraph_lin != lin || dom->vgraph_m != m || dom->vgraph_sub != sub ||
+                      dom->vgraph_prof != prof || dom->vgraph_stall != dom->barrier_stall)) {
     // different kernels: drop the graph and run once uncaptured (it may allocate) before re-capturing
     cudaGraphExecDestroy(dom->vgraph);
     dom->vgraph = nullptr;
@@ -450,6 +465,7 @@ void vcycle_fixed(dg_domain* dom, cudaStream_t s) {
     dom->vgraph_m = m;
     dom->vgraph_sub = sub;
     dom->vgraph_prof = prof;
+    dom->vgraph_stall = dom->barrier_stall;
   }
   DG_CUDA(cudaGraphLaunch(dom->vgraph, gs));
   count_launches(dom->vgraph_kernels);
@@ -546,6 +562,7 @@ double norm2(dg_domain* dom, const double* x, cudaStream_t s) {
 struct LinearResult {
   int iterations = 0;
   double r0 = 0, final_res = 0;
+  double ref = 0;  // the norm the tolerance is relative to: ||b|| or ||b - A x0||
   dg_status status = DG_OK;
 };
 
@@ -562,6 +579,7 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
   const double beta = norm2(dom, dom->r.get(), s);
   R.r0 = beta;
   const double ref = rel_to_b ? ref_b_norm : beta;
+  R.ref = ref;
   if (!std::isfinite(beta)) { R.status = DG_ERR_BREAKDOWN; return R; }
   if (beta <= tol * ref || beta == 0.0) { R.final_res = beta; return R; }
   launch_axpby<double>(n, 1.0 / beta, dom->r.get(), 0.0, dom->V.get(), s);
@@ -635,6 +653,401 @@ LinearResult fgmres(dg_domain* dom, const double* b, double* x, double tol, doub
   return R;
 }
 
+// ------------------------------------------------------------------ FGMRES as one CUDA graph
+//
+// The same method as fgmres() above with the Hessenberg column, the Givens rotations and the
+// stopping test on the device (krylov_dev.cu). A solve is one graph launch: prologue (r = b - A x,
+// norms, g_0, V_0), a conditional WHILE node whose body is one Arnoldi iteration (V_j into the
+// V-cycle's input, the V-cycle itself, Z_j, A Z_j, two classical Gram-Schmidt passes, the rotation
+// kernel that sets the loop condition, V_{j+1}), and the epilogue (y = R^-1 g, x += Z y, the true
+// residual). The graph works on fixed buffers (b and x are copied in and out around the launch),
+// and holds at most kGraphCap Arnoldi columns: a solve that needs more continues host-driven from
+// the graph's iterate (a restart).
+constexpr int kGraphCap = 40;
+
+// The captured solve's small device arrays, carved from one buffer.
+struct KrylovLayout {
+  int ldh;
+  double *H, *cs, *sn, *g, *y, *h1, *h2, *nrm;  // nrm: [0] ||r||^2 or ||w||^2, [1] ||b||^2, [2] final ||b - A x||^2
+  static size_t size(int cap) { return (size_t)(cap + 1) * cap + 3 * (size_t)cap + 3 * (size_t)(cap + 1) + 4; }
+  KrylovLayout(double* base, int cap) : ldh(cap + 1) {
+    H = base;
+    cs = H + (size_t)ldh * cap;
+    sn = cs + cap;
+    g = sn + cap;
+    y = g + cap + 1;
+    h1 = y + cap;
+    h2 = h1 + cap + 1;
+    nrm = h2 + cap + 1;
+  }
+};
+
+// what the captured kernels depend on besides the buffers' contents
+std::vector<int64_t> solve_graph_key(dg_domain* dom, int cap, double tol, bool rel_to_b) {
+  int64_t tb = 0;
+  std::memcpy(&tb, &tol, sizeof(tb));
+  return {cap, tb, rel_to_b ? 1 : 0, dom->mixed ? 1 : 0, dom->lin_set ? 1 : 0, dom->subdomain_iterations,
+          dom->subdomain_solver, dom->barrier_stall, (int64_t)(uintptr_t)dom->V.get(),
+          (int64_t)(uintptr_t)dom->Zb.get(), dom->desc.presmooth, dom->desc.postsmooth, dom->coarse_fused ? 1 : 0};
+}
+
+bool solve_graph_wanted(dg_domain* dom, int pmode) {
+  const char* e = std::getenv("DG_SOLVE_GRAPH");
+  if (e && std::strcmp(e, "0") == 0) return false;
+  return dom->graphs && pmode == 2 && !dom->prof.on;
+}
+
+// Arnoldi columns a captured solve holds (DG_SOLVE_GRAPH_CAP overrides, for tests of the restart)
+int solve_graph_cap(int max_it) {
+  const char* e = std::getenv("DG_SOLVE_GRAPH_CAP");
+  const int v = e ? std::atoi(e) : 0;
+  return std::min(max_it, v > 0 ? std::min(v, kGraphCap) : kGraphCap);
+}
+
+// Buffers, streams and the mapped cancel flag of a captured solve (allocated before any capture).
+void prepare_solve_graph(dg_domain* dom, int cap) {
+  const int64_t n = dom->levels[0].ndof;
+  ensure_workspace(dom, cap);
+  if (!dom->gstream) {
+    DG_CUDA(cudaStreamCreateWithFlags(&dom->gstream, cudaStreamNonBlocking));
+    DG_CUDA(cudaEventCreateWithFlags(&dom->gev_in, cudaEventDisableTiming));
+    DG_CUDA(cudaEventCreateWithFlags(&dom->gev_out, cudaEventDisableTiming));
+  }
+  if (!dom->gstream2) DG_CUDA(cudaStreamCreateWithFlags(&dom->gstream2, cudaStreamNonBlocking));
+  if (!dom->cancel_host) {
+    DG_CUDA(cudaHostAlloc((void**)&dom->cancel_host, sizeof(int), cudaHostAllocMapped));
+    *dom->cancel_host = 0;
+    DG_CUDA(cudaHostGetDevicePointer((void**)&dom->cancel_dev, dom->cancel_host, 0));
+  }
+  if (dom->kr_cap != cap || !dom->kst.get()) {
+    dom->kst.alloc(1);
+    dom->kbuf.alloc(KrylovLayout::size(cap) + 8);  // + the 8-double report
+    dom->kr_cap = cap;
+  }
+  if (!dom->kb.get()) {
+    dom->kb.alloc(n);
+    dom->kx.alloc(n);
+    dom->zfix.alloc(n);
+  }
+  if (dom->mixed) {
+    if (!dom->vin32.get()) dom->vin32.alloc(2 * n);
+  } else if (!dom->vin64.get()) {
+    dom->vin64.alloc(n);
+    dom->vout64.alloc(n);
+  }
+}
+
+// Run every kernel shape a captured solve uses once, uncaptured, so that launch shapes are tuned
+// and lazily built data exist before the capture (nothing may allocate or tune while capturing).
+void warm_solve_kernels(dg_domain* dom) {
+  cudaStream_t s = dom->stream;
+  const int64_t n = dom->levels[0].ndof;
+  DG_CUDA(cudaMemsetAsync(dom->kx.get(), 0, sizeof(double) * n, s));
+  DG_CUDA(cudaMemsetAsync(dom->kb.get(), 0, sizeof(double) * n, s));
+  apply_level(dom, 0, dom->kx.get(), dom->r.get(), dom->kb.get(), true, s);
+  apply_level(dom, 0, dom->kx.get(), dom->w.get(), nullptr, true, s);
+  if (dom->mixed) {
+    DG_CUDA(cudaMemsetAsync(dom->vin32.get(), 0, sizeof(float) * n, s));
+    vcycle<float>(dom, dom->vin32.get(), dom->vin32.get() + n, s);
+  } else {
+    DG_CUDA(cudaMemsetAsync(dom->vin64.get(), 0, sizeof(double) * n, s));
+    vcycle<double>(dom, dom->vin64.get(), dom->vout64.get(), s);
+  }
+  DG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Capture one whole FGMRES solve of `dom` into `graph` as an independent branch: the copies of the
+// caller's b and x in (when given), the prologue, the Arnoldi loop as a conditional WHILE node, the
+// epilogue, x copied out and the 8-double report written (when given). Counts the branch's kernels
+// outside the loop and per loop body into the domain.
+void capture_solve_branch(dg_domain* dom, cudaGraph_t graph, int cap, double tol, bool rel_to_b, const double* b_in,
+                          double* x_io, double* report) {
+  const int64_t n = dom->levels[0].ndof;
+  const KrylovLayout kl(dom->kbuf.get(), cap);
+  const int ldh = kl.ldh;
+  double *H = kl.H, *cs = kl.cs, *sn = kl.sn, *g = kl.g, *y = kl.y, *h1 = kl.h1, *h2 = kl.h2, *nrm = kl.nrm;
+  KrylovState* st = dom->kst.get();
+  double* V = dom->V.get();
+  double* Z = dom->Zb.get();
+  double* w = dom->w.get();
+  double* r = dom->r.get();
+  double* part = dom->partial.get();
+  double* kb = dom->kb.get();
+  double* kx = dom->kx.get();
+  cudaStream_t gs = dom->gstream, bs = dom->gstream2;
+  const int64_t k0 = launches_total();
+  cudaGraphConditionalHandle loop;
+  bool capturing = false;
+  try {
+    DG_CUDA(cudaGraphConditionalHandleCreate(&loop, graph, 0, cudaGraphCondAssignDefault));
+    DG_CUDA(cudaStreamBeginCaptureToGraph(gs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
+    if (b_in) DG_CUDA(cudaMemcpyAsync(kb, b_in, sizeof(double) * n, cudaMemcpyDeviceToDevice, gs));
+    if (x_io) DG_CUDA(cudaMemcpyAsync(kx, x_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, gs));
+    apply_level(dom, 0, kx, r, kb, true, gs);  // r = b - A x
+    launch_multidot(n, 1, r, n, r, part, nrm, gs);
+    if (rel_to_b) launch_multidot(n, 1, kb, n, kb, part, nrm + 1, gs);
+    launch_kr_start(st, tol, cap, rel_to_b, nrm, g, loop, gs);
+    launch_kr_scale_into_v(n, r, st, V, n, gs);
+    // the Arnoldi loop: a conditional WHILE node after the prologue
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    DG_CUDA(cudaStreamGetCaptureInfo(gs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+    DG_REQUIRE(cst == cudaStreamCaptureStatusActive, "solve capture was invalidated before the Arnoldi loop");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    DG_CUDA(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    DG_CUDA(cudaStreamUpdateCaptureDependencies(gs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    DG_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int64_t kb0 = launches_total();
+    try {
+      if (dom->mixed) {
+        float* v32 = dom->vin32.get();
+        launch_kr_load_v<float>(n, V, n, st, v32, bs);
+        vcycle<float>(dom, v32, v32 + n, bs);
+        launch_kr_store_z<float>(n, v32 + n, st, Z, n, dom->zfix.get(), bs);
+      } else {
+        launch_kr_load_v<double>(n, V, n, st, dom->vin64.get(), bs);
+        vcycle<double>(dom, dom->vin64.get(), dom->vout64.get(), bs);
+        launch_kr_store_z<double>(n, dom->vout64.get(), st, Z, n, dom->zfix.get(), bs);
+      }
+      apply_level(dom, 0, dom->zfix.get(), w, nullptr, true, bs);
+      launch_kr_multidot(n, cap, V, n, w, st, part, h1, bs);  // classical Gram-Schmidt, twice
+      launch_kr_sub_comb(n, V, n, h1, st, w, bs);
+      launch_kr_multidot(n, cap, V, n, w, st, part, h2, bs);
+      launch_kr_sub_comb(n, V, n, h2, st, w, bs);
+      launch_multidot(n, 1, w, n, w, part, nrm, bs);
+      launch_kr_givens(st, H, ldh, cs, sn, g, h1, h2, nrm, dom->cancel_dev, loop, bs);
+      launch_kr_scale_into_v(n, w, st, V, n, bs);
+    } catch (...) {
+      cudaGraph_t t = nullptr;
+      cudaStreamEndCapture(bs, &t);
+      throw;
+    }
+    dom->sgraph_body_kernels = launches_total() - kb0;
+    cudaStreamCaptureStatus bst = cudaStreamCaptureStatusNone;
+    DG_CUDA(cudaStreamIsCapturing(bs, &bst));
+    cudaGraph_t t = nullptr;
+    DG_CUDA(cudaStreamEndCapture(bs, &t));
+    DG_REQUIRE(bst == cudaStreamCaptureStatusActive, "capture of the Arnoldi loop body was invalidated");
+    // epilogue
+    launch_kr_trisolve(st, H, ldh, g, y, gs);
+    launch_kr_add_comb(n, Z, n, y, st, kx, gs);
+    apply_level(dom, 0, kx, r, kb, true, gs);
+    launch_multidot(n, 1, r, n, r, part, nrm + 2, gs);
+    if (x_io) DG_CUDA(cudaMemcpyAsync(x_io, kx, sizeof(double) * n, cudaMemcpyDeviceToDevice, gs));
+    if (report) launch_kr_report(st, nrm, report, gs);
+    capturing = false;
+    DG_CUDA(cudaStreamEndCapture(gs, &t));
+  } catch (...) {
+    if (capturing) {
+      cudaGraph_t t = nullptr;
+      cudaStreamEndCapture(gs, &t);
+    }
+    (void)cudaGetLastError();
+    count_launches(-(launches_total() - k0));
+    throw;
+  }
+  dom->sgraph_fixed_kernels = launches_total() - k0 - dom->sgraph_body_kernels;
+  count_launches(-(launches_total() - k0));  // captured, not launched: counted per execution
+}
+
+void build_solve_graph(dg_domain* dom, int cap, double tol, bool rel_to_b) {
+  prepare_solve_graph(dom, cap);
+  warm_solve_kernels(dom);
+  if (tune_log())
+    std::fprintf(stderr, "dg solve graph: capturing (n_dof %lld, %d columns, %s)\n", (long long)dom->levels[0].ndof,
+                 cap, dom->mixed ? "mixed" : "fp64");
+  if (dom->sgraph) {
+    cudaGraphExecDestroy(dom->sgraph);
+    dom->sgraph = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  DG_CUDA(cudaGraphCreate(&graph, 0));
+  try {
+    capture_solve_branch(dom, graph, cap, tol, rel_to_b, nullptr, nullptr,
+                         dom->kbuf.get() + KrylovLayout::size(cap));
+    DG_CUDA(cudaGraphInstantiate(&dom->sgraph, graph, 0));
+  } catch (const Error& e) {
+    if (tune_log()) std::fprintf(stderr, "dg solve graph: capture failed: %s\n", e.message.c_str());
+    cudaGraphDestroy(graph);
+    throw;
+  }
+  cudaGraphDestroy(graph);
+  if (tune_log())
+    std::fprintf(stderr, "dg solve graph: built (%lld kernels outside the loop, %lld per iteration)\n",
+                 (long long)dom->sgraph_fixed_kernels, (long long)dom->sgraph_body_kernels);
+}
+
+// A solve's result from its 8-double report (see launch_kr_report).
+LinearResult result_from_report(const double* rp) {
+  LinearResult R;
+  R.iterations = (int)rp[0];
+  R.r0 = rp[3];
+  R.ref = rp[4];
+  R.final_res = rp[5];
+  const int status = (int)rp[1];
+  R.status = DG_OK;
+  if (status == KR_BREAKDOWN) R.status = DG_ERR_BREAKDOWN;
+  else if (status == KR_CANCELLED) R.status = DG_ERR_CANCELLED;
+  else if (!std::isfinite(R.final_res)) R.status = DG_ERR_BREAKDOWN;
+  else if (R.final_res > rp[6] * (1.0 + 1e-6)) R.status = DG_ERR_NOT_CONVERGED;
+  return R;
+}
+
+// One linear solve through the captured graph; returns false (nothing done) where the graph path
+// does not apply, so that the caller runs the host-driven solver instead.
+bool fgmres_graph(dg_domain* dom, const double* b, double* x, double tol, int max_it, int pmode, bool rel_to_b,
+                  LinearResult& R) {
+  if (!solve_graph_wanted(dom, pmode)) return false;
+  const int cap = solve_graph_cap(max_it);
+  if (cap < 1) return false;
+  cudaStream_t s = dom->stream;
+  const int64_t n = dom->levels[0].ndof;
+  ensure_workspace(dom, cap);
+  const std::vector<int64_t> key = solve_graph_key(dom, cap, tol, rel_to_b);
+  if (!dom->sgraph || dom->sgraph_key != key) {
+    if (dom->skey_seen != key) {  // first solve with these kernels: host-driven (tunes and allocates)
+      dom->skey_seen = key;
+      return false;
+    }
+    try {
+      build_solve_graph(dom, cap, tol, rel_to_b);
+    } catch (const Error&) {
+      // the capture did not work out: this domain solves host-driven from now on
+      (void)cudaGetLastError();
+      DG_CUDA(cudaStreamSynchronize(s));
+      dom->graphs = false;
+      return false;
+    }
+    dom->sgraph_key = key;
+  }
+  *reinterpret_cast<volatile int*>(dom->cancel_host) = 0;
+  DG_CUDA(cudaMemcpyAsync(dom->kb.get(), b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(dom->kx.get(), x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaGraphLaunch(dom->sgraph, s));
+  DG_CUDA(cudaMemcpyAsync(x, dom->kx.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (dom->cancel) {
+    // keep a cancel request visible to the rotation kernel while the solve runs
+    DG_CUDA(cudaEventRecord(dom->gev_out, s));
+    for (;;) {
+      const cudaError_t q = cudaEventQuery(dom->gev_out);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) DG_CUDA(q);
+      if (dom->cancel->load(std::memory_order_relaxed)) *reinterpret_cast<volatile int*>(dom->cancel_host) = 1;
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
+  double rp[8];
+  DG_CUDA(cudaMemcpyAsync(rp, dom->kbuf.get() + KrylovLayout::size(cap), sizeof(rp), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  count_launches(dom->sgraph_fixed_kernels + (int64_t)rp[2] * dom->sgraph_body_kernels);
+  R = result_from_report(rp);
+  if ((int)rp[1] == KR_CAP && max_it > cap) {
+    // more columns than the graph holds: continue host-driven from this iterate (a restart)
+    const double r0 = R.r0, ref = R.ref;
+    LinearResult more = fgmres(dom, b, x, rp[6] / std::max(ref, 1e-300), ref, max_it - cap, pmode, true);
+    R = more;
+    R.iterations += cap;
+    R.r0 = r0;
+    R.ref = ref;
+  }
+  return true;
+}
+
+}  // namespace
+}  // namespace dg
+
+// ------------------------------------------------------------------ many solves in one graph launch
+
+struct dg_batch {
+  std::vector<dg_domain*> doms;
+  cudaGraphExec_t exec = nullptr;
+  dg::DevBuf<double> reports;  // 8 doubles per solve
+  std::vector<int64_t> fixed, body;
+  int cap = 0;
+  ~dg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+namespace dg {
+
+dg_batch* batch_create(dg_domain* const* doms, const double* const* b, double* const* u, int count, double tol,
+                       const dg_solve_opts& o) {
+  DG_REQUIRE(count >= 1, "batch needs at least one solve");
+  const int max_it = o.max_iterations > 0 ? o.max_iterations : 200;
+  DG_REQUIRE(o.krylov == 0 && o.precondition == 2, "a batch runs FGMRES with the multigrid preconditioner");
+  DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  std::unique_ptr<dg_batch> bt(new dg_batch());
+  bt->cap = std::min(max_it, kGraphCap);
+  bt->reports.alloc(8 * (size_t)count);
+  for (int i = 0; i < count; ++i) {
+    dg_domain* dom = doms[i];
+    DG_REQUIRE(dom && b[i] && u[i], "null domain or vector in the batch");
+    DG_REQUIRE(dom->desc.problem == DG_PROBLEM_POISSON, "a batch holds Poisson problems");
+    for (int j = 0; j < i; ++j) DG_REQUIRE(doms[j] != dom, "a domain appears twice in the batch");
+    dom->lin_set = false;
+    dom->barrier_stall = 0;
+    prepare_solve_graph(dom, bt->cap);
+    warm_solve_kernels(dom);
+  }
+  cudaGraph_t graph = nullptr;
+  DG_CUDA(cudaGraphCreate(&graph, 0));
+  try {
+    for (int i = 0; i < count; ++i) {
+      capture_solve_branch(doms[i], graph, bt->cap, tol, o.relative_to_b != 0, b[i], u[i],
+                           bt->reports.get() + 8 * (size_t)i);
+      bt->fixed.push_back(doms[i]->sgraph_fixed_kernels);
+      bt->body.push_back(doms[i]->sgraph_body_kernels);
+    }
+    DG_CUDA(cudaGraphInstantiate(&bt->exec, graph, 0));
+  } catch (...) {
+    cudaGraphDestroy(graph);
+    throw;
+  }
+  cudaGraphDestroy(graph);
+  bt->doms.assign(doms, doms + count);
+  return bt.release();
+}
+
+void batch_run(dg_batch* bt, cudaStream_t s, dg_solve_report* reps) {
+  const size_t count = bt->doms.size();
+  for (dg_domain* d : bt->doms) *reinterpret_cast<volatile int*>(d->cancel_host) = 0;
+  DG_CUDA(cudaGraphLaunch(bt->exec, s));
+  std::vector<double> rp(8 * count);
+  DG_CUDA(cudaMemcpyAsync(rp.data(), bt->reports.get(), sizeof(double) * rp.size(), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  int64_t k = 0;
+  for (size_t i = 0; i < count; ++i) {
+    k += bt->fixed[i] + (int64_t)rp[8 * i + 2] * bt->body[i];
+    if (!reps) continue;
+    const LinearResult L = result_from_report(&rp[8 * i]);
+    dg_solve_report R{};
+    R.iterations = L.iterations;
+    R.initial_residual = L.r0;
+    R.final_residual = L.final_res;
+    R.relative_residual = L.ref > 0 ? L.final_res / L.ref : 0.0;
+    R.status = L.status;
+    reps[i] = R;
+  }
+  count_launches(k);
+}
+
+void batch_destroy(dg_batch* bt) {
+  // every run waited for its launch, so nothing of the graph is in flight; the domains are not
+  // touched (they may already be gone)
+  delete bt;
+}
+
+namespace {
+
 // Flexible conjugate gradients (the SPD alternative to FGMRES): one search direction, made
 // A-orthogonal to the previous one after every (possibly non-symmetric) V-cycle. Three host reads
 // per iteration: z.A p_old, (p.r, p.A p), ||r||. Vectors r and q = A p sit next to each other in
@@ -658,6 +1071,7 @@ LinearResult fcg(dg_domain* dom, const double* b, double* x, double tol, double 
   const double beta = norm2(dom, r, s);
   R.r0 = beta;
   const double ref = rel_to_b ? ref_b_norm : beta;
+  R.ref = ref;
   if (!std::isfinite(beta)) { R.status = DG_ERR_BREAKDOWN; return R; }
   double res = beta, pq_old = 0.0;
   for (int k = 0; k < max_it && res > tol * ref && res > 0.0; ++k) {
@@ -784,18 +1198,24 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
   DG_REQUIRE(o.krylov == 0 || o.krylov == 1, "krylov must be 0 (FGMRES) or 1 (flexible CG)");
   DG_REQUIRE(!dom->mapped || o.krylov == 0, "flexible CG needs a symmetric operator; curved elements are not");
   DG_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  {
+    const char* e = std::getenv("DG_TEST_BARRIER_STALL");
+    dom->barrier_stall = (e && std::strcmp(e, "1") == 0) ? 1 : 0;
+  }
   ensure_workspace(dom, std::min(max_it, 16));
   dg_solve_report R{};
   if (dom->desc.problem == DG_PROBLEM_POISSON) {
-    const double bn = o.relative_to_b ? norm2(dom, b, s) : 0.0;
     dom->lin_set = false;
-    LinearResult L = o.krylov == 1 ? fcg(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0)
-                                   : fgmres(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0);
+    LinearResult L;
+    if (o.krylov == 1 || !fgmres_graph(dom, b, u, tol, max_it, pmode, o.relative_to_b != 0, L)) {
+      const double bn = o.relative_to_b ? norm2(dom, b, s) : 0.0;
+      L = o.krylov == 1 ? fcg(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0)
+                        : fgmres(dom, b, u, tol, bn, max_it, pmode, o.relative_to_b != 0);
+    }
     R.iterations = L.iterations;
     R.initial_residual = L.r0;
     R.final_residual = L.final_res;
-    const double ref = o.relative_to_b ? bn : L.r0;
-    R.relative_residual = ref > 0 ? L.final_res / ref : 0.0;
+    R.relative_residual = L.ref > 0 ? L.final_res / L.ref : 0.0;
     R.status = L.status;
   } else {
     // Newton-Raphson with line search (sufficient decrease c = 1e-4, quadratic backtracking)
@@ -821,8 +1241,10 @@ dg_status solve(dg_domain* dom, const double* b, double* u, double tol, const dg
       DG_CUDA(cudaMemsetAsync(dom->du.get(), 0, sizeof(double) * n, s));
       // the linear right-hand side is r (copied: the Krylov solver overwrites dom->r)
       DG_CUDA(cudaMemcpyAsync(dom->ut.get(), r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      LinearResult L = o.krylov == 1 ? fcg(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false)
-                                     : fgmres(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false);
+      LinearResult L;
+      if (o.krylov == 1 || !fgmres_graph(dom, dom->ut.get(), dom->du.get(), lin_tol, max_it, pmode, false, L))
+        L = o.krylov == 1 ? fcg(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false)
+                          : fgmres(dom, dom->ut.get(), dom->du.get(), lin_tol, 0.0, max_it, pmode, false);
       R.iterations += L.iterations;
       if (L.status == DG_ERR_BREAKDOWN || L.status == DG_ERR_CANCELLED) { R.status = L.status; break; }
       double lam = 1.0, rn_new = 0.0;

@@ -2,10 +2,11 @@
 //
 // du_S = A_S^-1 r_S for all subdomains of a class (Sec. III.E, explicit-inverse solver) is the one
 // dense contraction of the method: Y[:, cols] = Inv_c (ld x ld, row-major) * X[:, cols] with every
-// subdomain column of X contiguous. Both operands are K-major, so each CTA computes a 128 x 64
-// output tile: TMA streams 128 x 32 tiles of Inv_c and 64 x 32 tiles of X (128-byte swizzle) into a
-// 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = 64, K = 8 per
-// instruction) accumulating in tensor memory, and the four warps read the accumulator back with
+// subdomain column of X contiguous. Both operands are K-major, so each CTA computes a 128 x BN
+// output tile (BN = 64, or 256 so that a class of at most 256 subdomains reads each 128-row slab of
+// its inverse once): TMA streams 128 x 32 tiles of Inv_c and BN x 32 tiles of X (128-byte swizzle)
+// into a 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = BN, K = 8
+// per instruction) accumulating in tensor memory, and the four warps read the accumulator back with
 // tcgen05.ld and store it column-contiguously. When the tiles alone cannot fill the GPU, the K
 // range is split across a cluster of 2, 4 or 8 CTAs and the partial tiles are summed through
 // distributed shared memory in a fixed order. Every wait is bounded: on timeout the CTA raises an
@@ -23,18 +24,27 @@ namespace dg {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32, STAGES = 4;
+constexpr int BM = 128, BK = 32, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
-constexpr int B_BYTES = BN * BK * 4;  // 8 KiB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 128;  // >= BN: the accumulator uses BN columns
-constexpr int SLACK = 8 * 1024;  // spare shared memory after the ring
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 256;
+constexpr int SLACK = 8 * 1024;       // spare shared memory after the ring
 constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls before a wait gives up (far above any real wait)
-constexpr int kSlots = 2 * 152;             // co-resident CTAs: two per SM
 
-// instruction descriptor: F32 accumulate, TF32 A and B, both K-major, N = BN, M = BM
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Shape constants of the tile width BN (64 or 256).
+template <int BN>
+struct TcShape {
+  static constexpr int B_BYTES = BN * BK * 4;  // 8 or 32 KiB
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int TMEM_COLS = BN < 128 ? 128 : BN;  // >= BN, a power of two
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 256;
+  static constexpr int PER_SM = BN <= 64 ? 2 : 1;      // co-resident CTAs per SM
+  static constexpr int SLOTS = PER_SM * 152;
+  // instruction descriptor: F32 accumulate, TF32 A and B, both K-major, N = BN, M = BM
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05.mma with M = 128 takes N = 16..256");
+  static_assert(BM * BN * 4 <= STAGES * STAGE_BYTES, "split-K partial tile must fit in the idle ring");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -95,12 +105,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred P1;\n\t"
       "setp.ne.b32 P1, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, P1;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -144,14 +154,16 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
 }
 
 // SPLIT > 1: the K range of a tile is split across the SPLIT CTAs of a thread-block cluster; each
-// keeps its partial 128 x 64 tile in shared memory and, after a cluster barrier, every CTA sums a
+// keeps its partial 128 x BN tile in shared memory and, after a cluster barrier, every CTA sums a
 // 1/SPLIT of the tile's columns over all partials through distributed shared memory in
 // rank order, so the result does not depend on timing.
-template <int SPLIT>
-__global__ void __launch_bounds__(128, 2)
+template <int SPLIT, int BN>
+__global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    float* __restrict__ Y, int ld, const int4* __restrict__ tiles, int* __restrict__ err,
                    float alpha) {
+  using SH = TcShape<BN>;
+  constexpr int B_BYTES = SH::B_BYTES, STAGE_BYTES = SH::STAGE_BYTES, TMEM_COLS = SH::TMEM_COLS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(128, 2)
       const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
       for (int kk = 0; kk < BK / 8; ++kk)
-        mma_tf32(tmem, smem_desc(a0 + 32 * kk), smem_desc(b0 + 32 * kk), (kc | kk) != 0);
+        mma_tf32(tmem, smem_desc(a0 + 32 * kk), smem_desc(b0 + 32 * kk), SH::IDESC, (kc | kk) != 0);
       mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
       *s_consumed = kc + 1;
     }
@@ -325,10 +337,29 @@ std::vector<int> tc_gemm_splits(int ld) {
   return out;
 }
 
-void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split) {
-  if (n_tiles == 0) return;
-  DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
+namespace {
+
+template <int BN>
+void set_smem_attributes() {
+  // kernel attributes are per device
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(dev)) return;
+  constexpr int S = TcShape<BN>::SMEM_BYTES;
+  DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S));
+  DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<2, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S));
+  DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<4, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S));
+  DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<8, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S));
+  done.insert(dev);
+}
+
+template <int BN>
+void launch_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols, const int4* d_tiles,
+               int n_tiles, int* err, float alpha, cudaStream_t s, int split) {
+  using SH = TcShape<BN>;
   const cuuint64_t dA[3] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)n_classes};
   const cuuint64_t sAr[2] = {(cuuint64_t)ld * 4, (cuuint64_t)ld * ld * 4};
   const cuuint32_t bA[3] = {BK, BM, 1};
@@ -337,35 +368,20 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
   const cuuint32_t bB[2] = {BK, BN};
   const CUtensorMap mA = make_map(inv, 3, dA, sAr, bA);
   const CUtensorMap mB = make_map(X, 2, dB, sBr, bB);
-  {
-    // kernel attributes are per device
-    static std::mutex mu;
-    static std::set<int> done;
-    int dev = 0;
-    DG_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    if (!done.count(dev)) {
-      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-      DG_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-      done.insert(dev);
-    }
-  }
-  // Default: split K over a cluster of `split` CTAs so that the launch fills one wave of two CTAs
-  // per SM (the ring and the partial tile fit twice in an SM's shared memory), keeping >= 4 K
-  // chunks each.
+  set_smem_attributes<BN>();
+  // Default: split K over a cluster of `split` CTAs so that the launch fills one wave of the
+  // co-resident CTAs, keeping >= 4 K chunks each.
   const int nk = ld / BK;
   if (split == 0) {
     split = 1;
-    while (split < 8 && n_tiles * split * 2 <= kSlots && nk / (split * 2) >= 4) split *= 2;
+    while (split < 8 && n_tiles * split * 2 <= SH::SLOTS && nk / (split * 2) >= 4) split *= 2;
   }
   DG_REQUIRE(split == 1 || split == 2 || split == 4 || split == 8, "GEMM split must be 1, 2, 4 or 8");
   DG_REQUIRE(split == 1 || nk / split >= 1, "GEMM split larger than the K chunks");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_tiles * split);
   cfg.blockDim = dim3(128);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.dynamicSmemBytes = SH::SMEM_BYTES;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -377,14 +393,22 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
   const bool pdl = pdl_enabled();
   cfg.attrs = pdl ? at : at + 1;
   cfg.numAttrs = (pdl ? 1 : 0) + (split == 1 ? 0 : 1);
-  if (split == 1) {
-    DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1>, mA, mB, Y, ld, d_tiles, err, alpha));
-  } else {
-    if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<2>, mA, mB, Y, ld, d_tiles, err, alpha));
-    else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4>, mA, mB, Y, ld, d_tiles, err, alpha));
-    else DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8>, mA, mB, Y, ld, d_tiles, err, alpha));
-  }
+  if (split == 1) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
+  else if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<2, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
+  else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
+  else DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
   DG_LAUNCHED(1);
+}
+
+}  // namespace
+
+void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
+                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split, int bn) {
+  if (n_tiles == 0) return;
+  DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
+  DG_REQUIRE(bn == 64 || bn == 256, "tensor-core GEMM tile width must be 64 or 256");
+  if (bn == 256) launch_tc<256>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, err, alpha, s, split);
+  else launch_tc<64>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, err, alpha, s, split);
 }
 
 }  // namespace dg
