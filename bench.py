@@ -262,13 +262,13 @@ def served_run(dgg, workloads, duration, rate=200.0, seed=5, max_active=8, preci
             "precision": "mixed (TF32 subdomain GEMM, FP64 FGMRES)" if precision == "mixed" else "fp64"}
 
 
-def served_compare(dgg, workloads, duration, prefix):
+def served_compare(dgg, workloads, duration, prefix, streams=8):
     """The served stream in MIXED precision, and the first `prefix` seconds of arrivals in both
     precisions (the plain FP64 solver on the same requests, for the mixed/FP64 throughput ratio)."""
-    out = served_run(dgg, workloads, duration)
+    out = served_run(dgg, workloads, duration, max_active=streams)
     if prefix > 0:
-        m = served_run(dgg, workloads, prefix)
-        f = served_run(dgg, workloads, prefix, precision="fp64")
+        m = served_run(dgg, workloads, prefix, max_active=streams)
+        f = served_run(dgg, workloads, prefix, precision="fp64", max_active=streams)
         out["prefix"] = {"window_s": prefix, "mixed": m, "fp64": f,
                          "mixed_over_fp64_solves_per_s": m["solves_per_s"] / f["solves_per_s"]}
     return out
@@ -748,7 +748,7 @@ def run_ours(args):
                   "GB/s": round(v["bytes"] / max(v["ms"], 1e-12) / 1e6, 1)} for k, v in prof.items()}
 
     concurrent = concurrent_run(dgg, workloads, torch, args.concurrent) if args.concurrent > 0 and rank == 0 else None
-    served = (served_compare(dgg, workloads, args.served_seconds, args.served_fp64_seconds)
+    served = (served_compare(dgg, workloads, args.served_seconds, args.served_fp64_seconds, args.served_streams)
               if args.served_seconds > 0 and rank == 0 else None)
     batched = (batched_compare(dgg, workloads, torch, args.batched, args.batched_fp64)
                if args.batched > 0 and rank == 0 else None)
@@ -859,6 +859,8 @@ def main():
                     help="problem of the oracle sample (--impl reference): the headline 8^3 Gaussian workload, "
                          "or the small 2^3 sine problem (quick CPU checks of this script)")
     ap.add_argument("--served-seconds", type=float, default=20.0, help="arrival window of the served stream (0: skip)")
+    ap.add_argument("--served-streams", type=int, default=8,
+                    help="solves the server runs at once (one worker thread and CUDA stream each)")
     ap.add_argument("--served-fp64-seconds", type=float, default=0.25,
                     help="arrival window replayed in both precisions for the mixed/FP64 ratio (0: skip)")
     ap.add_argument("--batched", type=int, default=512, help="also run this many batched uneven solves (0: skip)")

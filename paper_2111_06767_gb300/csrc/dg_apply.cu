@@ -613,6 +613,448 @@ __global__ void __launch_bounds__(kSliceEPB * 4, 4) apply_slice4_kernel(const Ap
   }
 }
 
+// ------------------------------------------------------------------ block-of-lines apply (FP32)
+//
+// Shared memory serves one word per lane and cycle, so a contraction whose inputs come from other
+// threads is bound by the LSU pipe unless every word a thread loads feeds several of its own
+// outputs. Here a thread owns B consecutive x-lines: in the first phase B lines along y in one z
+// plane k (x-contractions in registers, each y-neighbour row loaded once for B outputs), in the
+// second phase B lines along z in one y row j (each z-neighbour row loaded once for B outputs).
+// The element, v_y then v_z, and the first phase's partial result pass through shared memory. The
+// threads of one block index form warp-uniform groups, so the Dhat rows a thread uses are
+// compile-time constants (constant-memory operands). With B = N (one block) a thread holds a whole
+// plane and that phase's contraction stays in registers. Neighbour data for the face terms is read
+// by the threads that own the face: the x-neighbours' lines of every own line, the y- (z-)
+// neighbour's plane (row) of a face the block touches, streamed row by row.
+template <int N, int B, int EPB>
+struct BlkShape {
+  static constexpr int NB = (N + B - 1) / B;  // blocks along the blocked direction
+  static constexpr int VW = LineVec<N, float>::per;
+  // strides in words: an odd number of vectors, so that the lanes of one vector phase (consecutive
+  // planes in the first phase, consecutive rows in the second) hit distinct banks
+  static constexpr int LS = ((N / VW) % 2 == 1) ? N : N + VW;
+  static constexpr int PS = (((N * LS) / VW) % 2 == 1) ? N * LS : N * LS + VW;
+  static constexpr int ES = N * PS;
+  static constexpr int GP = (EPB * N + 31) / 32 * 32;  // threads per group, whole warps
+  static constexpr int THREADS = NB * GP;
+  static constexpr int SMEM = 3 * EPB * ES * (int)sizeof(float);
+};
+
+struct BlkElem {
+  int64_t base;  // element offset in the vectors (ec N^3)
+  int nb[6];     // neighbour element across each face (ec itself where there is none)
+  bool has[6];
+};
+
+__device__ __forceinline__ BlkElem blk_elem(const OpGeom<float>& g, int ec, int n3) {
+  BlkElem c;
+  const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
+  const int cx = ec % nx, cy = (ec / nx) % ny, cz = ec / nxy;
+  c.has[0] = cx > 0;
+  c.has[1] = cx + 1 < nx;
+  c.has[2] = cy > 0;
+  c.has[3] = cy + 1 < ny;
+  c.has[4] = cz > 0;
+  c.has[5] = cz + 1 < g.nz;
+  const int step[3] = {1, nx, nxy};
+#pragma unroll
+  for (int f = 0; f < 6; ++f) c.nb[f] = c.has[f] ? ec + ((f & 1) ? step[f >> 1] : -step[f >> 1]) : ec;
+  c.base = (int64_t)ec * n3;
+  return c;
+}
+
+// First phase for the group of block jb (warp-uniform): lines j = jb B + jj of plane k. Leaves A u's
+// x and y terms (volume and face) of the own lines in the partial-result buffer (the x part goes
+// there first, so that it does not hold registers through the y contractions). The Dhat rows of
+// the block are read from constant memory with a warp-uniform index.
+template <int N, int B, int EPB>
+__device__ __forceinline__ void blk_phase_y(const ApplyArgs<float>& A, const BlkElem& c, int jb, int k, bool act,
+                                            float* us, float* vs, float* ps) {
+  using S = BlkShape<N, B, EPB>;
+  using C = CTab<float>;
+  constexpr int N2 = N * N, dO = dtab_off(N), wO = wtab_off(N);
+  constexpr int NJ = B;  // lines past N (a ragged last block) are computed on zeros and never stored
+  constexpr bool ragged = S::NB * B != N;
+  const int J0 = jb * B;
+  auto ok = [&](int jj) { return !ragged || J0 + jj < N; };
+  const OpGeom<float>& g = A.g;
+  const float* __restrict__ u = A.u;
+  const float wk = C::w(wO + k);  // k is a runtime index: one constant-cache read per thread
+  float U[NJ][N];
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) {
+    if (ok(jj)) {
+      gld_line<N>(u + c.base + k * N2 + (J0 + jj) * N, U[jj]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) U[jj][i] = 0.f;
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj)
+      if (ok(jj)) sst_line<N>(us + k * S::PS + (J0 + jj) * S::LS, U[jj]);
+  }
+  // x: neighbour traces, gradient, lifting, face fluxes and divergence in registers, line by line;
+  // the result goes to the partial-result buffer
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) {
+    if (!ok(jj)) continue;
+    float t[N];
+    gld_line<N>(u + (int64_t)c.nb[0] * N2 * N + k * N2 + (J0 + jj) * N, t);
+    const float uxm = t[N - 1];
+    float gxm = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) gxm += C::D(dO + (N - 1) * N + l) * t[l];
+    gld_line<N>(u + (int64_t)c.nb[1] * N2 * N + k * N2 + (J0 + jj) * N, t);
+    const float uxp = t[0];
+    float gxp = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) gxp += C::D(dO + l) * t[l];
+    float vx[N], o[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a += C::D(dO + i * N + l) * U[jj][l];
+      vx[i] = g.dxi[0] * a;
+      o[i] = 0.f;
+    }
+    const float wj = C::w(wO + J0 + jj);
+    const float Bf = g.Jf[0] * wj * wk, sml = g.sigma[0] - g.lift[0];
+    vx[0] = face_point(-1.f, U[jj][0], vx[0], uxm, g.dxi[0] * gxm, c.has[0], g.neumann & 1, g.lift[0], sml, Bf, o[0]);
+    vx[N - 1] = face_point(1.f, U[jj][N - 1], vx[N - 1], uxp, g.dxi[0] * gxp, c.has[1], (g.neumann >> 1) & 1,
+                           g.lift[0], sml, Bf, o[N - 1]);
+    const float M0 = g.J * wj * wk;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a += C::D(dO + i * N + l) * vx[l];
+      o[i] -= (M0 * C::w(wO + i)) * g.dxi[0] * a;
+    }
+    if (act) sst_line<N>(ps + k * S::PS + (J0 + jj) * S::LS, o);
+  }
+  __syncthreads();  // the element is in shared memory
+  // y gradient: each row of the plane (own rows from registers) feeds the NJ own outputs
+  float vy[NJ][N];
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+    for (int i = 0; i < N; ++i) vy[jj][i] = 0.f;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    float t[N];
+    if constexpr (S::NB == 1) {  // one block: the thread holds the whole plane
+#pragma unroll
+      for (int i = 0; i < N; ++i) t[i] = U[l < NJ ? l : 0][i];
+    } else {
+      sld_line<N>(us + k * S::PS + l * S::LS, t);
+    }
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      const float d = ok(jj) ? C::D(dO + (J0 + jj) * N + l) : 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) vy[jj][i] += d * t[i];
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+    for (int i = 0; i < N; ++i) vy[jj][i] *= g.dxi[1];
+  // y faces this block touches: neighbour traces (rows of the neighbour's plane k), lifting into
+  // v_y, face fluxes into fy
+  float fy[2][N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) fy[0][i] = fy[1][i] = 0.f;
+  {
+    const float sml = g.sigma[1] - g.lift[1];
+    if (J0 == 0) {
+      float uym[N], gym[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) gym[i] = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        float t[N];
+        gld_line<N>(u + (int64_t)c.nb[2] * N2 * N + k * N2 + l * N, t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          gym[i] += C::D(dO + (N - 1) * N + l) * t[i];
+          if (l == N - 1) uym[i] = t[i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        vy[0][i] = face_point(-1.f, U[0][i], vy[0][i], uym[i], g.dxi[1] * gym[i], c.has[2], (g.neumann >> 2) & 1,
+                              g.lift[1], sml, g.Jf[1] * C::w(wO + i) * wk, fy[0][i]);
+    }
+    if (J0 + NJ >= N) {  // the block holding the row j = N - 1 (at jj = N - 1 - J0)
+      float uyp[N], gyp[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) gyp[i] = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        float t[N];
+        gld_line<N>(u + (int64_t)c.nb[3] * N2 * N + k * N2 + l * N, t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          gyp[i] += C::D(dO + l) * t[i];
+          if (l == 0) uyp[i] = t[i];
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        if (J0 + jj != N - 1) continue;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          vy[jj][i] = face_point(1.f, U[jj][i], vy[jj][i], uyp[i], g.dxi[1] * gyp[i], c.has[3], (g.neumann >> 3) & 1,
+                                 g.lift[1], sml, g.Jf[1] * C::w(wO + i) * wk, fy[1][i]);
+      }
+    }
+  }
+  // y divergence (other blocks' v_y through shared memory)
+  if constexpr (S::NB > 1) {
+    if (act) {
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj)
+        if (ok(jj)) sst_line<N>(vs + k * S::PS + (J0 + jj) * S::LS, vy[jj]);
+    }
+    __syncthreads();
+  }
+  float dy[NJ][N];
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+    for (int i = 0; i < N; ++i) dy[jj][i] = 0.f;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    float t[N];
+    if constexpr (S::NB == 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) t[i] = vy[l < NJ ? l : 0][i];
+    } else {
+      sld_line<N>(vs + k * S::PS + l * S::LS, t);
+    }
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      const float d = ok(jj) ? C::D(dO + (J0 + jj) * N + l) : 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) dy[jj][i] += d * t[i];
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      if (!ok(jj)) continue;
+      const float M0 = g.J * C::w(wO + J0 + jj) * wk;
+      float r[N];
+      sld_line<N>(ps + k * S::PS + (J0 + jj) * S::LS, r);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        r[i] -= (M0 * C::w(wO + i)) * g.dxi[1] * dy[jj][i];
+        if (J0 + jj == 0) r[i] += fy[0][i];
+        if (J0 + jj == N - 1) r[i] += fy[1][i];
+      }
+      sst_line<N>(ps + k * S::PS + (J0 + jj) * S::LS, r);
+    }
+  }
+}
+
+// Second phase for the group of block kb (warp-uniform): lines (j, k = kb B + kk). Adds the z terms
+// to the partial result and writes A u (b - A u, + diag u) for the own lines.
+template <int N, int B, int EPB>
+__device__ __forceinline__ void blk_phase_z(const ApplyArgs<float>& A, const BlkElem& c, int kb, int j, bool act,
+                                            bool store, const float* us, float* vs, const float* ps) {
+  using S = BlkShape<N, B, EPB>;
+  using C = CTab<float>;
+  constexpr int N2 = N * N, dO = dtab_off(N), wO = wtab_off(N);
+  constexpr int NK = B;
+  constexpr bool ragged = S::NB * B != N;
+  const int K0 = kb * B;
+  auto ok = [&](int kk) { return !ragged || K0 + kk < N; };
+  const OpGeom<float>& g = A.g;
+  const float* __restrict__ u = A.u;
+  const float wj = C::w(wO + j);
+  // z gradient: each row u(., j, l) of the element feeds the NK own outputs
+  float vz[NK][N];
+#pragma unroll
+  for (int kk = 0; kk < NK; ++kk)
+#pragma unroll
+    for (int i = 0; i < N; ++i) vz[kk][i] = 0.f;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    float t[N];
+    sld_line<N>(us + l * S::PS + j * S::LS, t);
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) {
+      const float d = ok(kk) ? C::D(dO + (K0 + kk) * N + l) : 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) vz[kk][i] += d * t[i];
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < NK; ++kk)
+#pragma unroll
+    for (int i = 0; i < N; ++i) vz[kk][i] *= g.dxi[2];
+  // z faces this block touches: lifting into v_z, face fluxes into fz
+  float fz[2][N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) fz[0][i] = fz[1][i] = 0.f;
+  {
+    const float sml = g.sigma[2] - g.lift[2];
+    if (K0 == 0) {
+      float uzm[N], gzm[N], ui[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) gzm[i] = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        float t[N];
+        gld_line<N>(u + (int64_t)c.nb[4] * N2 * N + l * N2 + j * N, t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          gzm[i] += C::D(dO + (N - 1) * N + l) * t[i];
+          if (l == N - 1) uzm[i] = t[i];
+        }
+      }
+      sld_line<N>(us + j * S::LS, ui);
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        vz[0][i] = face_point(-1.f, ui[i], vz[0][i], uzm[i], g.dxi[2] * gzm[i], c.has[4], (g.neumann >> 4) & 1,
+                              g.lift[2], sml, g.Jf[2] * C::w(wO + i) * wj, fz[0][i]);
+    }
+    if (K0 + NK >= N) {  // the block holding the plane k = N - 1 (at kk = N - 1 - K0)
+      float uzp[N], gzp[N], ui[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) gzp[i] = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        float t[N];
+        gld_line<N>(u + (int64_t)c.nb[5] * N2 * N + l * N2 + j * N, t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          gzp[i] += C::D(dO + l) * t[i];
+          if (l == 0) uzp[i] = t[i];
+        }
+      }
+      sld_line<N>(us + (N - 1) * S::PS + j * S::LS, ui);
+#pragma unroll
+      for (int kk = 0; kk < NK; ++kk) {
+        if (K0 + kk != N - 1) continue;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          vz[kk][i] = face_point(1.f, ui[i], vz[kk][i], uzp[i], g.dxi[2] * gzp[i], c.has[5], (g.neumann >> 5) & 1,
+                                 g.lift[2], sml, g.Jf[2] * C::w(wO + i) * wj, fz[1][i]);
+      }
+    }
+  }
+  // z divergence (other blocks' v_z through shared memory; the first-phase reads of v_y ended
+  // before the barrier between the phases)
+  if constexpr (S::NB > 1) {
+    if (act) {
+#pragma unroll
+      for (int kk = 0; kk < NK; ++kk)
+        if (ok(kk)) sst_line<N>(vs + (K0 + kk) * S::PS + j * S::LS, vz[kk]);
+    }
+    __syncthreads();
+  }
+  float dz[NK][N];
+#pragma unroll
+  for (int kk = 0; kk < NK; ++kk)
+#pragma unroll
+    for (int i = 0; i < N; ++i) dz[kk][i] = 0.f;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    float t[N];
+    if constexpr (S::NB == 1) {  // one block: the thread holds the whole row of planes
+#pragma unroll
+      for (int i = 0; i < N; ++i) t[i] = vz[l < NK ? l : 0][i];
+    } else {
+      sld_line<N>(vs + l * S::PS + j * S::LS, t);
+    }
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) {
+      const float d = ok(kk) ? C::D(dO + (K0 + kk) * N + l) : 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) dz[kk][i] += d * t[i];
+    }
+  }
+  if (!store) return;
+#pragma unroll
+  for (int kk = 0; kk < NK; ++kk) {
+    if (!ok(kk)) continue;
+    const int k = K0 + kk;
+    const int64_t off = c.base + k * N2 + j * N;
+    const float M0 = g.J * wj * C::w(wO + k);
+    float pr[N], dl[N], bl[N], ul[N], val[N];
+    sld_line<N>(ps + k * S::PS + j * S::LS, pr);
+    if (A.diag) {
+      gld_line<N>(A.diag + off, dl);
+      sld_line<N>(us + k * S::PS + j * S::LS, ul);
+    }
+    if (A.b) gld_line<N>(A.b + off, bl);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float r = pr[i] - (M0 * C::w(wO + i)) * g.dxi[2] * dz[kk][i];
+      if (k == 0) r += fz[0][i];
+      if (k == N - 1) r += fz[1][i];
+      if (A.diag) r += dl[i] * ul[i];
+      val[i] = A.b ? bl[i] - r : r;
+    }
+    gst_line<N>(A.out + off, val);
+  }
+}
+
+template <int N, int B, int EPB>
+__global__ void __launch_bounds__(BlkShape<N, B, EPB>::THREADS) apply_blk_kernel(const ApplyArgs<float> A) {
+  using S = BlkShape<N, B, EPB>;
+  constexpr int N3 = N * N * N;
+  extern __shared__ __align__(16) float blk_smem[];
+  pdl_launch_dependents();
+  pdl_wait();
+  const int tid = threadIdx.x;
+  const int grp = tid / S::GP, r = tid - grp * S::GP;
+  const bool act = r < EPB * N;  // lanes past the last element of the group only take part in barriers
+  const int el = act ? r / N : 0, q = act ? r - (r / N) * N : 0;
+  const int e = blockIdx.x * EPB + el;
+  const int ec = e < A.E ? e : A.E - 1;  // past the end: compute on a real element, store nothing
+  const BlkElem c = blk_elem(A.g, ec, N3);
+  float* us = blk_smem + el * S::ES;
+  float* vs = blk_smem + (EPB + el) * S::ES;
+  float* ps = blk_smem + (2 * EPB + el) * S::ES;
+  blk_phase_y<N, B, EPB>(A, c, grp, q, act, us, vs, ps);
+  __syncthreads();  // the partial results are in shared memory
+  const bool store = act && e < A.E;
+  blk_phase_z<N, B, EPB>(A, c, grp, q, act, store, us, vs, ps);
+}
+
+// Launch shapes of the block kernel per N: (B, EPB) for variants 5 and 6.
+template <int N>
+struct BlkConfig;
+template <> struct BlkConfig<4> { static constexpr int B5 = 4, E5 = 16, B6 = 4, E6 = 8; };
+template <> struct BlkConfig<5> { static constexpr int B5 = 5, E5 = 12, B6 = 5, E6 = 6; };
+template <> struct BlkConfig<6> { static constexpr int B5 = 6, E5 = 10, B6 = 3, E6 = 5; };
+template <> struct BlkConfig<7> { static constexpr int B5 = 7, E5 = 8, B6 = 4, E6 = 4; };
+template <> struct BlkConfig<8> { static constexpr int B5 = 4, E5 = 4, B6 = 2, E6 = 4; };
+template <> struct BlkConfig<9> { static constexpr int B5 = 5, E5 = 3, B6 = 3, E6 = 3; };
+template <> struct BlkConfig<10> { static constexpr int B5 = 5, E5 = 3, B6 = 4, E6 = 3; };
+
+template <int N, int B, int EPB>
+void launch_blk(const ApplyArgs<float>& A, cudaStream_t s) {
+  using S = BlkShape<N, B, EPB>;
+  if constexpr (S::SMEM > 48 * 1024) {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
+      DG_CUDA(cudaFuncSetAttribute(apply_blk_kernel<N, B, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+      done.insert(dev);
+    }
+  }
+  launch_pdl(apply_blk_kernel<N, B, EPB>, dim3((A.E + EPB - 1) / EPB), dim3(S::THREADS), (size_t)S::SMEM, s, A);
+}
+
 template <int N, typename T, int EPB>
 void launch_apply_epb(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
                       const SubdomainOut& so, int E, cudaStream_t s) {
@@ -643,7 +1085,16 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
       return;
     }
   }
-  if (variant == 4) variant = 0;  // the plane kernel covers the plain N = 4 FP32 apply only
+  if constexpr (N >= 4 && std::is_same<T, float>::value) {
+    if ((variant == 5 || variant == 6) && !so.rS) {
+      const ApplyArgs<float> A{g, D, w, u, diag, b, out, E, nullptr, 0, 0, nullptr, nullptr, nullptr};
+      using BC = BlkConfig<N>;
+      if (variant == 5) launch_blk<N, BC::B5, BC::E5>(A, s);
+      else launch_blk<N, BC::B6, BC::E6>(A, s);
+      return;
+    }
+  }
+  if (variant >= 4) variant = 0;  // the slice and block kernels cover plain FP32 applies only
   if (variant == 0) variant = ((E + kBig - 1) / kBig >= 2 * 152) ? 3 : 1;
   if (variant == 1) launch_apply_epb<N, T, kSmall>(g, D, w, u, diag, b, out, so, E, s);
   else if (variant == 2) launch_apply_epb<N, T, kMid>(g, D, w, u, diag, b, out, so, E, s);

@@ -121,26 +121,29 @@ from gpu_util import box, rand
 out = {}
 cases = [((3, 2, 1), ()), ((5, 3, 4), ()), ((33, 2, 1), (1, 4)), ((7, 5, 3), (0, 2, 5)), ((1, 1, 1), ())]
 lower, upper = (-1.0, -0.5, 0.0), (1.0, 0.7, 2.5)
-for c, (n, neu) in enumerate(cases):
-    d = dgg.Domain(lower, upper, n, 4, mg_levels=1, overlap=1, neumann=neu)
-    u = rand(300 + c, (n[0] * n[1] * n[2], 4, 4, 4))
-    out[f"apply{c}"] = d.apply_f32(torch.from_numpy(u.ravel()).float().cuda()).double().cpu().numpy()
-d = dgg.Domain(n=(4, 4, 2), N=4, mg_levels=2, overlap=2, precision="mixed", gemm="simt")
-out["vcycle"] = d.vcycle(torch.from_numpy(rand(41, (32, 4, 4, 4)).ravel()).cuda()).cpu().numpy()
-dp = dgg.Domain((-20.0,) * 3, (20.0,) * 3, (4, 3, 2), 4, mg_levels=1, overlap=1, problem="puncture",
-                punctures=workloads.BINARY_PUNCTURES, precision="mixed")
-dp.set_linearization(torch.from_numpy(0.1 * rand(51, (24, 4, 4, 4)).ravel()).cuda())
-out["lin"] = dp.apply_f32(torch.from_numpy(rand(52, (24, 4, 4, 4)).ravel()).float().cuda()).double().cpu().numpy()
+for N in [int(x) for x in sys.argv[3].split(",")]:
+    for c, (n, neu) in enumerate(cases):
+        d = dgg.Domain(lower, upper, n, N, mg_levels=1, overlap=1, neumann=neu)
+        u = rand(300 + c, (n[0] * n[1] * n[2], N, N, N))
+        out[f"apply{N}_{c}"] = d.apply_f32(torch.from_numpy(u.ravel()).float().cuda()).double().cpu().numpy()
+    d = dgg.Domain(n=(4, 4, 2), N=N, mg_levels=2, overlap=2, precision="mixed", gemm="simt")
+    out[f"vcycle{N}"] = d.vcycle(torch.from_numpy(rand(41, (32, N, N, N)).ravel()).cuda()).cpu().numpy()
+    dp = dgg.Domain((-20.0,) * 3, (20.0,) * 3, (4, 3, 2), N, mg_levels=1, overlap=1, problem="puncture",
+                    punctures=workloads.BINARY_PUNCTURES, precision="mixed")
+    dp.set_linearization(torch.from_numpy(0.1 * rand(51, (24, N, N, N)).ravel()).cuda())
+    out[f"lin{N}"] = dp.apply_f32(torch.from_numpy(rand(52, (24, N, N, N)).ravel()).float().cuda()).double().cpu().numpy()
 np.savez(sys.argv[1], **out)
 """
 
 
-@pytest.mark.parametrize("variant", ["4", "1"])
-def test_plane_kernel_matches_oracle(tmp_path, variant):
-    """The plain FP32 apply at N = 4 in its plane-per-thread form (DG_APPLY_VARIANT=4; 1 = a line-kernel
-    shape for comparison), pinned for every apply of the process: operator against the oracle on
-    ragged element counts (33 elements: one CTA of 32 plus one), Neumann faces and a single element,
-    the V-cycle's residual (b - A u) and the linearized puncture operator (+ diag u)."""
+@pytest.mark.parametrize("variant,orders", [("4", (4,)), ("1", (4, 7)), ("5", (4, 5, 6, 7, 8, 9, 10)),
+                                            ("6", (4, 5, 6, 7, 8, 9, 10))])
+def test_pinned_fp32_apply_kernels_match_oracle(tmp_path, variant, orders):
+    """Each plain FP32 apply kernel pinned for every apply of the process (DG_APPLY_VARIANT: 4 the
+    slice-per-thread kernel at N = 4, 5 and 6 the two launch shapes of the block-of-lines kernel,
+    1 a line-kernel shape for comparison): the operator against the oracle on ragged element counts
+    (66 elements: no launch shape divides it), Neumann faces and a single element, the V-cycle's
+    residual (b - A u) and the linearized puncture operator (+ diag u), at every order offered."""
     import os
     import subprocess
     import sys
@@ -151,19 +154,20 @@ def test_plane_kernel_matches_oracle(tmp_path, variant):
     script = tmp_path / "plane.py"
     script.write_text(_PLANE_SCRIPT)
     f = tmp_path / "out.npz"
-    subprocess.run([sys.executable, str(script), str(f), root], env=dict(os.environ, DG_APPLY_VARIANT=variant),
-                   check=True, timeout=600)
+    subprocess.run([sys.executable, str(script), str(f), root, ",".join(str(N) for N in orders)],
+                   env=dict(os.environ, DG_APPLY_VARIANT=variant), check=True, timeout=900)
     got = np.load(f)
     cases = [((3, 2, 1), ()), ((5, 3, 4), ()), ((33, 2, 1), (1, 4)), ((7, 5, 3), (0, 2, 5)), ((1, 1, 1), ())]
     lower, upper = (-1.0, -0.5, 0.0), (1.0, 0.7, 2.5)
-    for c, (n, neu) in enumerate(cases):
-        grid = dg.BoxGrid(lower, upper, n, 4, 1.5, tuple(fc in neu for fc in range(6)))
-        u = rand(300 + c, (grid.n_elements, 4, 4, 4))
-        assert rel(got[f"apply{c}"], dg.apply(grid.graph(), u)) < 2e-5, (variant, n)
-    pr = solve.Problem(box((4, 4, 2), 4), mg_levels=2)
-    assert rel(got["vcycle"], pr.vcycle(rand(41, (32, 4, 4, 4)))) < 1e-4
-    gp = box((4, 3, 2), 4, lower=(-20.0,) * 3, upper=(20.0,) * 3)
-    pp = solve.PunctureProblem(gp, workloads.BINARY_PUNCTURES, mg_levels=1)
-    ul, v = 0.1 * rand(51, (24, 4, 4, 4)), rand(52, (24, 4, 4, 4))
-    ref = pp.apply(v) + pp.mass * puncture.source_deriv(ul, pp.alpha, pp.beta) * v
-    assert rel(got["lin"], ref) < 2e-5
+    for N in orders:
+        for c, (n, neu) in enumerate(cases):
+            grid = dg.BoxGrid(lower, upper, n, N, 1.5, tuple(fc in neu for fc in range(6)))
+            u = rand(300 + c, (grid.n_elements, N, N, N))
+            assert rel(got[f"apply{N}_{c}"], dg.apply(grid.graph(), u)) < 2e-5, (variant, N, n)
+        pr = solve.Problem(box((4, 4, 2), N), mg_levels=2)
+        assert rel(got[f"vcycle{N}"], pr.vcycle(rand(41, (32, N, N, N)))) < 1e-4, (variant, N)
+        gp = box((4, 3, 2), N, lower=(-20.0,) * 3, upper=(20.0,) * 3)
+        pp = solve.PunctureProblem(gp, workloads.BINARY_PUNCTURES, mg_levels=1)
+        ul, v = 0.1 * rand(51, (24, N, N, N)), rand(52, (24, N, N, N))
+        ref = pp.apply(v) + pp.mass * puncture.source_deriv(ul, pp.alpha, pp.beta) * v
+        assert rel(got[f"lin{N}"], ref) < 2e-5, (variant, N)
