@@ -32,6 +32,7 @@ WORKLOAD = ("poisson-gauss16-8x8x8-N8: 3-D Poisson on [-1,1]^3, 8^3 elements, N=
             "(262,144 DOF), 16 seeded Gaussians (widths U[0.1,0.4]), 3-level h-MG V-cycle, Schwarz overlap 2, "
             "3+3 smoothing, C=1.5, FGMRES to 1e-10 relative residual from u=0")
 N_CFG, n_CFG, LEVELS = 8, (8, 8, 8), 3
+FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate probed on this machine's GB300 (152 SMs)
 TOL = 1e-10
 
 # CPU baseline: the oracle (FP64 numpy) on the same 8^3, N = 8 problem, 3-level V-cycle. One solve
@@ -645,11 +646,14 @@ def run_ours(args):
            "relative_residual": max(r.relative_residual for r in repscg),
            "solution_rel_diff_vs_fgmres": float((u - u_mixed).norm() / u_mixed.norm())}
 
-    # ---- plain FP64 solver (same workload)
+    # ---- plain FP64 solver (same workload), with one profiled solve for its phases
     d64 = doms["fp64"]
     timed_solves(d64, 0, 1)
     t64, reps64, _ = timed_solves(d64, max(2, args.steps // 2), 0)
     value64 = len(t64) / (sum(t64) / 1e3)
+    _, _, prof64 = timed_solves(d64, 1, 0, profile=True)
+    g64 = prof64["subdomain_gemm"]
+    fp64_gemm_tflops = g64["flops"] / max(g64["ms"], 1e-12) / 1e9
     sol_diff = float((u_mixed - u).norm() / u.norm())
 
     # ---- end to end through the C ABI with host buffers (elliptic_solve_host): the call copies the
@@ -775,7 +779,11 @@ def run_ours(args):
         "iterations": reps[0].iterations, "relative_residual": max(r.relative_residual for r in reps),
         "fp64": {"value": value64, "unit": "solves/s", "iterations": reps64[0].iterations,
                  "relative_residual": max(r.relative_residual for r in reps64),
-                 "mixed_vs_fp64_solution_rel_diff": sol_diff, "mixed_speedup": value / value64 / world},
+                 "mixed_vs_fp64_solution_rel_diff": sol_diff, "mixed_speedup": value / value64 / world,
+                 "phases_ms": {k: round(v["ms"], 3) for k, v in prof64.items() if v["launches"]},
+                 "subdomain_gemm_tflops": fp64_gemm_tflops,
+                 "subdomain_gemm_frac_of_fp64_pipe": fp64_gemm_tflops / FP64_PEAK_TFLOPS,
+                 "fp64_peak": f"{FP64_PEAK_TFLOPS} TFLOP/s, FP64 FMA rate probed on this pool's GB300"},
         "fcg": fcg,
         "dg_apply": apply,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 2 * f.numel() * 8,

@@ -864,7 +864,8 @@ __device__ __forceinline__ void blk_phase_y(const ApplyArgs<float>& A, const Blk
 // to the partial result and writes A u (b - A u, + diag u) for the own lines.
 template <int N, int B, int EPB>
 __device__ __forceinline__ void blk_phase_z(const ApplyArgs<float>& A, const BlkElem& c, int kb, int j, bool act,
-                                            bool store, const float* us, float* vs, const float* ps) {
+                                            bool store, const float* us, float* vs, const float* ps,
+                                            const int* s_col, const int* s_map) {
   using S = BlkShape<N, B, EPB>;
   using C = CTab<float>;
   constexpr int N2 = N * N, dO = dtab_off(N), wO = wtab_off(N);
@@ -1000,7 +1001,36 @@ __device__ __forceinline__ void blk_phase_z(const ApplyArgs<float>& A, const Blk
       if (A.diag) r += dl[i] * ul[i];
       val[i] = A.b ? bl[i] - r : r;
     }
-    gst_line<N>(A.out + off, val);
+    if (!A.rS) {
+      gst_line<N>(A.out + off, val);
+      continue;
+    }
+    // written straight into the subdomain vectors: the element's own subdomain (slot 0) and, for
+    // points in a face neighbour's overlap layers, that neighbour's subdomain (slot 1 + (f ^ 1)); every
+    // subdomain row holds one point, so these stores never collide
+    const int t = k * N + j;
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) {
+      const int col = s_col[sl];
+      if (col < 0) continue;
+      int lo = 0, hi = N;
+      if (sl > 0) {
+        const int f = sl - 1, dd = f >> 1, side = f & 1;
+        if (dd == 0) {
+          if (side) lo = N - A.ov;
+          else hi = A.ov;
+        } else {
+          const int cc = dd == 1 ? j : k;
+          if ((side ? N - 1 - cc : cc) >= A.ov) continue;
+        }
+      }
+      int rows[N];
+      gld_line<N>(A.inv + s_map[sl] + t * N, rows);
+      float* colp = A.rS + (int64_t)col * A.ld;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i >= lo && i < hi && rows[i] >= 0) colp[rows[i]] = val[i];
+    }
   }
 }
 
@@ -1021,10 +1051,37 @@ __global__ void __launch_bounds__(BlkShape<N, B, EPB>::THREADS) apply_blk_kernel
   float* us = blk_smem + el * S::ES;
   float* vs = blk_smem + (EPB + el) * S::ES;
   float* ps = blk_smem + (2 * EPB + el) * S::ES;
+  // residual written into the subdomain vectors: column and point-map offset of each element's own
+  // subdomain (slot 0) and of each face neighbour's subdomain (slot 1 + (f ^ 1))
+  __shared__ int s_col[EPB][7], s_map[EPB][7];
+  if (A.rS) {
+    const int nx = A.g.nx, ny = A.g.ny, nxy = A.g.nx * A.g.ny;
+    for (int qq = tid; qq < EPB * 7; qq += S::THREADS) {
+      const int el2 = qq / 7, sl = qq - el2 * 7;
+      const int e2 = blockIdx.x * EPB + el2;
+      int col = -1, m = 0;
+      if (e2 < A.E) {
+        int rr = e2;
+        if (sl > 0) {
+          const int f = sl - 1, d = f >> 1;
+          int c3[3] = {e2 % nx, (e2 / nx) % ny, e2 / nxy};
+          const int nd = d == 0 ? nx : (d == 1 ? ny : A.g.nz);
+          c3[d] += (f & 1) ? 1 : -1;
+          rr = (c3[d] >= 0 && c3[d] < nd) ? c3[0] + nx * (c3[1] + ny * c3[2]) : -1;
+        }
+        if (rr >= 0) {
+          col = A.col_of_elem[rr];
+          m = (A.orient[rr] * 7 + (sl == 0 ? 0 : 1 + ((sl - 1) ^ 1))) * N3;
+        }
+      }
+      s_col[el2][sl] = col;
+      s_map[el2][sl] = m;
+    }
+  }
   blk_phase_y<N, B, EPB>(A, c, grp, q, act, us, vs, ps);
-  __syncthreads();  // the partial results are in shared memory
+  __syncthreads();  // the partial results (and the subdomain tables) are in shared memory
   const bool store = act && e < A.E;
-  blk_phase_z<N, B, EPB>(A, c, grp, q, act, store, us, vs, ps);
+  blk_phase_z<N, B, EPB>(A, c, grp, q, act, store, us, vs, ps, s_col[el], s_map[el]);
 }
 
 // Launch shapes of the block kernel per N: (B, EPB) for variants 5 and 6.
@@ -1086,15 +1143,16 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
     }
   }
   if constexpr (N >= 4 && std::is_same<T, float>::value) {
-    if ((variant == 5 || variant == 6) && !so.rS) {
-      const ApplyArgs<float> A{g, D, w, u, diag, b, out, E, nullptr, 0, 0, nullptr, nullptr, nullptr};
+    if (variant == 5 || variant == 6) {
+      const ApplyArgs<float> A{g, D, w, u, diag, b, out, E, static_cast<float*>(so.rS), so.ld, so.ov,
+                               so.col_of_elem, so.orient, so.inv};
       using BC = BlkConfig<N>;
       if (variant == 5) launch_blk<N, BC::B5, BC::E5>(A, s);
       else launch_blk<N, BC::B6, BC::E6>(A, s);
       return;
     }
   }
-  if (variant >= 4) variant = 0;  // the slice and block kernels cover plain FP32 applies only
+  if (variant >= 4) variant = 0;  // the slice kernel covers plain FP32 applies only, the block kernel FP32
   if (variant == 0) variant = ((E + kBig - 1) / kBig >= 2 * 152) ? 3 : 1;
   if (variant == 1) launch_apply_epb<N, T, kSmall>(g, D, w, u, diag, b, out, so, E, s);
   else if (variant == 2) launch_apply_epb<N, T, kMid>(g, D, w, u, diag, b, out, so, E, s);

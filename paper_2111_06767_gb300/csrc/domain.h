@@ -66,9 +66,10 @@ struct Level {
   LevelWork<double> w64;
   LevelWork<float> w32;
   // autotuned launch shapes (-1: not yet tuned): DG apply [FP64, FP32][plain, fused into r_S],
-  // tensor-core GEMM split
+  // tensor-core GEMM split and tile width, CUDA-core GEMM split [FP32, FP64]
   int apply_variant[2][2] = {{-1, -1}, {-1, -1}};
   int gemm_split = -1;
+  int simt_split[2] = {-1, -1};
 };
 
 // Event-based per-phase timing of launches (dg_profile_*).

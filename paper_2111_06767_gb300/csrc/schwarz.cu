@@ -430,33 +430,62 @@ template void launch_scatter_tab<float, float>(const SubdomainGeom&, const float
 // ------------------------------------------------------------------ class GEMM (SIMT)
 
 // Y[:, c0:c0+m] = Inv_c (nS x nS, row-major) * X[:, c0:c0+m] (columns of nS contiguous values).
-// 64 x 64 output tiles, K chunks of 16 staged in shared memory, 4 x 4 outputs per thread.
-template <typename T>
+// 64 x 64 output tiles, K chunks of 16 staged in shared memory, 4 x 4 outputs per thread. SPLIT > 1:
+// the K range of a tile is split over the SPLIT CTAs of a thread-block cluster (on GB300 a single
+// CTA of this FP64 product occupies an SM's FP64 pipe for a long time, so coarse levels with few
+// tiles would leave most SMs idle); each CTA keeps its partial tile in shared memory and, after a
+// cluster barrier, sums 1/SPLIT of the tile's rows over all partials through distributed shared
+// memory in rank order, so the result does not depend on timing.
+template <typename T, int SPLIT>
 __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ inv, const T* __restrict__ X,
                                                          T* __restrict__ Y, int nS, const int4* __restrict__ tiles,
                                                          T alpha) {
   constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ T sA[BK][BM + 1];
-  __shared__ T sB[BK][BN + 1];
-  const int4 tile = tiles[blockIdx.x];  // (class, row0, col0, ncols in this class from col0)
+  // the K chunks' staging, then (SPLIT > 1) the partial tile in the same memory
+  constexpr size_t kStage = 2 * BK * (BM + 1) * sizeof(T), kPart = SPLIT > 1 ? BM * (BN + 1) * sizeof(T) : 0;
+  __shared__ __align__(16) unsigned char raw[kStage > kPart ? kStage : kPart];
+  T(*sA)[BM + 1] = reinterpret_cast<T(*)[BM + 1]>(raw);
+  T(*sB)[BN + 1] = reinterpret_cast<T(*)[BN + 1]>(raw + BK * (BM + 1) * sizeof(T));
+  const int4 tile = tiles[blockIdx.x / SPLIT];  // (class, row0, col0, ncols in this class from col0)
   const int cls = tile.x, row0 = tile.y, col0 = tile.z, ncol = min(tile.w, BN);
   const T* A = inv + (size_t)cls * nS * nS;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  int rank = 0;
+  if constexpr (SPLIT > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  // K chunks [kc0, kc1) of this CTA
+  const int nk = (nS + BK - 1) / BK;
+  const int kc0 = rank * nk / SPLIT, kc1 = (rank + 1) * nk / SPLIT;
   T acc[4][4] = {};
   pdl_launch_dependents();
   pdl_wait();
-  for (int k0 = 0; k0 < nS; k0 += BK) {
-    for (int t = threadIdx.x; t < BM * BK; t += 256) {
+  // each thread stages 4 values of A and 4 of X per K chunk; the next chunk's values are loaded
+  // into registers while the current chunk is multiplied
+  constexpr int PER = BM * BK / 256;
+  static_assert(BM * BK % 256 == 0 && BN * BK % 256 == 0, "staging shape");
+  T pa[PER], pb[PER];
+  auto fetch = [&](int kc) {
+    const int k0 = kc * BK;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + 256 * q;
       const int r = t / BK, kk = t % BK;
       const int gr = row0 + r, gk = k0 + kk;
-      sA[kk][r] = (gr < nS && gk < nS) ? A[(size_t)gr * nS + gk] : T(0);
+      pa[q] = (gr < nS && gk < nS) ? A[(size_t)gr * nS + gk] : T(0);
+      const int c = r;  // BN == BM
+      pb[q] = (c < ncol && gk < nS) ? X[(size_t)(col0 + c) * nS + gk] : T(0);
     }
-    for (int t = threadIdx.x; t < BN * BK; t += 256) {
-      const int c = t / BK, kk = t % BK;
-      const int gk = k0 + kk;
-      sB[kk][c] = (c < ncol && gk < nS) ? X[(size_t)(col0 + c) * nS + gk] : T(0);
+  };
+  if (kc0 < kc1) fetch(kc0);
+  for (int kc = kc0; kc < kc1; ++kc) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int t = threadIdx.x + 256 * q;
+      const int r = t / BK, kk = t % BK;
+      sA[kk][r] = pa[q];
+      sB[kk][r] = pb[q];
     }
     __syncthreads();
+    if (kc + 1 < kc1) fetch(kc + 1);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[4], b[4];
@@ -469,23 +498,86 @@ __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ i
     }
     __syncthreads();
   }
+  if constexpr (SPLIT == 1) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int gr = row0 + ty + 16 * q;
-    if (gr >= nS) continue;
+    for (int q = 0; q < 4; ++q) {
+      const int gr = row0 + ty + 16 * q;
+      if (gr >= nS) continue;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int c = tx + 16 * r;
-      if (c < ncol) Y[(size_t)(col0 + c) * nS + gr] = alpha * acc[q][r];
+      for (int r = 0; r < 4; ++r) {
+        const int c = tx + 16 * r;
+        if (c < ncol) Y[(size_t)(col0 + c) * nS + gr] = alpha * acc[q][r];
+      }
     }
+  } else {
+    // partial tile [row][col] in this CTA's shared memory (the staging is free: the K loop ended
+    // with a barrier)
+    T(*part)[BN + 1] = reinterpret_cast<T(*)[BN + 1]>(raw);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) part[ty + 16 * q][tx + 16 * r] = acc[q][r];
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    // this CTA sums rows [rank BM / SPLIT, (rank + 1) BM / SPLIT) over the partials in rank order
+    constexpr int RPC = BM / SPLIT;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(&part[0][0]);
+    for (int t = threadIdx.x; t < RPC * BN; t += 256) {
+      const int rr = rank * RPC + t / BN, c = t % BN;
+      const uint32_t off = base + (uint32_t)((rr * (BN + 1) + c) * sizeof(T));
+      T sum = T(0);
+#pragma unroll
+      for (int p = 0; p < SPLIT; ++p) {
+        uint32_t remote;
+        asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(off), "r"(p));
+        T v;
+        if constexpr (sizeof(T) == 8) asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote));
+        else asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote));
+        sum += v;
+      }
+      const int gr = row0 + rr;
+      if (gr < nS && c < ncol) Y[(size_t)(col0 + c) * nS + gr] = alpha * sum;
+    }
+    // no CTA leaves while a peer still reads its partial tile
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   }
 }
 
+// K split of the CUDA-core class GEMM: 1, 2, 4 or 8 CTAs per tile (0: the smallest that gives at
+// least two CTAs per SM, keeping >= 8 K chunks per CTA).
 template <typename T>
 void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
-                             cudaStream_t s) {
+                             cudaStream_t s, int split) {
   if (n_tiles == 0) return;
-  launch_pdl(class_gemm_kernel<T>, dim3(n_tiles), dim3(256), 0, s, inv, X, Y, nS, d_tiles, alpha);
+  const int nk = (nS + 15) / 16;
+  if (split == 0) {
+    split = 1;
+    while (split < 8 && n_tiles * split < 2 * 152 && nk / (split * 2) >= 8) split *= 2;
+  }
+  DG_REQUIRE(split == 1 || split == 2 || split == 4 || split == 8, "class GEMM split must be 1, 2, 4 or 8");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_tiles * split);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (pdl_enabled()) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (split > 1) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = split;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  if (split == 1) DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 1>, inv, X, Y, nS, d_tiles, alpha));
+  else if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 2>, inv, X, Y, nS, d_tiles, alpha));
+  else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 4>, inv, X, Y, nS, d_tiles, alpha));
+  else DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 8>, inv, X, Y, nS, d_tiles, alpha));
   DG_LAUNCHED(1);
 }
 
@@ -646,8 +738,8 @@ template void launch_sub_lsq_combine<float>(int, int, int, const float*, const f
 
 
 template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int, double,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, float,
-                                             cudaStream_t);
+                                             cudaStream_t, int);
 
 }  // namespace dg

@@ -30,7 +30,7 @@ int apply_variant(dg_domain* dom, Level& L, bool fused, const std::function<void
     // launch shapes of the line kernel; the plane kernel for plain FP32 applies at N = 4
     std::vector<int> cand{0, 1, 2, 3};
     if (!fused && dom->N == 4 && sizeof(T) == 4) cand.push_back(4);
-    if (!fused && dom->N >= 4 && sizeof(T) == 4) {  // the block-of-lines kernel, two launch shapes
+    if (dom->N >= 4 && sizeof(T) == 4) {  // the block-of-lines kernel, two launch shapes
       cand.push_back(5);
       cand.push_back(6);
     }
@@ -182,7 +182,41 @@ const float* Ihi<float>(dg_domain* dom) { return dom->Ihi32.get(); }
 
 template <typename T>
 void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
-                             cudaStream_t s);
+                             cudaStream_t s, int split);
+
+namespace {
+// The CUDA-core class GEMM with its K split tuned per level and precision on first use (0, the
+// heuristic, then 1, 2, 4, 8); DG_GEMM_SPLIT pins it as for the tensor-core GEMM.
+template <typename T>
+void simt_class_gemm(Level& L, const T* inv, const T* X, T* Y, T alpha, cudaStream_t s) {
+  const SchwarzLevel& sw = L.sw;
+  int& pick = L.simt_split[sizeof(T) == 8];
+  auto run = [&](int split) {
+    launch_class_gemm_tiles<T>(inv, X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, alpha, s, split);
+  };
+  if (pick < 0) {
+    std::vector<int> cand{0};
+    const int nk = (sw.ld + 15) / 16;
+    for (int sp = 1; sp <= 8; sp *= 2)
+      if (nk / sp >= 4) cand.push_back(sp);
+    const char* e = std::getenv("DG_GEMM_SPLIT");
+    const int forced = e ? std::atoi(e) : -1;
+    if (forced >= 0 && std::find(cand.begin(), cand.end(), forced) != cand.end()) {
+      pick = forced;
+    } else {
+      const int p = autotune({4, (int64_t)sizeof(T), sw.n_classes, sw.ld, sw.n_tiles, L.E}, cand, run, s);
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      DG_CUDA(cudaStreamIsCapturing(s, &cap));
+      if (cap != cudaStreamCaptureStatusNone) {
+        run(p);
+        return;
+      }
+      pick = p;
+    }
+  }
+  run(pick);
+}
+}  // namespace
 
 namespace {
 // du_S = A_S^-1 r_S for every subdomain of every class
@@ -195,7 +229,7 @@ void class_gemm<double>(dg_domain* dom, Level& L, const double* X, double* Y, cu
     launch_lin_gemv<double>(sw.inv64.get(), X, sw.nS, sw.ld, L.E, Y, s);
     return;
   }
-  launch_class_gemm_tiles<double>(sw.inv64.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, sw.inv_scale, s);
+  simt_class_gemm<double>(L, sw.inv64.get(), X, Y, sw.inv_scale, s);
 }
 template <>
 void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaStream_t s) {
@@ -243,7 +277,7 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
     }
     run(L.gemm_split);
   } else
-    launch_class_gemm_tiles<float>(sw.inv32.get(), X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, (float)sw.inv_scale, s);
+    simt_class_gemm<float>(L, sw.inv32.get(), X, Y, (float)sw.inv_scale, s);
 }
 }  // namespace
 

@@ -99,3 +99,25 @@ def test_every_gemm_split_matches_simt(monkeypatch, n):
         d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=ov, precision="mixed", gemm="tf32")
         du_t = d.schwarz_smooth(0, b, u0.clone(), 1).cpu().numpy() - u0.cpu().numpy()
         assert rel(du_t, du_s) < 3e-3, split
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_cuda_core_gemm_split_matches_oracle(monkeypatch, precision):
+    """The CUDA-core class GEMM (FP64 domains, and MIXED with gemm="simt") with its K range split over
+    1, 2, 4 or 8 CTAs of a cluster (partial tiles summed in rank order through distributed shared
+    memory), pinned with DG_GEMM_SPLIT: one smoothing step equals the oracle's Schwarz step (FP64 to
+    1e-10, FP32 to 1e-4)."""
+    from oracle import schwarz
+
+    n, N, ov = (4, 4, 4), 6, 2
+    grid = box(n, N)
+    b = rand(85, (grid.n_elements, N, N, N))
+    u0 = rand(86, (grid.n_elements, N, N, N))
+    ref = schwarz.SchwarzLevel(grid, ov).smooth(b, u0, 1).ravel()
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    for split in (1, 2, 4, 8):
+        monkeypatch.setenv("DG_GEMM_SPLIT", str(split))
+        d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=ov, precision=precision, gemm="simt")
+        bt, ut = torch.from_numpy(b.ravel()).cuda(), torch.from_numpy(u0.ravel()).cuda()
+        got = d.schwarz_smooth(0, bt, ut, 1).cpu().numpy()
+        assert rel(got - u0.ravel(), ref - u0.ravel()) < tol, split
