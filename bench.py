@@ -33,6 +33,7 @@ WORKLOAD = ("poisson-gauss16-8x8x8-N8: 3-D Poisson on [-1,1]^3, 8^3 elements, N=
             "3+3 smoothing, C=1.5, FGMRES to 1e-10 relative residual from u=0")
 N_CFG, n_CFG, LEVELS = 8, (8, 8, 8), 3
 FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate probed on this machine's GB300 (152 SMs)
+FP32_PEAK_TFLOPS = 72.7   # FP32 FMA rate probed on this machine's GB300 (152 SMs at 1987 MHz)
 TOL = 1e-10
 
 # CPU baseline: the oracle (FP64 numpy) on the same 8^3, N = 8 problem, 3-level V-cycle. One solve
@@ -710,9 +711,15 @@ def run_ours(args):
         for Ns, ns in ((4, 96), (5, 77), (6, 64), (7, 55), (8, 48), (9, 43)):
             dm = dgg.Domain(n=(ns,) * 3, N=Ns, penalty=1.5, precision="mixed", mg_levels=1, overlap=1, stream=stream)
             r64, r32 = apply_rate(dm, "fp64", 3)[0], apply_rate(dm, "fp32", 5)[0]
-            sweep[f"N{Ns}_{ns}cubed"] = {"dof": dm.n_dof, "fp32_gdofs": r32, "fp32_hbm_frac": 8.0 * r32 / hbm,
-                                         "fp64_gdofs": r64, "fp64_hbm_frac": 16.0 * r64 / hbm,
-                                         "fp64_flop_rate_tflops": r64 * (12 * Ns + 12) / 1e3}
+            fl = 12 * Ns + 12  # flop per DOF of the sum-factorised operator
+            roof32 = min(hbm / 8.0, FP32_PEAK_TFLOPS * 1e3 / fl)  # GDOF/s: HBM (8 B/DOF) or the FP32 pipe
+            roof64 = min(hbm / 16.0, FP64_PEAK_TFLOPS * 1e3 / fl)
+            sweep[f"N{Ns}_{ns}cubed"] = {
+                "dof": dm.n_dof, "fp32_gdofs": r32, "fp32_hbm_frac": 8.0 * r32 / hbm,
+                "fp32_pipe_frac": r32 * fl / (FP32_PEAK_TFLOPS * 1e3),
+                "fp32_binding_roof": "hbm" if roof32 == hbm / 8.0 else "fp32 pipe", "fp32_roof_frac": r32 / roof32,
+                "fp64_gdofs": r64, "fp64_hbm_frac": 16.0 * r64 / hbm, "fp64_flop_rate_tflops": r64 * fl / 1e3,
+                "fp64_pipe_frac": r64 * fl / (FP64_PEAK_TFLOPS * 1e3), "fp64_roof_frac": r64 / roof64}
             dm.close()
         apply["sweep"] = sweep
 
