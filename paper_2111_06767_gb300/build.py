@@ -42,7 +42,7 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     path = os.path.join(CSRC, src)
     lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]
     cmd = [nvcc()] + lang + _flags(verbose_ptxas) + ["-c", path, "-o", obj]
-    deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(os.path.dirname(PKG), "include", "dg_elliptic.h"))
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj

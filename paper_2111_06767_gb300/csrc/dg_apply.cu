@@ -24,6 +24,9 @@
 // memory; the y- and z-contractions read whole lines from shared memory, which the threads of one
 // plane (y) or one column of planes (z) share as broadcasts, with the planes padded so that the
 // lines of one access fall into distinct banks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 #include <set>
@@ -613,6 +616,387 @@ __global__ void __launch_bounds__(kSliceEPB * 4, 4) apply_slice4_kernel(const Ap
   }
 }
 
+// ------------------------------------------------------------------ element-per-thread apply (N = 4, FP32)
+//
+// At N = 4 an element is 64 values, few enough for one thread to hold the element, one gradient
+// component and the result in registers, so the three contractions need no exchange between
+// threads at all. A CTA owns a brick of BX x BY x BZ elements. One TMA load stages the brick with a
+// one-element halo ((BX+2) x (BY+2) x (BZ+2) elements; elements outside the domain arrive as zeros
+// and are replaced by the ghost state) in shared memory, each element padded from 64 to 68 words:
+// the 16-byte reads of consecutive elements at one offset then fall into distinct banks. A thread
+// reads its element and its six face neighbours from there (a neighbour's normal derivative at the
+// shared face needs its whole element), works direction by direction (gradient component, face
+// lifting and fluxes, divergence), and the result leaves through the same padded layout with one
+// TMA store, which clips elements outside the domain. The flux of a face point enters the per-point
+// sum before the mass-matrix scaling, divided by that point's M: Bf / M = Jf_d / (J w_0) at every
+// face point of a face normal to d. Values are held as pairs of x-neighbouring points, so that the
+// contractions and most face terms run as packed two-wide FP32 FMAs (one instruction per pair):
+// the thread's 64-value working set leaves too few warps per SM to hide latency otherwise.
+constexpr int kE4Slot = 68;  // words per staged element
+
+template <int BX, int BY, int BZ>
+struct E4Shape {
+  static constexpr int PX = BX + 2, PY = BY + 2, PZ = BZ + 2;
+  static constexpr int THREADS = BX * BY * BZ;
+  static constexpr int IN_WORDS = PX * PY * PZ * kE4Slot;
+  static constexpr int SMEM = IN_WORDS * 4 + 16 + 128;  // staged box, mbarrier, alignment slack
+  static constexpr int PER_SM = (228 * 1024) / (SMEM + 1024) > 8 ? 8 : (228 * 1024) / (SMEM + 1024);
+  static_assert(PER_SM >= 1 && SMEM <= 227 * 1024, "staged brick must fit in shared memory");
+  static_assert(BX <= 254 && BY <= 254 && BZ <= 254, "TMA boxes are at most 256 elements per dimension");
+};
+
+constexpr uint32_t kE4WaitPolls = 1u << 20;  // polls before the staging wait gives up
+
+__device__ __forceinline__ uint32_t e4_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool e4_wait(uint32_t bar, int* err) {
+  for (uint32_t it = 0; it < kE4WaitPolls; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    if (ok) return true;
+  }
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void ld4p(const float* p, float2 (&r)[2]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  r[0] = make_float2(v.x, v.y);
+  r[1] = make_float2(v.z, v.w);
+}
+
+__device__ __forceinline__ void ld4s(const float* p, float (&r)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+
+// Lifting and flux of one face point, as face_point() above, with the flux added to the point's
+// pre-mass sum acc (cf = Bf / M of the point).
+__device__ __forceinline__ float e4_face(float s, float ui, float gi, float ue, float ge, bool has, bool neu,
+                                         float lift, float sml, float cf, float& acc) {
+  const float uE = has ? ue : (neu ? ui : -ui);
+  const float gE = has ? ge : (neu ? -gi : gi);
+  const float jump = uE - ui;
+  acc += cf * (0.5f * s * (gE - gi) + sml * jump);
+  return gi + s * jump * lift;
+}
+
+// Ghost-state blend of one face (Eq. bc): the exterior value is a ue + b ui and the exterior
+// normal derivative c ge + d gi, with (a, b, c, d) = (1, 0, 1, 0) where the neighbour exists, else
+// (0, -1, 0, 1) on a Dirichlet and (0, 1, 0, -1) on a Neumann face.
+struct E4Face {
+  float2 a, b, c, d, hs, sl, sml, cf;  // hs = s / 2, sl = s lift (both halves equal)
+  __device__ __forceinline__ E4Face(float s, bool has, bool neu, float lift, float sml_, float cf_) {
+    const float bb = has ? 0.f : (neu ? 1.f : -1.f);
+    a = make_float2(has ? 1.f : 0.f, has ? 1.f : 0.f);
+    b = make_float2(bb, bb);
+    c = a;
+    d = make_float2(-bb, -bb);
+    hs = make_float2(0.5f * s, 0.5f * s);
+    sl = make_float2(s * lift, s * lift);
+    sml = make_float2(sml_, sml_);
+    cf = make_float2(cf_, cf_);
+  }
+  // two face points at once: returns the lifted gradient component, adds the flux to acc
+  __device__ __forceinline__ float2 apply(float2 ui, float2 gi, float2 ue, float2 ge, float2& acc) const {
+    const float2 uE = __ffma2_rn(a, ue, __fmul2_rn(b, ui));
+    const float2 gE = __ffma2_rn(c, ge, __fmul2_rn(d, gi));
+    const float2 jump = __fadd2_rn(uE, make_float2(-ui.x, -ui.y));
+    const float2 dg = __fadd2_rn(gE, make_float2(-gi.x, -gi.y));
+    acc = __ffma2_rn(cf, __ffma2_rn(hs, dg, __fmul2_rn(sml, jump)), acc);
+    return __ffma2_rn(sl, jump, gi);
+  }
+};
+
+template <int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX* BY* BZ, E4Shape<BX, BY, BZ>::PER_SM)
+    apply_elem4_kernel(const ApplyArgs<float> A, const __grid_constant__ CUtensorMap mu,
+                       const __grid_constant__ CUtensorMap mo, int* __restrict__ err) {
+  using S = E4Shape<BX, BY, BZ>;
+  using C = CTab<float>;
+  constexpr int SL = kE4Slot, PX = S::PX, PY = S::PY;
+  constexpr int dO = dtab_off(4), wO = wtab_off(4);
+  extern __shared__ __align__(128) unsigned char e4_raw[];
+  // 128-byte aligned for TMA; offset from the shared array itself, so that the compiler keeps
+  // every access in the shared window (LDS/STS rather than generic loads)
+  float* sm = reinterpret_cast<float*>(e4_raw + ((128u - (e4_smem(e4_raw) & 127u)) & 127u));
+  const uint32_t bar = e4_smem(sm + S::IN_WORDS);
+  const OpGeom<float>& g = A.g;
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = (tid / BX) % BY, tz = tid / (BX * BY);
+  const int nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY;
+  const int blk = blockIdx.x;
+  const int x0 = (blk % nbx) * BX, y0 = ((blk / nbx) % nby) * BY, z0 = (blk / (nbx * nby)) * BZ;
+  const int cx = x0 + tx, cy = y0 + ty, cz = z0 + tz;
+  const bool hxm = cx > 0, hxp = cx + 1 < g.nx, hym = cy > 0, hyp = cy + 1 < g.ny, hzm = cz > 0, hzp = cz + 1 < g.nz;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_launch_dependents();
+  pdl_wait();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(S::IN_WORDS * 4)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(e4_smem(sm)),
+        "l"(&mu), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(z0 - 1), "r"(bar)
+        : "memory");
+  }
+  if (!__syncthreads_and(e4_wait(bar, err))) {
+    if (tid == 0) e4_wait(bar, err);  // let the copy land (bounded) before the CTA leaves
+    __syncthreads();
+    return;
+  }
+  const float* me = sm + (((tz + 1) * PY + ty + 1) * PX + tx + 1) * SL;
+  constexpr int DX = SL, DY = PX * SL, DZ = PY * PX * SL;  // neighbour offsets in words
+  // element, gradient component and pre-mass sum as pairs of x-neighbouring points ([k][j][i / 2]):
+  // the y- and z-contractions combine whole pairs with one packed FMA (Dhat entry in both halves)
+  float2 U[4][4][2], ACC[4][4][2], G[4][4][2];
+#define E4(a, k, j, i) ((i) & 1 ? a[k][j][(i) >> 1].y : a[k][j][(i) >> 1].x)
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = *reinterpret_cast<const float4*>(me + k * 16 + j * 4);
+      U[k][j][0] = make_float2(v.x, v.y);
+      U[k][j][1] = make_float2(v.z, v.w);
+      ACC[k][j][0] = ACC[k][j][1] = make_float2(0.f, 0.f);
+    }
+  const float w0 = C::w(wO);
+  const float cfx = g.Jf[0] / (g.J * w0), cfy = g.Jf[1] / (g.J * w0), cfz = g.Jf[2] / (g.J * w0);
+  const float smx = g.sigma[0] - g.lift[0], smy = g.sigma[1] - g.lift[1], smz = g.sigma[2] - g.lift[2];
+  const float2 dy2 = make_float2(g.dxi[1], g.dxi[1]), dz2 = make_float2(g.dxi[2], g.dxi[2]);
+  // x: gradient component along the thread's lines, faces from the x-neighbours' lines, divergence.
+  // Along a line the pairs multiply 2 x 2 blocks of Dhat: (y0, y1) = (D00, D11) (x0, x1) +
+  // (D01, D10) (x1, x0) + (D02, D13) (x2, x3) + (D03, D12) (x3, x2), and likewise for (y2, y3).
+  float2 Bx[8];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)      // output pair
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {  // input pair
+      const int r0 = 2 * q, c0 = 2 * c;
+      Bx[4 * q + 2 * c] = make_float2(C::D(dO + r0 * 4 + c0), C::D(dO + (r0 + 1) * 4 + c0 + 1));
+      Bx[4 * q + 2 * c + 1] = make_float2(C::D(dO + r0 * 4 + c0 + 1), C::D(dO + (r0 + 1) * 4 + c0));
+    }
+  const float2 dx2 = make_float2(g.dxi[0], g.dxi[0]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 sw[2] = {make_float2(U[k][j][0].y, U[k][j][0].x), make_float2(U[k][j][1].y, U[k][j][1].x)};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float2 a = __fmul2_rn(Bx[4 * q], U[k][j][0]);
+        a = __ffma2_rn(Bx[4 * q + 1], sw[0], a);
+        a = __ffma2_rn(Bx[4 * q + 2], U[k][j][1], a);
+        a = __ffma2_rn(Bx[4 * q + 3], sw[1], a);
+        G[k][j][q] = __fmul2_rn(dx2, a);
+      }
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float r[4];
+      ld4s(me - DX + k * 16 + j * 4, r);
+      float ge = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ge += C::D(dO + 12 + l) * r[l];
+      G[k][j][0].x = e4_face(-1.f, U[k][j][0].x, G[k][j][0].x, r[3], g.dxi[0] * ge, hxm, g.neumann & 1, g.lift[0],
+                             smx, cfx, ACC[k][j][0].x);
+      ld4s(me + DX + k * 16 + j * 4, r);
+      ge = 0.f;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ge += C::D(dO + l) * r[l];
+      G[k][j][1].y = e4_face(1.f, U[k][j][1].y, G[k][j][1].y, r[0], g.dxi[0] * ge, hxp, (g.neumann >> 1) & 1,
+                             g.lift[0], smx, cfx, ACC[k][j][1].y);
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 sw[2] = {make_float2(G[k][j][0].y, G[k][j][0].x), make_float2(G[k][j][1].y, G[k][j][1].x)};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float2 a = __fmul2_rn(Bx[4 * q], G[k][j][0]);
+        a = __ffma2_rn(Bx[4 * q + 1], sw[0], a);
+        a = __ffma2_rn(Bx[4 * q + 2], G[k][j][1], a);
+        a = __ffma2_rn(Bx[4 * q + 3], sw[1], a);
+        ACC[k][j][q] = __ffma2_rn(dx2, a, ACC[k][j][q]);
+      }
+    }
+  // y
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float d = C::D(dO + j * 4 + l);
+          a = __ffma2_rn(make_float2(d, d), U[k][l][p], a);
+        }
+        G[k][j][p] = __fmul2_rn(dy2, a);
+      }
+  {
+    const E4Face fm(-1.f, hym, (g.neumann >> 2) & 1, g.lift[1], smy, cfy), fp(1.f, hyp, (g.neumann >> 3) & 1,
+                                                                            g.lift[1], smy, cfy);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float2 r[4][2];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ld4p(me - DY + k * 16 + l * 4, r[l]);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 ge = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float dd = C::D(dO + 12 + l);
+          ge = __ffma2_rn(make_float2(dd, dd), r[l][p], ge);
+        }
+        G[k][0][p] = fm.apply(U[k][0][p], G[k][0][p], r[3][p], __fmul2_rn(dy2, ge), ACC[k][0][p]);
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ld4p(me + DY + k * 16 + l * 4, r[l]);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 ge = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float dd = C::D(dO + l);
+          ge = __ffma2_rn(make_float2(dd, dd), r[l][p], ge);
+        }
+        G[k][3][p] = fp.apply(U[k][3][p], G[k][3][p], r[0][p], __fmul2_rn(dy2, ge), ACC[k][3][p]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float d = C::D(dO + j * 4 + l);
+          a = __ffma2_rn(make_float2(d, d), G[k][l][p], a);
+        }
+        ACC[k][j][p] = __ffma2_rn(dy2, a, ACC[k][j][p]);
+      }
+  // z
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float d = C::D(dO + k * 4 + l);
+          a = __ffma2_rn(make_float2(d, d), U[l][j][p], a);
+        }
+        G[k][j][p] = __fmul2_rn(dz2, a);
+      }
+  {
+    const E4Face fm(-1.f, hzm, (g.neumann >> 4) & 1, g.lift[2], smz, cfz), fp(1.f, hzp, (g.neumann >> 5) & 1,
+                                                                            g.lift[2], smz, cfz);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float2 r[4][2];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ld4p(me - DZ + l * 16 + j * 4, r[l]);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 ge = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float dd = C::D(dO + 12 + l);
+          ge = __ffma2_rn(make_float2(dd, dd), r[l][p], ge);
+        }
+        G[0][j][p] = fm.apply(U[0][j][p], G[0][j][p], r[3][p], __fmul2_rn(dz2, ge), ACC[0][j][p]);
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ld4p(me + DZ + l * 16 + j * 4, r[l]);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 ge = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float dd = C::D(dO + l);
+          ge = __ffma2_rn(make_float2(dd, dd), r[l][p], ge);
+        }
+        G[3][j][p] = fp.apply(U[3][j][p], G[3][j][p], r[0][p], __fmul2_rn(dz2, ge), ACC[3][j][p]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const float d = C::D(dO + k * 4 + l);
+          a = __ffma2_rn(make_float2(d, d), G[l][j][p], a);
+        }
+        ACC[k][j][p] = __ffma2_rn(dz2, a, ACC[k][j][p]);
+      }
+  // A u = -M acc (+ diag u); b - A u with b
+  const bool valid = cx < g.nx && cy < g.ny && cz < g.nz;
+  const int64_t e = valid ? ((int64_t)cz * g.ny + cy) * g.nx + cx : 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float dl[4], bl[4];
+      if (A.diag && valid) row4_g(A.diag + e * 64 + k * 16 + j * 4, dl);
+      if (A.b && valid) row4_g(A.b + e * 64 + k * 16 + j * 4, bl);
+      const float mjk = -g.J * C::w(wO + j) * C::w(wO + k);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float res = mjk * C::w(wO + i) * E4(ACC, k, j, i);
+        if (A.diag && valid) res += dl[i] * E4(U, k, j, i);
+        E4(ACC, k, j, i) = (A.b && valid) ? bl[i] - res : res;
+      }
+    }
+#undef E4
+  __syncthreads();  // every read of the staged box is done: its first slots take the result
+  float* o = sm + tid * SL;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      *reinterpret_cast<float4*>(o + k * 16 + j * 4) =
+          make_float4(ACC[k][j][0].x, ACC[k][j][0].y, ACC[k][j][1].x, ACC[k][j][1].y);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(&mo),
+                 "r"(0), "r"(x0), "r"(y0), "r"(z0), "r"(e4_smem(sm))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  }
+}
+
 // ------------------------------------------------------------------ block-of-lines apply (FP32)
 //
 // Shared memory serves one word per lane and cycle, so a contraction whose inputs come from other
@@ -1112,6 +1496,63 @@ void launch_blk(const ApplyArgs<float>& A, cudaStream_t s) {
   launch_pdl(apply_blk_kernel<N, B, EPB>, dim3((A.E + EPB - 1) / EPB), dim3(S::THREADS), (size_t)S::SMEM, s, A);
 }
 
+// Tensor maps of the element-per-thread apply: u (or the result) as a 4-D tensor [nz][ny][nx][64]
+// read or written in boxes of (BX, BY, BZ) elements of 68 words (the 4 words past an element are
+// outside the tensor: zeros on loads, not written on stores). No swizzle.
+PFN_cuTensorMapEncodeTiled_v12000 e4_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+bool e4_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, int bx, int by, int bz) {
+  auto fn = e4_encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {64, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[3] = {256, 256ull * nx, 256ull * nx * ny};
+  const cuuint32_t box[4] = {(cuuint32_t)kE4Slot, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// False (nothing launched) where the element-per-thread kernel cannot run this apply: subdomain
+// output, buffers not 16-byte aligned, no error flag, or a tensor map the driver does not encode.
+template <int BX, int BY, int BZ>
+bool launch_elem4(const ApplyArgs<float>& A, int* err, cudaStream_t s) {
+  using S = E4Shape<BX, BY, BZ>;
+  auto kern = apply_elem4_kernel<BX, BY, BZ>;
+  const OpGeom<float>& g = A.g;
+  if (A.rS || !err || (((uintptr_t)A.u | (uintptr_t)A.out) & 15)) return false;
+  CUtensorMap mu, mo;
+  if (!e4_map(&mu, A.u, g.nx, g.ny, g.nz, BX + 2, BY + 2, BZ + 2) || !e4_map(&mo, A.out, g.nx, g.ny, g.nz, BX, BY, BZ))
+    return false;
+  {
+    static std::mutex mu_attr;
+    static std::set<int> done;
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu_attr);
+    if (!done.count(dev)) {
+      DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+      done.insert(dev);
+    }
+  }
+  const int nb = ((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + BZ - 1) / BZ);
+  launch_pdl(kern, dim3(nb), dim3(S::THREADS), (size_t)S::SMEM, s, A, mu, mo, err);
+  return true;
+}
+
 template <int N, typename T, int EPB>
 void launch_apply_epb(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
                       const SubdomainOut& so, int E, cudaStream_t s) {
@@ -1125,7 +1566,7 @@ void launch_apply_epb(const OpGeom<T>& g, const T* D, const T* w, const T* u, co
 // (the autotuner times them per level).
 template <int N, typename T>
 void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                    const SubdomainOut& so, int variant, cudaStream_t s) {
+                    const SubdomainOut& so, int variant, int* err, cudaStream_t s) {
   const int E = g.nx * g.ny * g.nz;
   if (E == 0) return;
   constexpr unsigned a = LineVec<N, T>::w - 1;  // lines move in vectors of this many bytes
@@ -1141,6 +1582,11 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
       launch_pdl(apply_slice4_kernel, dim3((E + kSliceEPB - 1) / kSliceEPB), dim3(kSliceEPB * 4), 0, s, A);
       return;
     }
+    if (variant == 7) {
+      const ApplyArgs<float> A{g, D, w, u, diag, b, out, E, nullptr, 0, 0, nullptr, nullptr, nullptr};
+      if (!so.rS && launch_elem4<8, 4, 4>(A, err, s)) return;
+      variant = 0;
+    }
   }
   if constexpr (N >= 4 && std::is_same<T, float>::value) {
     if (variant == 5 || variant == 6) {
@@ -1152,7 +1598,7 @@ void launch_apply_n(const OpGeom<T>& g, const T* D, const T* w, const T* u, cons
       return;
     }
   }
-  if (variant >= 4) variant = 0;  // the slice kernel covers plain FP32 applies only, the block kernel FP32
+  if (variant >= 4) variant = 0;  // the slice and element kernels cover plain FP32 applies, the block kernel FP32
   if (variant == 0) variant = ((E + kBig - 1) / kBig >= 2 * 152) ? 3 : 1;
   if (variant == 1) launch_apply_epb<N, T, kSmall>(g, D, w, u, diag, b, out, so, E, s);
   else if (variant == 2) launch_apply_epb<N, T, kMid>(g, D, w, u, diag, b, out, so, E, s);
@@ -1344,27 +1790,27 @@ void upload_operator_tables() {
 
 template <typename T>
 void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                  cudaStream_t s, const SubdomainOut* so_ptr, int variant) {
+                  cudaStream_t s, const SubdomainOut* so_ptr, int variant, int* err) {
   const SubdomainOut so = so_ptr ? *so_ptr : SubdomainOut{};
   switch (N) {
-    case 2: launch_apply_n<2, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 3: launch_apply_n<3, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 4: launch_apply_n<4, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 5: launch_apply_n<5, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 6: launch_apply_n<6, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 7: launch_apply_n<7, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 8: launch_apply_n<8, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 9: launch_apply_n<9, T>(g, D, w, u, diag, b, out, so, variant, s); break;
-    case 10: launch_apply_n<10, T>(g, D, w, u, diag, b, out, so, variant, s); break;
+    case 2: launch_apply_n<2, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 3: launch_apply_n<3, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 4: launch_apply_n<4, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 5: launch_apply_n<5, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 6: launch_apply_n<6, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 7: launch_apply_n<7, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 8: launch_apply_n<8, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 9: launch_apply_n<9, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
+    case 10: launch_apply_n<10, T>(g, D, w, u, diag, b, out, so, variant, err, s); break;
     default: fail(DG_ERR_INVALID_ARG, "unsupported N");
   }
   DG_LAUNCHED(1);
 }
 
 template void launch_apply<double>(int, const OpGeom<double>&, const double*, const double*, const double*,
-                                   const double*, const double*, double*, cudaStream_t, const SubdomainOut*, int);
+                                   const double*, const double*, double*, cudaStream_t, const SubdomainOut*, int, int*);
 template void launch_apply<float>(int, const OpGeom<float>&, const float*, const float*, const float*, const float*,
-                                  const float*, float*, cudaStream_t, const SubdomainOut*, int);
+                                  const float*, float*, cudaStream_t, const SubdomainOut*, int, int*);
 
 // static shared memory of the fused kernel stays within 48 KiB up to N = 8
 bool coarse_smooth_available(int N) { return N >= 2 && N <= 8; }

@@ -167,10 +167,13 @@ struct ApplyArgs {
 };
 
 // out = A u (+ diag * u)  or, with b != nullptr, out = b - (A u + diag * u). variant: launch shape
-// (0 chosen by grid size, 1..3 few / middle / many elements per CTA).
+// (0 chosen by grid size, 1..3 few / middle / many elements per CTA; FP32 only: 4 the N = 4
+// slice-per-thread kernel, 5 and 6 the block-of-lines kernel, 7 the N = 4 element-per-thread kernel,
+// whose bounded staging wait raises *err if it gives up; a variant that cannot serve the call runs
+// as 0).
 template <typename T>
 void launch_apply(int N, const OpGeom<T>& g, const T* D, const T* w, const T* u, const T* diag, const T* b, T* out,
-                  cudaStream_t s, const SubdomainOut* so = nullptr, int variant = 0);
+                  cudaStream_t s, const SubdomainOut* so = nullptr, int variant = 0, int* err = nullptr);
 constexpr int kApplyVariants = 3;
 
 // Build explicit subdomain matrices A_S for a set of classes (column-major == row-major by symmetry).

@@ -29,7 +29,10 @@ int apply_variant(dg_domain* dom, Level& L, bool fused, const std::function<void
   if (v < 0) {
     // launch shapes of the line kernel; the plane kernel for plain FP32 applies at N = 4
     std::vector<int> cand{0, 1, 2, 3};
-    if (!fused && dom->N == 4 && sizeof(T) == 4) cand.push_back(4);
+    if (!fused && dom->N == 4 && sizeof(T) == 4) {  // the slice kernel and the element kernel
+      cand.push_back(4);
+      cand.push_back(7);
+    }
     if (dom->N >= 4 && sizeof(T) == 4) {  // the block-of-lines kernel, two launch shapes
       cand.push_back(5);
       cand.push_back(6);
@@ -91,7 +94,8 @@ void apply_level(dg_domain* dom, int level, const double* u, double* out, const 
   const double* diag = (with_lin && level == 0 && dom->lin_set) ? dom->lin64.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP64, s, apply_bytes(L.ndof, 8, b, diag), apply_flops(L.ndof, dom->N));
   auto run = [&](int v) {
-    launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s, so, v);
+    launch_apply<double>(dom->N, L.g64, dom->D64.get(), dom->w64.get(), u, diag, b, out, s, so, v,
+                         dom->err_flag.get());
   };
   run(apply_variant<double>(dom, L, so != nullptr, run, s));
 }
@@ -108,7 +112,8 @@ void apply_level_f32(dg_domain* dom, int level, const float* u, float* out, cons
   const float* diag = (with_lin && level == 0 && dom->lin_set && dom->lin32.get()) ? dom->lin32.get() : nullptr;
   PhaseScope ps(dom->prof, DG_PHASE_APPLY_FP32, s, apply_bytes(L.ndof, 4, b, diag), apply_flops(L.ndof, dom->N));
   auto run = [&](int v) {
-    launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s, so, v);
+    launch_apply<float>(dom->N, L.g32, dom->D32.get(), dom->w32.get(), u, diag, b, out, s, so, v,
+                        dom->err_flag.get());
   };
   run(apply_variant<float>(dom, L, so != nullptr, run, s));
 }

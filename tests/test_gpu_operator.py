@@ -136,12 +136,12 @@ np.savez(sys.argv[1], **out)
 """
 
 
-@pytest.mark.parametrize("variant,orders", [("4", (4,)), ("1", (4, 7)), ("5", (4, 5, 6, 7, 8, 9, 10)),
-                                            ("6", (4, 5, 6, 7, 8, 9, 10))])
+@pytest.mark.parametrize("variant,orders", [("4", (4,)), ("7", (4,)), ("1", (4, 7)),
+                                            ("5", (4, 5, 6, 7, 8, 9, 10)), ("6", (4, 5, 6, 7, 8, 9, 10))])
 def test_pinned_fp32_apply_kernels_match_oracle(tmp_path, variant, orders):
     """Each plain FP32 apply kernel pinned for every apply of the process (DG_APPLY_VARIANT: 4 the
-    slice-per-thread kernel at N = 4, 5 and 6 the two launch shapes of the block-of-lines kernel,
-    1 a line-kernel shape for comparison): the operator against the oracle on ragged element counts
+    slice-per-thread kernel at N = 4, 7 the element-per-thread kernel at N = 4, 5 and 6 the two launch
+    shapes of the block-of-lines kernel, 1 a line-kernel shape for comparison): the operator against the oracle on ragged element counts
     (66 elements: no launch shape divides it), Neumann faces and a single element, the V-cycle's
     residual (b - A u) and the linearized puncture operator (+ diag u), at every order offered."""
     import os
