@@ -59,15 +59,32 @@ void keep_pool_memory() {
 AllocStreamScope::AllocStreamScope(cudaStream_t s) : prev(tl_alloc_stream) { tl_alloc_stream = s; }
 AllocStreamScope::~AllocStreamScope() { tl_alloc_stream = prev; }
 
-// Off by default: measured on the 8^3, N = 8 workload it slowed the FP64 solve from 339 to 630 ms
-// (dependent CTAs parked on the SMs during the long FP64 GEMMs) and the mixed one from 5.55 to
-// 5.78 ms. DG_PDL=1 turns it on.
+// Off by default for every launch: measured on the 8^3, N = 8 workload it slowed the FP64 solve
+// from 339 to 630 ms (dependent CTAs parked on the SMs during the long FP64 GEMMs) and the mixed one
+// from 5.55 to 5.78 ms. DG_PDL=1 turns it on everywhere; a PdlScope turns it on for the launches
+// made inside it on this thread (the coarse levels of the V-cycle, see schwarz_smooth).
+namespace {
+thread_local int tl_pdl_scope = 0;
+}
 bool pdl_enabled() {
   static const bool on = [] {
     const char* v = std::getenv("DG_PDL");
     return v && std::strcmp(v, "1") == 0;
   }();
-  return on;
+  return on || tl_pdl_scope > 0;
+}
+PdlScope::PdlScope(bool on_) : on(on_) {
+  if (on) ++tl_pdl_scope;
+}
+PdlScope::~PdlScope() {
+  if (on) --tl_pdl_scope;
+}
+int pdl_vcycle_mode() {
+  static const int mode = [] {
+    const char* v = std::getenv("DG_PDL_COARSE");
+    return v ? std::atoi(v) : 1;
+  }();
+  return mode;
 }
 
 int autotune(const std::vector<int64_t>& key, const std::vector<int>& candidates,

@@ -50,6 +50,18 @@ const char* null_handle_error();
 // stream-ordered (cudaMallocAsync / cudaFreeAsync), so one domain's set-up or teardown does not
 // wait for the work of domains on other streams, as cudaMalloc / cudaFree would.
 cudaStream_t alloc_stream();
+// Programmatic dependent launch for the launches made on this thread while a scope with on = true
+// is alive (pdl_enabled() in pdl.cuh); pdl_vcycle_mode(): which FP32 V-cycle launches open one
+// (DG_PDL_COARSE: 0 none, 1 the coarse levels' smoothing, 2 every level and the transfers).
+struct PdlScope {
+  bool on;
+  explicit PdlScope(bool on_);
+  ~PdlScope();
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
+};
+int pdl_vcycle_mode();
+
 struct AllocStreamScope {
   cudaStream_t prev;
   explicit AllocStreamScope(cudaStream_t s);

@@ -291,6 +291,9 @@ constexpr int kCoarseFusedElems = 64;
 
 template <typename T>
 void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations, bool u_is_zero, cudaStream_t s) {
+  // FP32 coarse levels: each kernel is a short latency chain, so the next one's launch and set-up
+  // overlap it (programmatic dependent launch); the fine level and FP64 keep plain stream order
+  const PdlScope pdl(sizeof(T) == 4 && pdl_vcycle_mode() >= (level > 0 ? 1 : 2));
   ensure_schwarz(dom, level);
   Level& L = dom->levels[level];
   LevelWork<T>& W = work<T>(L);
@@ -413,6 +416,7 @@ void vcycle(dg_domain* dom, const T* r, T* z, cudaStream_t s) {
   auto B = [&](int l) -> const T* { return l == 0 ? r : work<T>(dom->levels[l]).b.get(); };
   auto U = [&](int l) -> T* { return l == 0 ? z : work<T>(dom->levels[l]).u.get(); };
   for (int l = 0; l < nl; ++l) DG_CUDA(cudaMemsetAsync(U(l), 0, sizeof(T) * dom->levels[l].ndof, s));
+  const PdlScope pdl(sizeof(T) == 4 && pdl_vcycle_mode() >= 2);  // transfers and residuals
   for (int l = 0; l < nl - 1; ++l) {
     Level& L = dom->levels[l];
     schwarz_smooth<T>(dom, l, B(l), U(l), pre, true, s);
