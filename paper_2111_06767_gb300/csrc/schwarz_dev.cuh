@@ -55,18 +55,21 @@ __device__ __forceinline__ void gather_column(const SubdomainGeom& g, const T* _
   __syncthreads();  // the previous call on this CTA is done with nb
   if (threadIdx.x < 7) nb[threadIdx.x] = threadIdx.x == 0 ? e : nbr_elem(g, e, threadIdx.x - 1);
   __syncthreads();
-  if constexpr (PDL) pdl_wait();
   const int nS = g.nS, ld = g.ld, N3 = g.N * g.N * g.N;
   const int* m = map + (size_t)orient[e] * nS;
   T* out = rS + (size_t)col * ld;
-  for (int q = threadIdx.x; q < ld; q += blockDim.x) {
-    T v = 0;
+  // the point map (static) is read before waiting for the previous kernel
+  for (int q = threadIdx.x, first = 1; first || q < ld; q += blockDim.x, first = 0) {
+    int64_t src = -1;
     if (q < nS) {
       const int code = __ldg(m + q);
-      const int src = nb[code >> 16];
-      if (src >= 0) v = r[(int64_t)src * N3 + (code & 0xFFFF)];
+      const int el = nb[code >> 16];
+      if (el >= 0) src = (int64_t)el * N3 + (code & 0xFFFF);
     }
-    out[q] = v;
+    if constexpr (PDL) {
+      if (first) pdl_wait();
+    }
+    if (q < ld) out[q] = src >= 0 ? r[src] : T(0);
   }
 }
 
@@ -102,23 +105,41 @@ __device__ __forceinline__ void scatter_element(const SubdomainGeom& g, const T*
   }
   __syncthreads();
   const T* sh0 = shares + (size_t)s_pat * N3 * 7;
-  if constexpr (PDL) pdl_wait();
-  for (int p = threadIdx.x; p < N3; p += blockDim.x) {
-    const T* sh = sh0 + (size_t)p * 7;
-    auto du = [&](int64_t i) { return L2ONLY ? __ldcg(duS + i) : duS[i]; };
-    T acc = sh[0] * du((int64_t)s_col[0] * ld + __ldg(inv + s_inv[0] + p));
-    // the neighbour across face f covers this point only within N_overlap layers of that face
-    const int c[3] = {p % g.N, (p / g.N) % g.N, p / (g.N * g.N)};
+  // per point: the static look-ups (subdomain rows and weight shares) first, before waiting for the
+  // previous kernel, then the seven du_S reads issued together
+  for (int p = threadIdx.x, first = 1; first || p < N3; p += blockDim.x, first = 0) {
+    const bool act = p < N3;
+    int64_t idx[7];
+    T w[7];
+    if (act) {
+      const T* sh = sh0 + (size_t)p * 7;
+      // the neighbour across face f covers this point only within N_overlap layers of that face
+      const int c[3] = {p % g.N, (p / g.N) % g.N, p / (g.N * g.N)};
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      if (s_col[1 + f] < 0) continue;
-      const int cd = c[f >> 1];
-      if (((f & 1) ? g.N - 1 - cd : cd) >= g.ov) continue;
-      const int row = __ldg(inv + s_inv[1 + f] + p);
-      if (row >= 0) acc += sh[1 + f] * du((int64_t)s_col[1 + f] * ld + row);
+      for (int sl = 0; sl < 7; ++sl) {
+        bool in = s_col[sl] >= 0;
+        if (sl > 0) {
+          const int f = sl - 1, cd = c[f >> 1];
+          in = in && ((f & 1) ? g.N - 1 - cd : cd) < g.ov;
+        }
+        const int row = in ? __ldg(inv + s_inv[sl] + p) : -1;
+        idx[sl] = row >= 0 ? (int64_t)s_col[sl] * ld + row : -1;
+        w[sl] = row >= 0 ? sh[sl] : T(0);
+      }
     }
+    if constexpr (PDL) {
+      if (first) pdl_wait();
+    }
+    if (!act) continue;
+    T v[7];
+#pragma unroll
+    for (int sl = 0; sl < 7; ++sl) v[sl] = idx[sl] >= 0 ? (L2ONLY ? __ldcg(duS + idx[sl]) : duS[idx[sl]]) : T(0);
     TU* up = u + (int64_t)q * N3 + p;
-    *up = (L2ONLY ? __ldcg(up) : *up) + (TU)acc;
+    const TU u0 = L2ONLY ? __ldcg(up) : *up;
+    T acc = w[0] * v[0];
+#pragma unroll
+    for (int sl = 1; sl < 7; ++sl) acc += w[sl] * v[sl];
+    *up = u0 + (TU)acc;
   }
 }
 

@@ -35,10 +35,12 @@ def _sine_problem(n, N):
 
 
 def _recovers(d, f, ud):
+    # to 1e-11: on this small problem a 1e-10 residual leaves the solution up to 1.9e-10 from the
+    # direct solve (the residual bounds the error only up to the condition number)
     b = d.rhs(torch.from_numpy(f.ravel()).cuda())
     u = torch.zeros_like(b)
-    rep = d.solve(b, u, tol=1e-10)
-    assert rep.status == STATUS["DG_OK"] and rep.relative_residual <= 1e-10
+    rep = d.solve(b, u, tol=1e-11)
+    assert rep.status == STATUS["DG_OK"] and rep.relative_residual <= 1e-11
     assert rel(u.cpu().numpy(), ud) < 1e-10
 
 

@@ -36,10 +36,10 @@ def _golden(name):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("krylov", ["fgmres", "fcg"])
 def test_sine_2x2x2_N6_matches_dense_direct_solve(precision, krylov):
-    """FGMRES at the 1e-10 residual of the configuration meets 1e-10 solution parity; flexible CG
-    with the FP32 V-cycle stopped at 1e-10 is 3.6e-10 from the direct solution (measured), so it
-    solves to 1e-11, the tolerance at which the parity holds."""
-    tol = 1e-10 if krylov == "fgmres" else 1e-11
+    """A 1e-10 residual leaves this problem up to 1.9e-10 (FGMRES, depending on the tuned launch
+    shapes) or 3.6e-10 (flexible CG with the FP32 V-cycle) from the direct solution (measured), so
+    both solve to 1e-11, the tolerance at which the parity holds."""
+    tol = 1e-11
     cfg = workloads.SINE_2x2x2
     grid = box(cfg.n, cfg.N, cfg.penalty)
     x, y, z = grid.coordinates()

@@ -14,8 +14,10 @@ dgg = pytest.importorskip("paper_2111_06767_gb300")
 
 def test_sine_2x2x2_N6_matches_direct_solution():
     """3-D sine problem on 2^3 elements, N = 6, C = 1.5, two levels: the solution must agree with the
-    oracle's dense direct solve to 1e-10 relative at a 1e-10 residual, with FGMRES iteration
-    counts within one of the oracle's."""
+    oracle's dense direct solve to 1e-10 relative, with FGMRES iteration counts within one of the
+    oracle's. A 1e-10 residual bounds the error only up to the condition number: a solve stopped
+    there measured up to 1.9e-10 from the direct solution, depending on the launch shapes the
+    autotuner picked (they change FP32 and split-K summation orders), so the solve runs to 1e-11."""
     n, N = (2, 2, 2), 6
     grid = box(n, N)
     pr = solve.Problem(grid)
@@ -30,12 +32,15 @@ def test_sine_2x2x2_N6_matches_direct_solution():
         u = torch.zeros_like(b)
         rep = d.solve(b, u, tol=1e-10)
         assert rep.relative_residual <= 1e-10
-        assert rel(u.cpu().numpy(), u_direct) < 1e-10
         if precision == "fp64":
             assert abs(rep.iterations - info["iterations"]) <= 1
+        u = torch.zeros_like(b)
+        rep = d.solve(b, u, tol=1e-11)
+        assert rep.relative_residual <= 1e-11
+        assert rel(u.cpu().numpy(), u_direct) < 1e-10
         # the oracle's operator confirms the residual
         assert np.linalg.norm(b_ref.ravel() - dg.apply(pr.graphs[0], u.cpu().numpy().reshape(-1, N, N, N)).ravel()) \
-            <= 1.01e-10 * np.linalg.norm(b_ref)
+            <= 1.01e-11 * np.linalg.norm(b_ref)
 
 
 def test_gaussian_4x4x4_matches_oracle_solution():
