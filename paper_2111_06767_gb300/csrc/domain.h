@@ -31,8 +31,12 @@ struct SchwarzLevel {
   DevBuf<float> inv32;             // FP32 copies (mixed mode)
   DevBuf<uint16_t> inv16;          // curved MIXED domains: per-subdomain inverses in FP16, each scaled
   DevBuf<float> inv16_scale;       //   by its largest magnitude (kept here)
-  DevBuf<int4> tiles;              // SIMT GEMM tile list (class, row0, col0, columns left): 64 x 64
-  int n_tiles = 0;
+  DevBuf<int4> tiles;              // SIMT GEMM tiles (class | width code << 24 | zero << 30, row0, col0,
+  int n_tiles = 0;                 //   columns left): 64 rows x 64, 32 or 16 columns
+  DevBuf<int> kchunks16;           // per class: [count, K chunks of 16 that meet a present slot]
+  DevBuf<int> kchunks32;           // the same for chunks of 32 (tensor-core GEMM)
+  std::vector<int> class_nS;       // per class: rows of the slots present (its real subdomain size)
+  double alg_inv = 0, alg_vec = 0, alg_mac = 0;  // sum_c nS_c^2, sum_c E_c nS_c, sum_c E_c nS_c^2
   DevBuf<int4> tiles_tc;           // tensor-core GEMM tiles: 128 rows x 64 columns
   int n_tiles_tc = 0;
   DevBuf<int4> tiles_tc256;        // tensor-core GEMM tiles: 128 rows x 256 columns (one read of a

@@ -238,10 +238,11 @@ void launch_coarse_smooth(int N, const CoarseArgs& a, cudaStream_t s);
 // Tensor-core (tcgen05, TF32) class GEMM; Y columns of ld values, n_cols columns in X and Y.
 bool tc_gemm_available();
 // split: K split across a cluster of 1, 2, 4 or 8 CTAs; 0 picks it from the tile count. bn: tile
-// width, 64 or 256 (d_tiles must list tiles of that width).
+// width, 64 or 256 (d_tiles must list tiles of that width). d_kchunks: per class [count, indices of
+// the 32-wide K chunks that meet a present slot], ld / 32 + 1 ints per class.
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split = 0,
-                          int bn = 64);
+                          const int4* d_tiles, int n_tiles, const int* d_kchunks, int* err, float alpha,
+                          cudaStream_t s, int split = 0, int bn = 64);
 // Splits the tensor-core GEMM accepts for this shape (each CTA keeps >= 4 K chunks).
 std::vector<int> tc_gemm_splits(int ld);
 

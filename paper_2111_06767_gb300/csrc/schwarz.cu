@@ -430,71 +430,71 @@ template void launch_scatter_tab<float, float>(const SubdomainGeom&, const float
 // ------------------------------------------------------------------ class GEMM (SIMT)
 
 // Y[:, c0:c0+m] = Inv_c (nS x nS, row-major) * X[:, c0:c0+m] (columns of nS contiguous values).
-// 64 x 64 output tiles, K chunks of 16 staged in shared memory, 4 x 4 outputs per thread. SPLIT > 1:
-// the K range of a tile is split over the SPLIT CTAs of a thread-block cluster (on GB300 a single
-// CTA of this FP64 product occupies an SM's FP64 pipe for a long time, so coarse levels with few
-// tiles would leave most SMs idle); each CTA keeps its partial tile in shared memory and, after a
-// cluster barrier, sums 1/SPLIT of the tile's rows over all partials through distributed shared
-// memory in rank order, so the result does not depend on timing.
-template <typename T, int SPLIT>
-__global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ inv, const T* __restrict__ X,
-                                                         T* __restrict__ Y, int nS, const int4* __restrict__ tiles,
-                                                         T alpha) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  // the K chunks' staging, then (SPLIT > 1) the partial tile in the same memory
-  constexpr size_t kStage = 2 * BK * (BM + 1) * sizeof(T), kPart = SPLIT > 1 ? BM * (BN + 1) * sizeof(T) : 0;
-  __shared__ __align__(16) unsigned char raw[kStage > kPart ? kStage : kPart];
+// 64-row output tiles of 64, 32 or 16 columns (a class's columns are covered with little padding),
+// K chunks of 16 staged in shared memory, 4 x (width / 16) outputs per thread. Only the K chunks
+// that meet a slot of the subdomain present in the class are read (a missing neighbour's slot has
+// zero coupling in the inverse), and tiles whose rows all lie in missing slots only write zeros.
+// SPLIT > 1: the K chunks of a tile are split over the SPLIT CTAs of a thread-block cluster (on
+// GB300 a single CTA of this FP64 product occupies an SM's FP64 pipe for a long time, so coarse
+// levels with few tiles would leave most SMs idle); each CTA keeps its partial tile in shared
+// memory and, after a cluster barrier, sums 1/SPLIT of the tile's rows over all partials through
+// distributed shared memory in rank order, so the result does not depend on timing.
+template <typename T, int SPLIT, int NR>
+__device__ __forceinline__ void class_gemm_tile(const T* __restrict__ A, const T* __restrict__ X, T* __restrict__ Y,
+                                                int ld, int row0, int col0, int ncol, const int* __restrict__ kl,
+                                                int nk, int rank, unsigned char* raw, T alpha) {
+  constexpr int BM = 64, BN = 16 * NR, BK = 16;
   T(*sA)[BM + 1] = reinterpret_cast<T(*)[BM + 1]>(raw);
-  T(*sB)[BN + 1] = reinterpret_cast<T(*)[BN + 1]>(raw + BK * (BM + 1) * sizeof(T));
-  const int4 tile = tiles[blockIdx.x / SPLIT];  // (class, row0, col0, ncols in this class from col0)
-  const int cls = tile.x, row0 = tile.y, col0 = tile.z, ncol = min(tile.w, BN);
-  const T* A = inv + (size_t)cls * nS * nS;
+  T(*sB)[BM + 1] = reinterpret_cast<T(*)[BM + 1]>(raw + BK * (BM + 1) * sizeof(T));
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  int rank = 0;
-  if constexpr (SPLIT > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  // K chunks [kc0, kc1) of this CTA
-  const int nk = (nS + BK - 1) / BK;
   const int kc0 = rank * nk / SPLIT, kc1 = (rank + 1) * nk / SPLIT;
-  T acc[4][4] = {};
-  pdl_launch_dependents();
-  pdl_wait();
-  // each thread stages 4 values of A and 4 of X per K chunk; the next chunk's values are loaded
+  T acc[4][NR] = {};
+  // each thread stages 4 values of A and NR of X per K chunk; the next chunk's values are loaded
   // into registers while the current chunk is multiplied
-  constexpr int PER = BM * BK / 256;
-  static_assert(BM * BK % 256 == 0 && BN * BK % 256 == 0, "staging shape");
-  T pa[PER], pb[PER];
+  constexpr int PA = BM * BK / 256, PB = BN * BK / 256;
+  T pa[PA], pb[PB];
   auto fetch = [&](int kc) {
-    const int k0 = kc * BK;
+    const int k0 = kl[kc] * BK;
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
+    for (int q = 0; q < PA; ++q) {
       const int t = threadIdx.x + 256 * q;
       const int r = t / BK, kk = t % BK;
       const int gr = row0 + r, gk = k0 + kk;
-      pa[q] = (gr < nS && gk < nS) ? A[(size_t)gr * nS + gk] : T(0);
-      const int c = r;  // BN == BM
-      pb[q] = (c < ncol && gk < nS) ? X[(size_t)(col0 + c) * nS + gk] : T(0);
+      pa[q] = (gr < ld && gk < ld) ? A[(size_t)gr * ld + gk] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int t = threadIdx.x + 256 * q;
+      const int c = t / BK, kk = t % BK;
+      const int gk = k0 + kk;
+      pb[q] = (c < ncol && gk < ld) ? X[(size_t)(col0 + c) * ld + gk] : T(0);
     }
   };
   if (kc0 < kc1) fetch(kc0);
   for (int kc = kc0; kc < kc1; ++kc) {
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
+    for (int q = 0; q < PA; ++q) {
       const int t = threadIdx.x + 256 * q;
-      const int r = t / BK, kk = t % BK;
-      sA[kk][r] = pa[q];
-      sB[kk][r] = pb[q];
+      sA[t % BK][t / BK] = pa[q];
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int t = threadIdx.x + 256 * q;
+      sB[t % BK][t / BK] = pb[q];
     }
     __syncthreads();
     if (kc + 1 < kc1) fetch(kc + 1);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a[4], b[NR];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { a[q] = sA[kk][ty + 16 * q]; b[q] = sB[kk][tx + 16 * q]; }
+      for (int q = 0; q < 4; ++q) a[q] = sA[kk][ty + 16 * q];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) b[r] = sB[kk][tx + 16 * r];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[q][r] += a[q] * b[r];
+        for (int r = 0; r < NR; ++r) acc[q][r] += a[q] * b[r];
     }
     __syncthreads();
   }
@@ -502,28 +502,28 @@ __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ i
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int gr = row0 + ty + 16 * q;
-      if (gr >= nS) continue;
+      if (gr >= ld) continue;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < NR; ++r) {
         const int c = tx + 16 * r;
-        if (c < ncol) Y[(size_t)(col0 + c) * nS + gr] = alpha * acc[q][r];
+        if (c < ncol) Y[(size_t)(col0 + c) * ld + gr] = alpha * acc[q][r];
       }
     }
   } else {
     // partial tile [row][col] in this CTA's shared memory (the staging is free: the K loop ended
-    // with a barrier)
-    T(*part)[BN + 1] = reinterpret_cast<T(*)[BN + 1]>(raw);
+    // with a barrier, or never ran)
+    T(*part)[64 + 1] = reinterpret_cast<T(*)[64 + 1]>(raw);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) part[ty + 16 * q][tx + 16 * r] = acc[q][r];
+      for (int r = 0; r < NR; ++r) part[ty + 16 * q][tx + 16 * r] = acc[q][r];
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     // this CTA sums rows [rank BM / SPLIT, (rank + 1) BM / SPLIT) over the partials in rank order
     constexpr int RPC = BM / SPLIT;
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(&part[0][0]);
     for (int t = threadIdx.x; t < RPC * BN; t += 256) {
       const int rr = rank * RPC + t / BN, c = t % BN;
-      const uint32_t off = base + (uint32_t)((rr * (BN + 1) + c) * sizeof(T));
+      const uint32_t off = base + (uint32_t)((rr * (64 + 1) + c) * sizeof(T));
       T sum = T(0);
 #pragma unroll
       for (int p = 0; p < SPLIT; ++p) {
@@ -535,20 +535,46 @@ __global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ i
         sum += v;
       }
       const int gr = row0 + rr;
-      if (gr < nS && c < ncol) Y[(size_t)(col0 + c) * nS + gr] = alpha * sum;
+      if (gr < ld && c < ncol) Y[(size_t)(col0 + c) * ld + gr] = alpha * sum;
     }
     // no CTA leaves while a peer still reads its partial tile
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   }
 }
 
+// tiles: (class | width code << 24 | zero-tile flag << 30, row0, col0, columns of the class from
+// col0); kchunks: per class [count, chunk indices...] (ld / 16 + 1 ints per class).
+template <typename T, int SPLIT>
+__global__ void __launch_bounds__(256) class_gemm_kernel(const T* __restrict__ inv, const T* __restrict__ X,
+                                                         T* __restrict__ Y, int ld, const int4* __restrict__ tiles,
+                                                         const int* __restrict__ kchunks, T alpha) {
+  // the K chunks' staging, then (SPLIT > 1) the partial tile in the same memory
+  constexpr size_t kStage = 2 * 16 * (64 + 1) * sizeof(T), kPart = SPLIT > 1 ? 64 * (64 + 1) * sizeof(T) : 0;
+  __shared__ __align__(16) unsigned char raw[kStage > kPart ? kStage : kPart];
+  const int4 tile = tiles[blockIdx.x / SPLIT];
+  const int cls = tile.x & 0xFFFF, wcode = (tile.x >> 24) & 3;
+  const bool zero = (tile.x >> 30) & 1;
+  const int ncol = min(tile.w, 64 >> wcode);
+  const T* A = inv + (size_t)cls * ld * ld;
+  const int* kl = kchunks + (size_t)cls * (ld / 16 + 1);
+  int rank = 0;
+  if constexpr (SPLIT > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  pdl_launch_dependents();
+  pdl_wait();
+  const int nk = zero ? 0 : kl[0];
+  if (wcode == 0) class_gemm_tile<T, SPLIT, 4>(A, X, Y, ld, tile.y, tile.z, ncol, kl + 1, nk, rank, raw, alpha);
+  else if (wcode == 1) class_gemm_tile<T, SPLIT, 2>(A, X, Y, ld, tile.y, tile.z, ncol, kl + 1, nk, rank, raw, alpha);
+  else class_gemm_tile<T, SPLIT, 1>(A, X, Y, ld, tile.y, tile.z, ncol, kl + 1, nk, rank, raw, alpha);
+}
+
 // K split of the CUDA-core class GEMM: 1, 2, 4 or 8 CTAs per tile (0: the smallest that gives at
 // least two CTAs per SM, keeping >= 8 K chunks per CTA).
 template <typename T>
-void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
-                             cudaStream_t s, int split) {
+void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int ld, const int4* d_tiles, int n_tiles,
+                             const int* d_kchunks, T alpha, cudaStream_t s, int split) {
   if (n_tiles == 0) return;
-  const int nk = (nS + 15) / 16;
+  DG_REQUIRE(ld % 16 == 0, "class GEMM stride must be a multiple of 16");
+  const int nk = ld / 16;
   if (split == 0) {
     split = 1;
     while (split < 8 && n_tiles * split < 2 * 152 && nk / (split * 2) >= 8) split *= 2;
@@ -574,10 +600,13 @@ void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4*
   }
   cfg.attrs = at;
   cfg.numAttrs = na;
-  if (split == 1) DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 1>, inv, X, Y, nS, d_tiles, alpha));
-  else if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 2>, inv, X, Y, nS, d_tiles, alpha));
-  else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 4>, inv, X, Y, nS, d_tiles, alpha));
-  else DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 8>, inv, X, Y, nS, d_tiles, alpha));
+  if (split == 1)
+    DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 1>, inv, X, Y, ld, d_tiles, d_kchunks, alpha));
+  else if (split == 2)
+    DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 2>, inv, X, Y, ld, d_tiles, d_kchunks, alpha));
+  else if (split == 4)
+    DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 4>, inv, X, Y, ld, d_tiles, d_kchunks, alpha));
+  else DG_CUDA(cudaLaunchKernelEx(&cfg, class_gemm_kernel<T, 8>, inv, X, Y, ld, d_tiles, d_kchunks, alpha));
   DG_LAUNCHED(1);
 }
 
@@ -737,9 +766,9 @@ template void launch_sub_lsq_combine<float>(int, int, int, const float*, const f
                                             cudaStream_t);
 
 
-template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int, double,
-                                              cudaStream_t, int);
-template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, float,
-                                             cudaStream_t, int);
+template void launch_class_gemm_tiles<double>(const double*, const double*, double*, int, const int4*, int,
+                                               const int*, double, cudaStream_t, int);
+template void launch_class_gemm_tiles<float>(const float*, const float*, float*, int, const int4*, int, const int*,
+                                              float, cudaStream_t, int);
 
 }  // namespace dg

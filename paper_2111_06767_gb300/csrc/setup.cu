@@ -201,25 +201,67 @@ void classify_schwarz(dg_domain* dom, Level& L) {
     upload(sw.class_of_col, class_of_col, s);
   }
   upload(sw.xform_of_elem, xform, s);
+  // Rows (and columns) of a class's inverse in the slots of missing neighbours have no coupling to
+  // the rest (identity block): K chunks and row tiles that meet no present slot are skipped, and
+  // tiles whose rows lie only there just write zeros (zero flag, bit 30 of the tile's first word).
+  const int slot_rows = ov * N * N;
+  auto present = [&](int c, int r0, int r1) {  // does row range [r0, r1) meet a present slot?
+    if (dom->curved) return true;
+    for (int sl = 0; sl < 7; ++sl) {
+      if (!sw.patch[(size_t)c * 49 + 42 + sl]) continue;
+      const int a = sl == 0 ? 0 : N3 + (sl - 1) * slot_rows, b = sl == 0 ? N3 : a + slot_rows;
+      if (r0 < b && a < r1) return true;
+    }
+    return false;
+  };
+  sw.class_nS.assign(nc, sw.nS);
+  sw.alg_inv = sw.alg_vec = sw.alg_mac = 0;
+  for (int c = 0; c < nc; ++c) {
+    if (!dom->curved) {
+      sw.class_nS[c] = N3;
+      for (int f = 0; f < 6; ++f) sw.class_nS[c] += sw.patch[(size_t)c * 49 + 43 + f] ? slot_rows : 0;
+    }
+    const double n = sw.class_nS[c], m = sw.class_count[c];
+    sw.alg_inv += dom->curved ? m * n * n : n * n;  // curved: one inverse per subdomain
+    sw.alg_vec += m * n;
+    sw.alg_mac += m * n * n;
+  }
+  for (int bk : {16, 32}) {
+    const int per = sw.ld / bk + 1, nck = dom->curved ? 0 : nc;  // curved levels use no class GEMM
+    std::vector<int> kc((size_t)nck * per, 0);
+    for (int c = 0; c < nck; ++c) {
+      int* k = &kc[(size_t)c * per];
+      for (int q = 0; q < sw.ld / bk; ++q)
+        if (present(c, q * bk, (q + 1) * bk)) k[1 + k[0]++] = q;
+    }
+    upload(bk == 16 ? sw.kchunks16 : sw.kchunks32, kc, s);
+  }
+  auto tile = [&](int c, int r0, int rows, int c0, int wcode) {
+    const int zero = present(c, r0, std::min(r0 + rows, sw.ld)) ? 0 : 1;
+    return make_int4(c | (wcode << 24) | (zero << 30), r0, sw.class_first[c] + c0, sw.class_count[c] - c0);
+  };
+  // CUDA-core tiles: 64 columns while more than 48 are left, then 32 and/or 16
   std::vector<int4> tiles;
   for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 64)
-      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
-        tiles.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
+      for (int c0 = 0; c0 < sw.class_count[c];) {
+        const int left = sw.class_count[c] - c0;
+        const int w = left > 48 ? 64 : (left > 16 ? 32 : 16);
+        tiles.push_back(tile(c, r0, 64, c0, w == 64 ? 0 : (w == 32 ? 1 : 2)));
+        c0 += w;
+      }
   sw.n_tiles = (int)tiles.size();
   upload(sw.tiles, tiles, s);
   std::vector<int4> tiles_tc;
   for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 128)
-      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64)
-        tiles_tc.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
+      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64) tiles_tc.push_back(tile(c, r0, 128, c0, 0));
   sw.n_tiles_tc = (int)tiles_tc.size();
   upload(sw.tiles_tc, tiles_tc, s);
   std::vector<int4> tiles_tc256;
   for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 128)
-      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 256)
-        tiles_tc256.push_back(make_int4(c, r0, sw.class_first[c] + c0, sw.class_count[c] - c0));
+      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 256) tiles_tc256.push_back(tile(c, r0, 128, c0, 0));
   sw.n_tiles_tc256 = (int)tiles_tc256.size();
   upload(sw.tiles_tc256, tiles_tc256, s);
   std::vector<int4> units;

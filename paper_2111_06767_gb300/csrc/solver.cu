@@ -186,8 +186,8 @@ const float* Ihi<float>(dg_domain* dom) { return dom->Ihi32.get(); }
 }  // namespace
 
 template <typename T>
-void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int nS, const int4* d_tiles, int n_tiles, T alpha,
-                             cudaStream_t s, int split);
+void launch_class_gemm_tiles(const T* inv, const T* X, T* Y, int ld, const int4* d_tiles, int n_tiles,
+                             const int* d_kchunks, T alpha, cudaStream_t s, int split);
 
 namespace {
 // The CUDA-core class GEMM with its K split tuned per level and precision on first use (0, the
@@ -197,7 +197,7 @@ void simt_class_gemm(Level& L, const T* inv, const T* X, T* Y, T alpha, cudaStre
   const SchwarzLevel& sw = L.sw;
   int& pick = L.simt_split[sizeof(T) == 8];
   auto run = [&](int split) {
-    launch_class_gemm_tiles<T>(inv, X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, alpha, s, split);
+    launch_class_gemm_tiles<T>(inv, X, Y, sw.ld, sw.tiles.get(), sw.n_tiles, sw.kchunks16.get(), alpha, s, split);
   };
   if (pick < 0) {
     std::vector<int> cand{0};
@@ -254,7 +254,8 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
       const bool wide = (shape & kWide) != 0;
       launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E,
                            wide ? sw.tiles_tc256.get() : sw.tiles_tc.get(), wide ? sw.n_tiles_tc256 : sw.n_tiles_tc,
-                           dom->err_flag.get(), (float)sw.inv_scale, s, shape & 15, wide ? 256 : 64);
+                           sw.kchunks32.get(), dom->err_flag.get(), (float)sw.inv_scale, s, shape & 15,
+                           wide ? 256 : 64);
     };
     if (L.gemm_split < 0) {
       // the default (0) first, then every split the shape allows, at both tile widths
@@ -354,8 +355,9 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
     const bool linearized = linearized_level;
     auto gemm = [&](const T* X, T* Y) {
       const double isz = (sizeof(T) == 4 && sw.inv16.get()) ? 2.0 : sz;  // FP16-stored inverses
-      PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, (double)sw.n_classes * sw.nS * sw.nS * isz + 2 * vec,
-                    2.0 * sw.nS * (double)sw.nS * L.E);
+      // algorithmic: each class's inverse and vectors at its real subdomain size (slots present)
+      PhaseScope ps(dom->prof, DG_PHASE_SUBDOMAIN_GEMM, s, sw.alg_inv * isz + 2.0 * sw.alg_vec * sz,
+                    2.0 * sw.alg_mac);
       class_gemm<T>(dom, L, X, Y, s);
     };
     if (!linearized) {

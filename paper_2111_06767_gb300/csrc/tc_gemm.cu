@@ -7,7 +7,9 @@
 // its inverse once): TMA streams 128 x 32 tiles of Inv_c and BN x 32 tiles of X (128-byte swizzle)
 // into a 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = BN, K = 8
 // per instruction) accumulating in tensor memory, and the four warps read the accumulator back with
-// tcgen05.ld and store it column-contiguously. When the tiles alone cannot fill the GPU, the K
+// tcgen05.ld and store it column-contiguously. Only the K chunks that meet a slot of the subdomain
+// present in the class are streamed (the slots of missing neighbours have zero coupling), and
+// tiles whose rows lie only in such slots write zeros without a K loop. When the tiles alone cannot fill the GPU, the K
 // range is split across a cluster of 2, 4 or 8 CTAs and the partial tiles are summed through
 // distributed shared memory in a fixed order. Every wait is bounded: on timeout the CTA raises an
 // error flag, drains and frees its tensor memory.
@@ -160,8 +162,8 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
 template <int SPLIT, int BN>
 __global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   float* __restrict__ Y, int ld, const int4* __restrict__ tiles, int* __restrict__ err,
-                   float alpha) {
+                   float* __restrict__ Y, int ld, const int4* __restrict__ tiles, const int* __restrict__ kchunks,
+                   int* __restrict__ err, float alpha) {
   using SH = TcShape<BN>;
   constexpr int B_BYTES = SH::B_BYTES, STAGE_BYTES = SH::STAGE_BYTES, TMEM_COLS = SH::TMEM_COLS;
   extern __shared__ unsigned char smem_raw[];
@@ -175,11 +177,15 @@ __global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
 
   const int split = SPLIT > 1 ? (int)cluster_rank() : 0;
   const int4 tile = tiles[blockIdx.x / SPLIT];
-  const int cls = tile.x, row0 = tile.y, col0 = tile.z, ncol = min(tile.w, BN);
+  const int cls = tile.x & 0xFFFF, row0 = tile.y, col0 = tile.z, ncol = min(tile.w, BN);
+  const bool zero = (tile.x >> 30) & 1;  // rows only in the slots of missing neighbours: zeros
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk_all = ld / BK;
+  // the K chunks of this class that meet a present slot (the rest of the inverse's row is zero)
+  const int* kl = kchunks + (size_t)cls * (ld / BK + 1);
+  const int nk_all = zero ? 0 : kl[0];
   const int kc0 = split * nk_all / SPLIT, kc1 = (split + 1) * nk_all / SPLIT;
   const int nk = kc1 - kc0;
+  ++kl;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
 
   if (threadIdx.x == 0) {
@@ -212,8 +218,9 @@ __global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
       const int s = kc % STAGES;
       if (kc >= STAGES && !mbar_wait(empty0 + 8 * s, ((kc / STAGES) & 1) ^ 1, err)) break;
       mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-      tma_load_3d(smem_u32(sA + s * A_BYTES), &mapA, full0 + 8 * s, (kc0 + kc) * BK, row0, cls);
-      tma_load_2d(smem_u32(sB + s * B_BYTES), &mapB, full0 + 8 * s, (kc0 + kc) * BK, col0);
+      const int k0 = kl[kc0 + kc] * BK;
+      tma_load_3d(smem_u32(sA + s * A_BYTES), &mapA, full0 + 8 * s, k0, row0, cls);
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &mapB, full0 + 8 * s, k0, col0);
       *s_issued = kc + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -238,16 +245,17 @@ __global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int r_local = warp * 32 + lane;
   const int row = row0 + r_local;
+  const bool acc = nk > 0;  // the accumulator holds a product (else this CTA's part is zero)
   if (SPLIT == 1) {
 #pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 16) {
       if (!ok) break;
       uint32_t v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (acc) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
       if (row < ld) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j < ncol) Y[(size_t)(col0 + c0 + j) * ld + row] = alpha * __uint_as_float(v[j]);
+          if (c0 + j < ncol) Y[(size_t)(col0 + c0 + j) * ld + row] = acc ? alpha * __uint_as_float(v[j]) : 0.0f;
       }
     }
   } else {
@@ -256,9 +264,9 @@ __global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
 #pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t v[16];
-      if (ok) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (ok && acc) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) part[(c0 + j) * BM + r_local] = ok ? __uint_as_float(v[j]) : 0.0f;
+      for (int j = 0; j < 16; ++j) part[(c0 + j) * BM + r_local] = ok && acc ? __uint_as_float(v[j]) : 0.0f;
     }
     cluster_sync();
     constexpr int CPR = BN / SPLIT;  // columns reduced by this CTA
@@ -358,7 +366,7 @@ void set_smem_attributes() {
 
 template <int BN>
 void launch_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols, const int4* d_tiles,
-               int n_tiles, int* err, float alpha, cudaStream_t s, int split) {
+               int n_tiles, const int* d_kchunks, int* err, float alpha, cudaStream_t s, int split) {
   using SH = TcShape<BN>;
   const cuuint64_t dA[3] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)n_classes};
   const cuuint64_t sAr[2] = {(cuuint64_t)ld * 4, (cuuint64_t)ld * ld * 4};
@@ -393,22 +401,23 @@ void launch_tc(const float* inv, int n_classes, const float* X, float* Y, int ld
   const bool pdl = pdl_enabled();
   cfg.attrs = pdl ? at : at + 1;
   cfg.numAttrs = (pdl ? 1 : 0) + (split == 1 ? 0 : 1);
-  if (split == 1) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
-  else if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<2, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
-  else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
-  else DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8, BN>, mA, mB, Y, ld, d_tiles, err, alpha));
+  if (split == 1) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, BN>, mA, mB, Y, ld, d_tiles, d_kchunks, err, alpha));
+  else if (split == 2) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<2, BN>, mA, mB, Y, ld, d_tiles, d_kchunks, err, alpha));
+  else if (split == 4) DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4, BN>, mA, mB, Y, ld, d_tiles, d_kchunks, err, alpha));
+  else DG_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8, BN>, mA, mB, Y, ld, d_tiles, d_kchunks, err, alpha));
   DG_LAUNCHED(1);
 }
 
 }  // namespace
 
 void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float* Y, int ld, int n_cols,
-                          const int4* d_tiles, int n_tiles, int* err, float alpha, cudaStream_t s, int split, int bn) {
+                          const int4* d_tiles, int n_tiles, const int* d_kchunks, int* err, float alpha,
+                          cudaStream_t s, int split, int bn) {
   if (n_tiles == 0) return;
   DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
   DG_REQUIRE(bn == 64 || bn == 256, "tensor-core GEMM tile width must be 64 or 256");
-  if (bn == 256) launch_tc<256>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, err, alpha, s, split);
-  else launch_tc<64>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, err, alpha, s, split);
+  if (bn == 256) launch_tc<256>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, d_kchunks, err, alpha, s, split);
+  else launch_tc<64>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, d_kchunks, err, alpha, s, split);
 }
 
 }  // namespace dg

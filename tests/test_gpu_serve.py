@@ -146,7 +146,7 @@ def test_cancel_waiting_and_running_requests():
     Krylov iteration), a queued one is cancelled before admission, and the remaining request is
     served as if alone; tickets that were never issued report NOT_FOUND."""
     srv = dgg.Server(max_active=1, n_streams=1)
-    long_desc, long_f = _request("poisson", 8, 8, 30)  # FP64 8^3, N = 8: a few hundred ms
+    long_desc, long_f = _request("poisson", 12, 8, 30)  # FP64 12^3, N = 8: over a second with its set-up
     short_desc, short_f = _request("poisson", 2, 4, 31)
     t_long = srv.submit(long_desc, long_f, tol=1e-10)
     t_queued = srv.submit(short_desc, short_f, tol=1e-10)
