@@ -79,6 +79,13 @@ PdlScope::PdlScope(bool on_) : on(on_) {
 PdlScope::~PdlScope() {
   if (on) --tl_pdl_scope;
 }
+bool pdl_krylov_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("DG_PDL_KRYLOV");
+    return !(v && std::strcmp(v, "0") == 0);
+  }();
+  return on;
+}
 int pdl_vcycle_mode() {
   static const int mode = [] {
     const char* v = std::getenv("DG_PDL_COARSE");

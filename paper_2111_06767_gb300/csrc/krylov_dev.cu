@@ -10,6 +10,7 @@
 // (per-block partial sums over the same chunks, summed in the same order), so the inner products,
 // and with them the Krylov basis, are the same bit for bit.
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace dg {
 
@@ -23,6 +24,8 @@ inline int grid_for(int64_t n) {
 // r0 = ||b - A x0||, reference norm, g_0 = beta, V_0 scale; sets the loop condition.
 __global__ void kr_start_kernel(KrylovState* st, double tol, int max_it, int rel_to_b, const double* __restrict__ nrm2,
                                 double* __restrict__ g, cudaGraphConditionalHandle loop) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->tol = tol;
   st->max_it = max_it;
@@ -48,6 +51,8 @@ __global__ void kr_start_kernel(KrylovState* st, double tol, int max_it, int rel
 // V_j = scale x while the loop runs (j and scale from the state)
 __global__ void kr_scale_into_v_kernel(int64_t n, const double* __restrict__ x, const KrylovState* __restrict__ st,
                                        double* __restrict__ V, int64_t ld) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   if (st->status != KR_RUNNING) return;
   const double a = st->scale;
   double* v = V + (int64_t)st->j * ld;
@@ -59,6 +64,8 @@ __global__ void kr_scale_into_v_kernel(int64_t n, const double* __restrict__ x, 
 template <typename T>
 __global__ void kr_load_v_kernel(int64_t n, const double* __restrict__ V, int64_t ld,
                                  const KrylovState* __restrict__ st, T* __restrict__ out) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   const double* v = V + (int64_t)st->j * ld;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (T)v[i];
@@ -69,6 +76,8 @@ __global__ void kr_load_v_kernel(int64_t n, const double* __restrict__ V, int64_
 template <typename T>
 __global__ void kr_store_z_kernel(int64_t n, const T* __restrict__ z, const KrylovState* __restrict__ st,
                                   double* __restrict__ Z, int64_t ld, double* __restrict__ zfix) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   double* zj = Z + (int64_t)st->j * ld;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = (double)z[i];
@@ -82,6 +91,8 @@ __global__ void kr_store_z_kernel(int64_t n, const T* __restrict__ z, const Kryl
 __global__ void kr_multidot_partial_kernel(int64_t n, const double* __restrict__ V, int64_t ld,
                                            const double* __restrict__ w, const KrylovState* __restrict__ st,
                                            double* __restrict__ partial, int blocks) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   const int k = blockIdx.y;
   if (k > st->j) return;
   __shared__ double red[kThreads / 32];
@@ -103,6 +114,8 @@ __global__ void kr_multidot_partial_kernel(int64_t n, const double* __restrict__
 
 __global__ void kr_multidot_final_kernel(const double* __restrict__ partial, const KrylovState* __restrict__ st,
                                          double* __restrict__ out, int blocks) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   const int k = blockIdx.x;
   if (k > st->j) return;
   __shared__ double red[kThreads / 32];
@@ -122,6 +135,8 @@ __global__ void kr_multidot_final_kernel(const double* __restrict__ partial, con
 // w -= sum_{k <= j} h[k] V_k
 __global__ void kr_sub_comb_kernel(int64_t n, const double* __restrict__ V, int64_t ld, const double* __restrict__ h,
                                    const KrylovState* __restrict__ st, double* __restrict__ w) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   const int m = st->j + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double acc = w[i];
@@ -137,6 +152,8 @@ __global__ void kr_givens_kernel(KrylovState* st, double* __restrict__ H, int ld
                                  double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ h1,
                                  const double* __restrict__ h2, const double* __restrict__ nrm2,
                                  const volatile int* cancel, cudaGraphConditionalHandle loop) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (st->status != KR_RUNNING) {
     cudaGraphSetConditional(loop, 0u);
@@ -183,6 +200,8 @@ __global__ void kr_givens_kernel(KrylovState* st, double* __restrict__ H, int ld
 // y = R^-1 g over the k completed columns (back substitution). One thread.
 __global__ void kr_trisolve_kernel(const KrylovState* __restrict__ st, const double* __restrict__ H, int ldh,
                                    const double* __restrict__ g, double* __restrict__ y) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int k = st->k;
   for (int i = k - 1; i >= 0; --i) {
@@ -195,6 +214,8 @@ __global__ void kr_trisolve_kernel(const KrylovState* __restrict__ st, const dou
 // x += sum_{l < k} y[l] Z_l
 __global__ void kr_add_comb_kernel(int64_t n, const double* __restrict__ Z, int64_t ld, const double* __restrict__ y,
                                    const KrylovState* __restrict__ st, double* __restrict__ x) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   const int m = st->k;
   if (m == 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -205,10 +226,15 @@ __global__ void kr_add_comb_kernel(int64_t n, const double* __restrict__ Z, int6
 }
 
 // ------------------------------------------------------------------ launchers
+//
+// Every kernel above waits for its predecessor (griddepcontrol.wait) before touching the state or
+// the vectors, so they are launched with programmatic dependent launch unless DG_PDL_KRYLOV=0:
+// each one's launch and set-up overlap the previous kernel.
 
 void launch_kr_start(KrylovState* st, double tol, int max_it, bool rel_to_b, const double* nrm2, double* g,
                      cudaGraphConditionalHandle loop, cudaStream_t s) {
-  kr_start_kernel<<<1, 32, 0, s>>>(st, tol, max_it, rel_to_b ? 1 : 0, nrm2, g, loop);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_start_kernel, dim3(1), dim3(32), 0, s, st, tol, max_it, rel_to_b ? 1 : 0, nrm2, g, loop);
   DG_LAUNCHED(1);
 }
 
@@ -216,6 +242,8 @@ void launch_kr_start(KrylovState* st, double tol, int max_it, bool rel_to_b, con
 // ||b - A x0||, the reference norm, the final ||b - A x||, the stopping threshold.
 __global__ void kr_report_kernel(const KrylovState* __restrict__ st, const double* __restrict__ nrm2,
                                  double* __restrict__ out) {
+  pdl_launch_dependents();
+  pdl_wait();  // the state and vectors come from the previous kernel
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   out[0] = st->k;
   out[1] = st->status;
@@ -227,16 +255,19 @@ __global__ void kr_report_kernel(const KrylovState* __restrict__ st, const doubl
   out[7] = 0.0;
 }
 void launch_kr_report(const KrylovState* st, const double* nrm2, double* out, cudaStream_t s) {
-  kr_report_kernel<<<1, 32, 0, s>>>(st, nrm2, out);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_report_kernel, dim3(1), dim3(32), 0, s, st, nrm2, out);
   DG_LAUNCHED(1);
 }
 void launch_kr_scale_into_v(int64_t n, const double* x, const KrylovState* st, double* V, int64_t ld, cudaStream_t s) {
-  kr_scale_into_v_kernel<<<grid_for(n), kThreads, 0, s>>>(n, x, st, V, ld);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_scale_into_v_kernel, dim3(grid_for(n)), dim3(kThreads), 0, s, n, x, st, V, ld);
   DG_LAUNCHED(1);
 }
 template <typename T>
 void launch_kr_load_v(int64_t n, const double* V, int64_t ld, const KrylovState* st, T* out, cudaStream_t s) {
-  kr_load_v_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, V, ld, st, out);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_load_v_kernel<T>, dim3(grid_for(n)), dim3(kThreads), 0, s, n, V, ld, st, out);
   DG_LAUNCHED(1);
 }
 template void launch_kr_load_v<float>(int64_t, const double*, int64_t, const KrylovState*, float*, cudaStream_t);
@@ -244,7 +275,8 @@ template void launch_kr_load_v<double>(int64_t, const double*, int64_t, const Kr
 template <typename T>
 void launch_kr_store_z(int64_t n, const T* z, const KrylovState* st, double* Z, int64_t ld, double* zfix,
                        cudaStream_t s) {
-  kr_store_z_kernel<T><<<grid_for(n), kThreads, 0, s>>>(n, z, st, Z, ld, zfix);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_store_z_kernel<T>, dim3(grid_for(n)), dim3(kThreads), 0, s, n, z, st, Z, ld, zfix);
   DG_LAUNCHED(1);
 }
 template void launch_kr_store_z<float>(int64_t, const float*, const KrylovState*, double*, int64_t, double*,
@@ -253,29 +285,35 @@ template void launch_kr_store_z<double>(int64_t, const double*, const KrylovStat
                                         cudaStream_t);
 void launch_kr_multidot(int64_t n, int cap, const double* V, int64_t ld, const double* w, const KrylovState* st,
                         double* partial, double* out, cudaStream_t s) {
+  const PdlScope pdl(pdl_krylov_enabled());
   const int blocks = multidot_partial_blocks();
-  kr_multidot_partial_kernel<<<dim3(blocks, cap), kThreads, 0, s>>>(n, V, ld, w, st, partial, blocks);
-  kr_multidot_final_kernel<<<cap, kThreads, 0, s>>>(partial, st, out, blocks);
+  launch_pdl(kr_multidot_partial_kernel, dim3(blocks, cap), dim3(kThreads), 0, s, n, V, ld, w, st, partial,
+             blocks);
+  launch_pdl(kr_multidot_final_kernel, dim3(cap), dim3(kThreads), 0, s, partial, st, out, blocks);
   DG_LAUNCHED(2);
 }
 void launch_kr_sub_comb(int64_t n, const double* V, int64_t ld, const double* h, const KrylovState* st, double* w,
                         cudaStream_t s) {
-  kr_sub_comb_kernel<<<grid_for(n), kThreads, 0, s>>>(n, V, ld, h, st, w);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_sub_comb_kernel, dim3(grid_for(n)), dim3(kThreads), 0, s, n, V, ld, h, st, w);
   DG_LAUNCHED(1);
 }
 void launch_kr_givens(KrylovState* st, double* H, int ldh, double* cs, double* sn, double* g, const double* h1,
                       const double* h2, const double* nrm2, const volatile int* cancel,
                       cudaGraphConditionalHandle loop, cudaStream_t s) {
-  kr_givens_kernel<<<1, 32, 0, s>>>(st, H, ldh, cs, sn, g, h1, h2, nrm2, cancel, loop);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_givens_kernel, dim3(1), dim3(32), 0, s, st, H, ldh, cs, sn, g, h1, h2, nrm2, cancel, loop);
   DG_LAUNCHED(1);
 }
 void launch_kr_trisolve(const KrylovState* st, const double* H, int ldh, const double* g, double* y, cudaStream_t s) {
-  kr_trisolve_kernel<<<1, 32, 0, s>>>(st, H, ldh, g, y);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_trisolve_kernel, dim3(1), dim3(32), 0, s, st, H, ldh, g, y);
   DG_LAUNCHED(1);
 }
 void launch_kr_add_comb(int64_t n, const double* Z, int64_t ld, const double* y, const KrylovState* st, double* x,
                         cudaStream_t s) {
-  kr_add_comb_kernel<<<grid_for(n), kThreads, 0, s>>>(n, Z, ld, y, st, x);
+  const PdlScope pdl(pdl_krylov_enabled());
+  launch_pdl(kr_add_comb_kernel, dim3(grid_for(n)), dim3(kThreads), 0, s, n, Z, ld, y, st, x);
   DG_LAUNCHED(1);
 }
 
