@@ -79,10 +79,14 @@ PdlScope::PdlScope(bool on_) : on(on_) {
 PdlScope::~PdlScope() {
   if (on) --tl_pdl_scope;
 }
+// Off unless DG_PDL_KRYLOV=1: on the 8^3, N = 8 workload it gained 0.4 % for one solve at a time
+// (194.0 -> 194.8 solves/s) but cost concurrent solves much more (a 512-solve batched graph 600 ->
+// 516 solves/s, 8 streams 370 -> 341): the next vector kernel's ~1200 CTAs wait on the SMs that
+// other solves' kernels would use.
 bool pdl_krylov_enabled() {
   static const bool on = [] {
     const char* v = std::getenv("DG_PDL_KRYLOV");
-    return !(v && std::strcmp(v, "0") == 0);
+    return v && std::strcmp(v, "1") == 0;
   }();
   return on;
 }

@@ -61,7 +61,7 @@ struct PdlScope {
   PdlScope& operator=(const PdlScope&) = delete;
 };
 int pdl_vcycle_mode();
-bool pdl_krylov_enabled();  // the device-resident FGMRES kernels (DG_PDL_KRYLOV=0 turns it off)
+bool pdl_krylov_enabled();  // the device-resident FGMRES kernels (DG_PDL_KRYLOV=1 turns it on)
 
 struct AllocStreamScope {
   cudaStream_t prev;

@@ -228,8 +228,8 @@ __global__ void kr_add_comb_kernel(int64_t n, const double* __restrict__ Z, int6
 // ------------------------------------------------------------------ launchers
 //
 // Every kernel above waits for its predecessor (griddepcontrol.wait) before touching the state or
-// the vectors, so they are launched with programmatic dependent launch unless DG_PDL_KRYLOV=0:
-// each one's launch and set-up overlap the previous kernel.
+// the vectors, so they can be launched with programmatic dependent launch (DG_PDL_KRYLOV=1; off by
+// default, see pdl_krylov_enabled).
 
 void launch_kr_start(KrylovState* st, double tol, int max_it, bool rel_to_b, const double* nrm2, double* g,
                      cudaGraphConditionalHandle loop, cudaStream_t s) {
