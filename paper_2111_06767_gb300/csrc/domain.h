@@ -39,6 +39,8 @@ struct SchwarzLevel {
   double alg_inv = 0, alg_vec = 0, alg_mac = 0;  // sum_c nS_c^2, sum_c E_c nS_c, sum_c E_c nS_c^2
   DevBuf<int4> tiles_tc;           // tensor-core GEMM tiles: 128 rows x 64 columns
   int n_tiles_tc = 0;
+  DevBuf<int4> tiles_tc128;        // tensor-core GEMM tiles: 128 rows x 128 columns
+  int n_tiles_tc128 = 0;
   DevBuf<int4> tiles_tc256;        // tensor-core GEMM tiles: 128 rows x 256 columns (one read of a
   int n_tiles_tc256 = 0;           //   128-row slab of the inverse per class of at most 256 columns)
   DevBuf<int4> units;              // fused coarse smoother GEMM units: 16 rows x all columns of a class

@@ -630,6 +630,33 @@ __device__ __forceinline__ T warp_total(T v) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// 16-byte vector moves of a column's values (the register forms of the kernels below)
+template <typename T>
+struct SubVec;
+template <>
+struct SubVec<float> {
+  using V = float4;
+  static constexpr int E = 4;
+  static __device__ __forceinline__ void ld(const float* p, float (&r)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&r)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+};
+template <>
+struct SubVec<double> {
+  static constexpr int E = 2;
+  static __device__ __forceinline__ void ld(const double* p, double (&r)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double (&r)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+  }
+};
+
 // V_0 = r_S / ||r_S|| per column; beta[col] = ||r_S||
 template <typename T>
 __global__ void __launch_bounds__(32 * kSubWarps)
@@ -686,7 +713,7 @@ __global__ void __launch_bounds__(32 * kSubWarps)
 }
 
 // y = argmin || beta e1 - H y || (Givens, by lane 0 of the column's warp), then du_S = sum_j y_j Z_j.
-template <typename T>
+template <typename T, int G = 0>
 __global__ void __launch_bounds__(32 * kSubWarps)
     sub_lsq_combine_kernel(int E, int nS, int64_t stride, int m, const T* __restrict__ beta,
                            const T* __restrict__ H, const T* __restrict__ Z, T* __restrict__ duS) {
@@ -728,31 +755,204 @@ __global__ void __launch_bounds__(32 * kSubWarps)
   }
   __syncwarp();
   const size_t off = (size_t)col * nS;
-  for (int t = lane; t < nS; t += 32) {
-    T acc = 0;
-    for (int c = 0; c < m; ++c) acc += y[c] * Z[(size_t)c * stride + off + t];
-    duS[off + t] = acc;
+  if constexpr (G == 0) {
+    for (int t = lane; t < nS; t += 32) {
+      T acc = 0;
+      for (int c = 0; c < m; ++c) acc += y[c] * Z[(size_t)c * stride + off + t];
+      duS[off + t] = acc;
+    }
+  } else {
+    // 16-byte vectors per lane, as the register forms of the other two kernels
+    using SV = SubVec<T>;
+    constexpr int EV = SV::E;
+    T acc[G][EV] = {};
+    for (int c = 0; c < m; ++c) {
+      const T yc = y[c];
+      const T* zc = Z + (size_t)c * stride + off;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int i = (g * 32 + lane) * EV;
+        if (i >= nS) continue;
+        T z[EV];
+        SV::ld(zc + i, z);
+#pragma unroll
+        for (int e = 0; e < EV; ++e) acc[g][e] += yc * z[e];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int i = (g * 32 + lane) * EV;
+      if (i < nS) SV::st(duS + off + i, acc[g]);
+    }
   }
+}
+
+// Register-resident forms of the two per-subdomain kernels above: a warp keeps its column's w
+// (and the current V_i) in registers as G 16-byte vectors per lane (lane l holds elements
+// 16/sizeof(T) x (32 g + l) + 0..), so every vector of the column is read or written once per call
+// with 16-byte coalesced accesses instead of once per Gram-Schmidt pass. Same operations in the
+// same order per element as the kernels above; only the partial sums of each inner product are
+// grouped differently across the lanes.
+template <typename T, int G>
+__global__ void __launch_bounds__(32 * kSubWarps)
+    sub_normalize_reg_kernel(int E, int ld, const T* __restrict__ rS, T* __restrict__ V0, T* __restrict__ beta) {
+  using SV = SubVec<T>;
+  constexpr int EV = SV::E;
+  const int col = blockIdx.x * kSubWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (col >= E) return;  // whole warps
+  const size_t off = (size_t)col * ld;
+  T r[G][EV];
+  T acc = 0;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int i = (g * 32 + lane) * EV;
+    if (i < ld) SV::ld(rS + off + i, r[g]);
+    else
+#pragma unroll
+      for (int e = 0; e < EV; ++e) r[g][e] = 0;
+#pragma unroll
+    for (int e = 0; e < EV; ++e) acc += r[g][e] * r[g][e];
+  }
+  const T nrm = sqrt(warp_total(acc));
+  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int i = (g * 32 + lane) * EV;
+    if (i >= ld) continue;
+#pragma unroll
+    for (int e = 0; e < EV; ++e) r[g][e] *= inv;
+    SV::st(V0 + off + i, r[g]);
+  }
+  if (lane == 0) beta[col] = nrm;
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(32 * kSubWarps)
+    sub_arnoldi_reg_kernel(int E, int ld, int64_t stride, int j, int m, const T* __restrict__ D, T* V,
+                           const T* __restrict__ Z, T* __restrict__ H) {
+  using SV = SubVec<T>;
+  constexpr int EV = SV::E;
+  const int col = blockIdx.x * kSubWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (col >= E) return;  // whole warps
+  const size_t off = (size_t)col * ld;
+  const T* vj = V + (size_t)j * stride + off;
+  const T* zj = Z + (size_t)j * stride + off;
+  T w[G][EV];
+  T acc0 = 0;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int i = (g * 32 + lane) * EV;
+    if (i < ld) {
+      T a[EV], d[EV], z[EV];
+      SV::ld(vj + i, a);
+      SV::ld(D + off + i, d);
+      SV::ld(zj + i, z);
+#pragma unroll
+      for (int e = 0; e < EV; ++e) w[g][e] = a[e] + d[e] * z[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < EV; ++e) w[g][e] = 0;
+    }
+#pragma unroll
+    for (int e = 0; e < EV; ++e) acc0 += w[g][e] * w[g][e];
+  }
+  const T w0 = sqrt(warp_total(acc0));  // ||w|| before orthogonalisation
+  T* h = H + (size_t)col * (m + 1) * m;
+  for (int ii = 0; ii <= j; ++ii) {
+    const T* vi = V + (size_t)ii * stride + off;
+    T v[G][EV];
+    T acc = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int i = (g * 32 + lane) * EV;
+      if (i < ld) SV::ld(vi + i, v[g]);
+      else
+#pragma unroll
+        for (int e = 0; e < EV; ++e) v[g][e] = 0;
+#pragma unroll
+      for (int e = 0; e < EV; ++e) acc += w[g][e] * v[g][e];
+    }
+    const T hij = warp_total(acc);
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int e = 0; e < EV; ++e) w[g][e] -= hij * v[g][e];
+    if (lane == 0) h[ii * m + j] = hij;
+  }
+  T acc = 0;
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int e = 0; e < EV; ++e) acc += w[g][e] * w[g][e];
+  T hn = sqrt(warp_total(acc));
+  // rounding noise after orthogonalisation is a (happy) breakdown, as in sub_arnoldi_kernel
+  if (hn <= T(64) * std::numeric_limits<T>::epsilon() * w0) hn = T(0);
+  if (lane == 0) h[(j + 1) * m + j] = hn;
+  const T inv = hn > T(0) ? T(1) / hn : T(0);
+  T* wout = V + (size_t)(j + 1) * stride + off;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int i = (g * 32 + lane) * EV;
+    if (i >= ld) continue;
+#pragma unroll
+    for (int e = 0; e < EV; ++e) w[g][e] *= inv;
+    SV::st(wout + i, w[g]);
+  }
+}
+
+// 16-byte vectors per lane a column of ld values needs, rounded up to an instantiated count (0: the
+// column is too long for the register forms)
+template <typename T>
+int sub_reg_groups(int ld) {
+  if (ld % (16 / (int)sizeof(T)) != 0) return 0;
+  const int g = (ld + 32 * (16 / (int)sizeof(T)) - 1) / (32 * (16 / (int)sizeof(T)));
+  for (int c : {1, 2, 3, 4, 6, 8, 10, 12, 14, 16})
+    if (g <= c) return c;
+  return 0;
 }
 
 template <typename T>
 void launch_sub_normalize(int E, int nS, const T* rS, T* V0, T* beta, cudaStream_t s) {
   if (E == 0) return;
-  sub_normalize_kernel<T><<<(E + kSubWarps - 1) / kSubWarps, 32 * kSubWarps, 0, s>>>(E, nS, rS, V0, beta);
+  const dim3 grid((E + kSubWarps - 1) / kSubWarps), block(32 * kSubWarps);
+  switch (sub_reg_groups<T>(nS)) {
+#define DG_SUB_NORM(GG) \
+  case GG: sub_normalize_reg_kernel<T, GG><<<grid, block, 0, s>>>(E, nS, rS, V0, beta); break;
+    DG_SUB_NORM(1) DG_SUB_NORM(2) DG_SUB_NORM(3) DG_SUB_NORM(4) DG_SUB_NORM(6) DG_SUB_NORM(8) DG_SUB_NORM(10)
+    DG_SUB_NORM(12) DG_SUB_NORM(14) DG_SUB_NORM(16)
+#undef DG_SUB_NORM
+    default: sub_normalize_kernel<T><<<grid, block, 0, s>>>(E, nS, rS, V0, beta);
+  }
   DG_LAUNCHED(1);
 }
 template <typename T>
 void launch_sub_arnoldi(int E, int nS, int j, int m, const T* D, T* V, const T* Z, T* H, cudaStream_t s) {
   if (E == 0) return;
-  sub_arnoldi_kernel<T><<<(E + kSubWarps - 1) / kSubWarps, 32 * kSubWarps, 0, s>>>(E, nS, (int64_t)E * nS, j, m, D, V,
-                                                                                  Z, H);
+  const dim3 grid((E + kSubWarps - 1) / kSubWarps), block(32 * kSubWarps);
+  const int64_t stride = (int64_t)E * nS;
+  switch (sub_reg_groups<T>(nS)) {
+#define DG_SUB_ARN(GG) \
+  case GG: sub_arnoldi_reg_kernel<T, GG><<<grid, block, 0, s>>>(E, nS, stride, j, m, D, V, Z, H); break;
+    DG_SUB_ARN(1) DG_SUB_ARN(2) DG_SUB_ARN(3) DG_SUB_ARN(4) DG_SUB_ARN(6) DG_SUB_ARN(8) DG_SUB_ARN(10)
+    DG_SUB_ARN(12) DG_SUB_ARN(14) DG_SUB_ARN(16)
+#undef DG_SUB_ARN
+    default: sub_arnoldi_kernel<T><<<grid, block, 0, s>>>(E, nS, stride, j, m, D, V, Z, H);
+  }
   DG_LAUNCHED(1);
 }
 template <typename T>
 void launch_sub_lsq_combine(int E, int nS, int m, const T* beta, const T* H, const T* Z, T* duS, cudaStream_t s) {
   if (E == 0) return;
-  sub_lsq_combine_kernel<T><<<(E + kSubWarps - 1) / kSubWarps, 32 * kSubWarps, 0, s>>>(E, nS, (int64_t)E * nS, m, beta,
-                                                                                      H, Z, duS);
+  const dim3 grid((E + kSubWarps - 1) / kSubWarps), block(32 * kSubWarps);
+  const int64_t stride = (int64_t)E * nS;
+  switch (sub_reg_groups<T>(nS)) {
+#define DG_SUB_LSQ(GG) \
+  case GG: sub_lsq_combine_kernel<T, GG><<<grid, block, 0, s>>>(E, nS, stride, m, beta, H, Z, duS); break;
+    DG_SUB_LSQ(1) DG_SUB_LSQ(2) DG_SUB_LSQ(3) DG_SUB_LSQ(4) DG_SUB_LSQ(6) DG_SUB_LSQ(8) DG_SUB_LSQ(10)
+    DG_SUB_LSQ(12) DG_SUB_LSQ(14) DG_SUB_LSQ(16)
+#undef DG_SUB_LSQ
+    default: sub_lsq_combine_kernel<T><<<grid, block, 0, s>>>(E, nS, stride, m, beta, H, Z, duS);
+  }
   DG_LAUNCHED(1);
 }
 template void launch_sub_normalize<double>(int, int, const double*, double*, double*, cudaStream_t);

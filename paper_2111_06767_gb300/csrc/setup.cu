@@ -258,6 +258,12 @@ void classify_schwarz(dg_domain* dom, Level& L) {
       for (int c0 = 0; c0 < sw.class_count[c]; c0 += 64) tiles_tc.push_back(tile(c, r0, 128, c0, 0));
   sw.n_tiles_tc = (int)tiles_tc.size();
   upload(sw.tiles_tc, tiles_tc, s);
+  std::vector<int4> tiles_tc128;
+  for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
+    for (int r0 = 0; r0 < sw.ld; r0 += 128)
+      for (int c0 = 0; c0 < sw.class_count[c]; c0 += 128) tiles_tc128.push_back(tile(c, r0, 128, c0, 0));
+  sw.n_tiles_tc128 = (int)tiles_tc128.size();
+  upload(sw.tiles_tc128, tiles_tc128, s);
   std::vector<int4> tiles_tc256;
   for (int c = 0; c < (dom->curved ? 0 : nc); ++c)
     for (int r0 = 0; r0 < sw.ld; r0 += 128)
@@ -716,7 +722,7 @@ size_t domain_device_bytes(const dg_domain* dom) {
     b += sw.elem_of_col.bytes() + sw.col_of_elem.bytes() + sw.class_of_col.bytes() + sw.xform_of_elem.bytes() +
          sw.inv64.bytes() +
          sw.inv32.bytes() + sw.inv16.bytes() + sw.inv16_scale.bytes() + sw.tiles.bytes() + sw.tiles_tc.bytes() +
-         sw.tiles_tc256.bytes() +
+         sw.tiles_tc128.bytes() + sw.tiles_tc256.bytes() +
          sw.units.bytes() + sw.bar.bytes();
     for (auto* p : {&L.w64.b, &L.w64.u, &L.w64.r, &L.w64.rS, &L.w64.duS, &L.w64.gV, &L.w64.gZ, &L.w64.gW, &L.w64.gD,
                     &L.w64.gH, &L.w64.linA, &L.w64.linv})

@@ -248,21 +248,23 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
   }
   if (dom->use_tc) {
     // launch shape: split-K factor (low 4 bits; 0 = chosen from the tile count) and tile width
-    // (kWide: 256 columns, else 64)
-    constexpr int kWide = 16;
+    // (kWide: 256 columns, kMid: 128, else 64)
+    constexpr int kWide = 16, kMid = 32;
     auto run = [&](int shape) {
-      const bool wide = (shape & kWide) != 0;
-      launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E,
-                           wide ? sw.tiles_tc256.get() : sw.tiles_tc.get(), wide ? sw.n_tiles_tc256 : sw.n_tiles_tc,
-                           sw.kchunks32.get(), dom->err_flag.get(), (float)sw.inv_scale, s, shape & 15,
-                           wide ? 256 : 64);
+      const int bn = (shape & kWide) ? 256 : ((shape & kMid) ? 128 : 64);
+      const int4* t = bn == 256 ? sw.tiles_tc256.get() : (bn == 128 ? sw.tiles_tc128.get() : sw.tiles_tc.get());
+      const int nt = bn == 256 ? sw.n_tiles_tc256 : (bn == 128 ? sw.n_tiles_tc128 : sw.n_tiles_tc);
+      launch_class_gemm_tc(sw.inv32.get(), sw.n_classes, X, Y, sw.ld, L.E, t, nt, sw.kchunks32.get(),
+                           dom->err_flag.get(), (float)sw.inv_scale, s, shape & 15, bn);
     };
     if (L.gemm_split < 0) {
-      // the default (0) first, then every split the shape allows, at both tile widths
+      // the default (0) first, then every split the shape allows, at every tile width
       std::vector<int> cand{0};
       for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(sp);
-      cand.push_back(kWide);
-      for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(kWide | sp);
+      for (int w : {kMid, kWide}) {
+        cand.push_back(w);
+        for (int sp : tc_gemm_splits(sw.ld)) cand.push_back(w | sp);
+      }
       // DG_GEMM_SPLIT=k pins one candidate (tests and measurements of each launch shape); read
       // when a level first runs its GEMM, so a process can set it per domain
       const char* e = std::getenv("DG_GEMM_SPLIT");
@@ -272,7 +274,8 @@ void class_gemm<float>(dg_domain* dom, Level& L, const float* X, float* Y, cudaS
         run(forced);
         return;
       }
-      const int pick = autotune({3, sw.n_classes, sw.ld, sw.n_tiles_tc, sw.n_tiles_tc256, L.E}, cand, run, s);
+      const int pick = autotune({3, sw.n_classes, sw.ld, sw.n_tiles_tc, sw.n_tiles_tc128, sw.n_tiles_tc256, L.E}, cand,
+                                run, s);
       cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
       DG_CUDA(cudaStreamIsCapturing(s, &cap));
       if (cap != cudaStreamCaptureStatusNone) {

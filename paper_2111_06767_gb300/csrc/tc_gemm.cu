@@ -3,16 +3,17 @@
 // du_S = A_S^-1 r_S for all subdomains of a class (Sec. III.E, explicit-inverse solver) is the one
 // dense contraction of the method: Y[:, cols] = Inv_c (ld x ld, row-major) * X[:, cols] with every
 // subdomain column of X contiguous. Both operands are K-major, so each CTA computes a 128 x BN
-// output tile (BN = 64, or 256 so that a class of at most 256 subdomains reads each 128-row slab of
-// its inverse once): TMA streams 128 x 32 tiles of Inv_c and BN x 32 tiles of X (128-byte swizzle)
-// into a 4-stage shared-memory ring, one elected thread issues tcgen05.mma (M = 128, N = BN, K = 8
-// per instruction) accumulating in tensor memory, and the four warps read the accumulator back with
-// tcgen05.ld and store it column-contiguously. Only the K chunks that meet a slot of the subdomain
-// present in the class are streamed (the slots of missing neighbours have zero coupling), and
-// tiles whose rows lie only in such slots write zeros without a K loop. When the tiles alone cannot fill the GPU, the K
-// range is split across a cluster of 2, 4 or 8 CTAs and the partial tiles are summed through
-// distributed shared memory in a fixed order. Every wait is bounded: on timeout the CTA raises an
-// error flag, drains and frees its tensor memory.
+// output tile (BN = 64, or 128 / 256 so that a class of at most that many subdomains reads each
+// 128-row slab of its inverse once): TMA streams 128 x 32 tiles of Inv_c and BN x 32 tiles of X
+// (128-byte swizzle) into a 3- or 4-stage shared-memory ring, one elected thread issues
+// tcgen05.mma (M = 128, N = BN, K = 8 per instruction) accumulating in tensor memory, and the four
+// warps read the accumulator back with tcgen05.ld and store it column-contiguously. Only the K
+// chunks that meet a slot of the subdomain present in the class are streamed (the slots of missing
+// neighbours have zero coupling), and tiles whose rows lie only in such slots write zeros without
+// a K loop. When the tiles alone cannot fill the GPU, the K range is split across a cluster of 2,
+// 4 or 8 CTAs and the partial tiles are summed through distributed shared memory in a fixed order.
+// Every wait is bounded: on timeout the CTA raises an error flag, drains and frees its tensor
+// memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,19 +27,20 @@ namespace dg {
 
 namespace {
 
-constexpr int BM = 128, BK = 32, STAGES = 4;
+constexpr int BM = 128, BK = 32;
 constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
 constexpr int SLACK = 8 * 1024;       // spare shared memory after the ring
 constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls before a wait gives up (far above any real wait)
 
-// Shape constants of the tile width BN (64 or 256).
+// Shape constants of the tile width BN (64, 128 or 256).
 template <int BN>
 struct TcShape {
-  static constexpr int B_BYTES = BN * BK * 4;  // 8 or 32 KiB
+  static constexpr int STAGES = BN == 128 ? 3 : 4;  // TMA ring depth (two CTAs per SM up to BN = 128)
+  static constexpr int B_BYTES = BN * BK * 4;  // 8, 16 or 32 KiB
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = BN < 128 ? 128 : BN;  // >= BN, a power of two
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 256;
-  static constexpr int PER_SM = BN <= 64 ? 2 : 1;      // co-resident CTAs per SM
+  static constexpr int PER_SM = BN <= 128 ? 2 : 1;     // co-resident CTAs per SM
   static constexpr int SLOTS = PER_SM * 152;
   // instruction descriptor: F32 accumulate, TF32 A and B, both K-major, N = BN, M = BM
   static constexpr uint32_t IDESC =
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(128, TcShape<BN>::PER_SM)
                    float* __restrict__ Y, int ld, const int4* __restrict__ tiles, const int* __restrict__ kchunks,
                    int* __restrict__ err, float alpha) {
   using SH = TcShape<BN>;
+  constexpr int STAGES = SH::STAGES;
   constexpr int B_BYTES = SH::B_BYTES, STAGE_BYTES = SH::STAGE_BYTES, TMEM_COLS = SH::TMEM_COLS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -415,8 +418,10 @@ void launch_class_gemm_tc(const float* inv, int n_classes, const float* X, float
                           cudaStream_t s, int split, int bn) {
   if (n_tiles == 0) return;
   DG_REQUIRE(ld % BK == 0, "tensor-core GEMM needs a 32-aligned subdomain stride");
-  DG_REQUIRE(bn == 64 || bn == 256, "tensor-core GEMM tile width must be 64 or 256");
+  DG_REQUIRE(bn == 64 || bn == 128 || bn == 256, "tensor-core GEMM tile width must be 64, 128 or 256");
   if (bn == 256) launch_tc<256>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, d_kchunks, err, alpha, s, split);
+  else if (bn == 128)
+    launch_tc<128>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, d_kchunks, err, alpha, s, split);
   else launch_tc<64>(inv, n_classes, X, Y, ld, n_cols, d_tiles, n_tiles, d_kchunks, err, alpha, s, split);
 }
 

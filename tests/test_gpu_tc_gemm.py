@@ -84,17 +84,17 @@ def test_autotuned_launch_shapes_match_fixed_ones(tmp_path):
 @pytest.mark.parametrize("n", [(4, 4, 4), (8, 8, 8)])
 def test_every_gemm_split_matches_simt(monkeypatch, n):
     """Each K split of the tensor-core GEMM (1, 2, 4 or 8 CTAs of a cluster, partial tiles summed
-    through distributed shared memory) at both tile widths (64 columns, and 256 columns: 16 + split),
-    pinned with DG_GEMM_SPLIT, gives the CUDA-core FP32 smoothing step to TF32 accuracy. N = 8 offers
-    every split (40 K chunks of 32); 8^3 elements give classes of 216 subdomains (one 256-wide tile)
-    and 4^3 classes of at most 8."""
+    through distributed shared memory) at every tile width (64 columns; 256 columns: 16 + split; 128
+    columns: 32 + split), pinned with DG_GEMM_SPLIT, gives the CUDA-core FP32 smoothing step to TF32
+    accuracy. N = 8 offers every split (40 K chunks of 32); 8^3 elements give classes of up to 96
+    subdomains in one 128- or 256-wide tile, 4^3 classes of at most 24."""
     N, ov = 8, 2
     grid = box(n, N)
     b = torch.from_numpy(rand(83, (grid.n_elements * N**3,))).cuda()
     u0 = torch.from_numpy(rand(84, (grid.n_elements * N**3,))).cuda()
     ref = dgg.Domain(n=n, N=N, mg_levels=1, overlap=ov, precision="mixed", gemm="simt")
     du_s = ref.schwarz_smooth(0, b, u0.clone(), 1).cpu().numpy() - u0.cpu().numpy()
-    for split in (1, 2, 4, 8, 16, 17, 18, 20, 24):
+    for split in (1, 2, 4, 8, 16, 17, 18, 20, 24, 32, 33, 34, 36, 40):
         monkeypatch.setenv("DG_GEMM_SPLIT", str(split))
         d = dgg.Domain(n=n, N=N, mg_levels=1, overlap=ov, precision="mixed", gemm="tf32")
         du_t = d.schwarz_smooth(0, b, u0.clone(), 1).cpu().numpy() - u0.cpu().numpy()
