@@ -264,10 +264,47 @@ def served_run(dgg, workloads, duration, rate=200.0, seed=5, max_active=8, preci
             "precision": "mixed (TF32 subdomain GEMM, FP64 FGMRES)" if precision == "mixed" else "fp64"}
 
 
+def served_capacity(dgg, workloads, count=400, seed=5, max_active=8):
+    """Service capacity of the server on the served stream's mix: the first `count` requests of the
+    arrival stream submitted at once (every shape warmed first, as in served_run), solves/s until the
+    last one completes. The timed window of served_run cannot exceed its arrival rate; this is the
+    rate the server would sustain under a heavier stream."""
+    import time as _t
+
+    arr = workloads.poisson_arrivals(seed, 200.0, 20.0)[:count]
+    reqs = build_requests(dgg, workloads, [(k, n, N, rs) for _, k, n, N, rs in arr])
+    srv = dgg.Server(max_active=max_active, n_streams=max_active, queue_capacity=1 << 20)
+    seen, first = set(), []
+    for (_, k, n, N, _), rq in zip(arr, reqs):
+        if (k, n, N) not in seen:
+            seen.add((k, n, N))
+            first.append(rq)
+    for _ in range(2):
+        tks = [srv.submit(d, f, tol=TOL) for d, f in first]
+        for tk in tks:
+            while srv.poll(tk)[0] == 1:
+                _t.sleep(0.0005)
+    t0 = srv.clock()
+    tks = [srv.submit(d, f, tol=TOL) for d, f in reqs]
+    ok = 0
+    for tk in tks:
+        while True:
+            st, _ = srv.poll(tk)
+            if st != 1:
+                ok += st == 0
+                break
+            _t.sleep(0.0005)
+    total = srv.clock() - t0
+    srv.close()
+    return {"requests": count, "solves_per_s": count / total, "ok": ok, "max_active": max_active,
+            "timing": "all requests submitted at once, host wall clock to the last completion"}
+
+
 def served_compare(dgg, workloads, duration, prefix, streams=8):
     """The served stream in MIXED precision, and the first `prefix` seconds of arrivals in both
     precisions (the plain FP64 solver on the same requests, for the mixed/FP64 throughput ratio)."""
     out = served_run(dgg, workloads, duration, max_active=streams)
+    out["capacity"] = served_capacity(dgg, workloads, max_active=streams)
     if prefix > 0:
         m = served_run(dgg, workloads, prefix, max_active=streams)
         f = served_run(dgg, workloads, prefix, precision="fp64", max_active=streams)
@@ -577,11 +614,6 @@ def run_ours(args):
             dist.barrier()
 
     cpu_proc, cpu_threads = None, 0
-    if rank == 0 and not args.no_cpu:
-        # the oracle sample runs in its own interpreter beside the GPU legs, on all host cores but
-        # four (which stay with this process's launch threads)
-        cpu_threads = max(1, oracle_threads() - 4)
-        cpu_proc = start_cpu_sample(2, 420.0, cpu_threads)
 
     stream = torch.cuda.Stream()
     src = workloads.gaussian_source(2)
@@ -768,6 +800,11 @@ def run_ours(args):
     curv = (curved_compare(dgg, workloads, torch, stream, args.curved_steps)
             if args.curved_steps > 0 and rank == 0 else None)
 
+    if rank == 0 and not args.no_cpu:
+        # the oracle sample runs in its own interpreter after the GPU legs, on all host cores: beside
+        # them its BLAS threads would compete with the server's and the host-driven solves' threads
+        cpu_threads = oracle_threads()
+        cpu_proc = start_cpu_sample(2, 420.0, cpu_threads)
     cpu = finish_cpu_sample(cpu_proc, cpu_threads) if cpu_proc is not None else None
     if cpu is not None:
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
