@@ -221,6 +221,14 @@ enum { DG_NOALLOC_MAX_VECTORS = 64 };
 dg_status dg_dot_noalloc(int64_t n, int32_t m, const double* V, int64_t ld, const double* w, double* out,
                          void* stream);
 
+/* Debug builds only (the library compiled with index bounds checks: libdg_elliptic_debug.so, from
+ * `python paper_2111_06767_gb300/build.py --debug`): the indices the kernels take from set-up
+ * tables (subdomain point maps, orientation and column maps) are checked before use, an index out
+ * of range is skipped instead of used, and the first offending kernel source line is recorded. The
+ * call synchronises the current device, returns that line (0: no index was out of range since the
+ * last call) and clears it; -1 in a release build, which has no checks. Not in the paper. */
+int32_t dg_debug_bounds_check(void);
+
 /* PUNCTURE: r = b - A(u) with A(u) = A u + M S(u), S(u) = -beta (1 + alpha (1 + u))^-7. */
 dg_status dg_nonlinear_residual(struct dg_domain* dom, const double* u, const double* b, double* r, void* stream);
 /* PUNCTURE: linearize at u (Eq. linearized): dg_apply then applies A + M diag(S'(u)). NULL clears. */

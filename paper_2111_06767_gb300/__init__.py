@@ -105,6 +105,12 @@ def solve_opts(max_iterations=200, precondition=2, linear_tol=1e-4, max_newton_s
                              int(relative_to_b), KRYLOV[krylov], SUBDOMAIN_SOLVERS[subdomain_solver])
 
 
+def debug_bounds_check():
+    """First kernel source line whose set-up-table index was out of range since the last call (0: none),
+    in the bounds-checked build (DG_DEBUG_BUILD=1); -1 in the release build."""
+    return int(_lib.dg_debug_bounds_check())
+
+
 @dataclasses.dataclass
 class SolveReport:
     status: int

@@ -7,7 +7,9 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdg_elliptic.so")
+# DG_DEBUG_BUILD=1 loads the bounds-checked build (paper_2111_06767_gb300/build.py --debug) instead
+LIB_PATH = os.path.join(_HERE, "libdg_elliptic_debug.so" if os.environ.get("DG_DEBUG_BUILD") == "1"
+                        else "libdg_elliptic.so")
 
 DG_OK, DG_PENDING = 0, 1
 DG_ERR_CANCELLED = -9
@@ -92,6 +94,7 @@ SIGNATURES = {
     "dg_vcycle": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_dot": (C.c_int, [_vp, _i32, _vp, C.c_int64, _vp, _vp, _vp]),
     "dg_dot_noalloc": (C.c_int, [C.c_int64, _i32, _vp, C.c_int64, _vp, _vp, _vp]),
+    "dg_debug_bounds_check": (_i32, []),
     "dg_nonlinear_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dg_set_linearization": (C.c_int, [_vp, _vp, _vp]),
     "dg_set_subdomain_solver": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp]),
@@ -132,7 +135,8 @@ def load(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"{path} is missing: build it with `python paper_2111_06767_gb300/build.py`")
+        raise ImportError(f"{path} is missing: build it with `python paper_2111_06767_gb300/build.py`"
+                          + (" --debug" if path.endswith("_debug.so") else ""))
     lib = C.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

@@ -2,6 +2,8 @@
 // thrown by the setup/orchestration code into dg_status codes with a per-handle message.
 #include <atomic>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "domain.h"
 
@@ -67,6 +69,20 @@ void check_level(const dg_domain* dom, int level) {
 
 }  // namespace
 
+namespace dg {
+// readers of the per-module bounds-check words (debug builds; see bounds.cuh)
+std::vector<int (*)()>& oob_readers() {
+  static std::vector<int (*)()> r;
+  return r;
+}
+int register_oob_reader(int (*reader)()) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  oob_readers().push_back(reader);
+  return (int)oob_readers().size();
+}
+}  // namespace dg
+
 extern "C" {
 
 dg_status dg_domain_create(const dg_domain_desc* desc, void* cuda_stream, dg_domain** out) {
@@ -108,6 +124,20 @@ void dg_domain_destroy(dg_domain* dom) {
   cudaStream_t s = dom->own_stream ? dom->stream : nullptr;
   delete dom;
   if (s) cudaStreamDestroy(s);
+}
+
+int32_t dg_debug_bounds_check(void) {
+#ifdef DG_BOUNDS_CHECK
+  if (cudaDeviceSynchronize() != cudaSuccess) return 0;
+  int first = 0;
+  for (auto reader : dg::oob_readers()) {
+    const int line = reader();
+    if (line && !first) first = line;
+  }
+  return first;
+#else
+  return -1;
+#endif
 }
 
 const char* dg_last_error(const dg_domain* dom) {

@@ -32,6 +32,7 @@
 #include <set>
 #include <type_traits>
 
+#include "bounds.cuh"
 #include "internal.h"
 #include "lines.cuh"
 #include "pdl.cuh"
@@ -369,10 +370,11 @@ __device__ __forceinline__ void apply_line_block(const ApplyArgs<T>& A, int blk)
     }
     int rows[N];
     gld_line<N>(inv + s_map[el][sl] + t * N, rows);
+    if (!DG_IN_BOUNDS(c, E)) continue;
     T* colp = rS + (int64_t)c * ld;
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      if (i >= lo && i < hi && rows[i] >= 0) colp[rows[i]] = val[i];
+      if (i >= lo && i < hi && rows[i] >= 0 && DG_IN_BOUNDS(rows[i], ld)) colp[rows[i]] = val[i];
   }
 }
 
@@ -1410,10 +1412,11 @@ __device__ __forceinline__ void blk_phase_z(const ApplyArgs<float>& A, const Blk
       }
       int rows[N];
       gld_line<N>(A.inv + s_map[sl] + t * N, rows);
+      if (!DG_IN_BOUNDS(col, A.E)) continue;
       float* colp = A.rS + (int64_t)col * A.ld;
 #pragma unroll
       for (int i = 0; i < N; ++i)
-        if (i >= lo && i < hi && rows[i] >= 0) colp[rows[i]] = val[i];
+        if (i >= lo && i < hi && rows[i] >= 0 && DG_IN_BOUNDS(rows[i], A.ld)) colp[rows[i]] = val[i];
     }
   }
 }

@@ -4,6 +4,7 @@
 // calling CTA (any block size of at least 32) and may be called back to back on the same CTA.
 #pragma once
 
+#include "bounds.cuh"
 #include "internal.h"
 #include "pdl.cuh"
 
@@ -63,8 +64,10 @@ __device__ __forceinline__ void gather_column(const SubdomainGeom& g, const T* _
     int64_t src = -1;
     if (q < nS) {
       const int code = __ldg(m + q);
-      const int el = nb[code >> 16];
-      if (el >= 0) src = (int64_t)el * N3 + (code & 0xFFFF);
+      const int sl = code >> 16;
+      const int el = DG_IN_BOUNDS(sl, 7) ? nb[sl] : -1;
+      if (el >= 0 && DG_IN_BOUNDS((int64_t)el * N3 + (code & 0xFFFF), (int64_t)g.E * N3))
+        src = (int64_t)el * N3 + (code & 0xFFFF);
     }
     if constexpr (PDL) {
       if (first) pdl_wait();
@@ -123,7 +126,8 @@ __device__ __forceinline__ void scatter_element(const SubdomainGeom& g, const T*
           in = in && ((f & 1) ? g.N - 1 - cd : cd) < g.ov;
         }
         const int row = in ? __ldg(inv + s_inv[sl] + p) : -1;
-        idx[sl] = row >= 0 ? (int64_t)s_col[sl] * ld + row : -1;
+        idx[sl] = row >= 0 && DG_IN_BOUNDS(row, ld) && DG_IN_BOUNDS(s_col[sl], g.E) ? (int64_t)s_col[sl] * ld + row
+                                                                                   : -1;
         w[sl] = row >= 0 ? sh[sl] : T(0);
       }
     }

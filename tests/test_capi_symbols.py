@@ -28,3 +28,12 @@ def test_binding_declares_exactly_the_header():
     from paper_2111_06767_gb300 import _native
 
     assert sorted(_native.SIGNATURES) == declared_functions()
+
+
+def test_release_build_has_no_bounds_checks():
+    """dg_debug_bounds_check() answers -1 in the release build without touching the GPU."""
+    import ctypes
+
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2111_06767_gb300", "libdg_elliptic.so"))
+    lib.dg_debug_bounds_check.restype = ctypes.c_int32
+    assert lib.dg_debug_bounds_check() == -1
