@@ -107,6 +107,25 @@ __device__ __forceinline__ T face_point(T s, T ui, T gi, T ue, T ge, bool has, b
   return gi + s * jump * lift;
 }
 
+// y[i] += d x[i] along a line: in FP32 as packed two-wide FMAs on pairs of points (one instruction
+// per pair, same rounding as the scalar FMA), in FP64 scalar.
+template <int N, typename T>
+__device__ __forceinline__ void axpy_line(T d, const T (&x)[N], T (&y)[N]) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float2 dd = make_float2(d, d);
+#pragma unroll
+    for (int i = 0; i + 1 < N; i += 2) {
+      const float2 r = __ffma2_rn(dd, make_float2(x[i], x[i + 1]), make_float2(y[i], y[i + 1]));
+      y[i] = r.x;
+      y[i + 1] = r.y;
+    }
+    if constexpr (N % 2 == 1) y[N - 1] += d * x[N - 1];
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] += d * x[i];
+  }
+}
+
 // One group of EPB elements (block index blk) of the DG apply, for the kernel below and for the
 // fused coarse-level smoother; with PDL the set-up before the first read of u overlaps the
 // previous kernel on the stream.
@@ -241,14 +260,12 @@ __device__ __forceinline__ void apply_line_block(const ApplyArgs<T>& A, int blk)
 #pragma unroll
   for (int l = 0; l < N; ++l) {
     sld_line<N>(&sm[0][el][k * P + l * N], tmp);
-#pragma unroll
-    for (int i = 0; i < N; ++i) vy[i] += Dj[l] * tmp[i];
+    axpy_line<N>(Dj[l], tmp, vy);
   }
 #pragma unroll
   for (int l = 0; l < N; ++l) {
     sld_line<N>(&sm[0][el][l * P + j * N], tmp);
-#pragma unroll
-    for (int i = 0; i < N; ++i) vz[i] += Dk[l] * tmp[i];
+    axpy_line<N>(Dk[l], tmp, vz);
   }
   // x faces in registers: lifting into v_x at i = 0 and N-1, primal flux into o
   T o[N];
@@ -322,14 +339,12 @@ __device__ __forceinline__ void apply_line_block(const ApplyArgs<T>& A, int blk)
 #pragma unroll
   for (int l = 0; l < N; ++l) {
     sld_line<N>(&sm[1][el][k * P + l * N], tmp);
-#pragma unroll
-    for (int i = 0; i < N; ++i) dy[i] += Dj[l] * tmp[i];
+    axpy_line<N>(Dj[l], tmp, dy);
   }
 #pragma unroll
   for (int l = 0; l < N; ++l) {
     sld_line<N>(&sm[2][el][l * P + j * N], tmp);
-#pragma unroll
-    for (int i = 0; i < N; ++i) dz[i] += Dk[l] * tmp[i];
+    axpy_line<N>(Dk[l], tmp, dz);
   }
   if (!valid) return;
   const int64_t base = (int64_t)ec * N3 + line;
@@ -1140,8 +1155,7 @@ __device__ __forceinline__ void blk_phase_y(const ApplyArgs<float>& A, const Blk
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
       const float d = ok(jj) ? C::D(dO + (J0 + jj) * N + l) : 0.f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) vy[jj][i] += d * t[i];
+      axpy_line<N>(d, t, vy[jj]);
     }
   }
 #pragma unroll
@@ -1224,8 +1238,7 @@ __device__ __forceinline__ void blk_phase_y(const ApplyArgs<float>& A, const Blk
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
       const float d = ok(jj) ? C::D(dO + (J0 + jj) * N + l) : 0.f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) dy[jj][i] += d * t[i];
+      axpy_line<N>(d, t, dy[jj]);
     }
   }
   if (act) {
@@ -1275,8 +1288,7 @@ __device__ __forceinline__ void blk_phase_z(const ApplyArgs<float>& A, const Blk
 #pragma unroll
     for (int kk = 0; kk < NK; ++kk) {
       const float d = ok(kk) ? C::D(dO + (K0 + kk) * N + l) : 0.f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) vz[kk][i] += d * t[i];
+      axpy_line<N>(d, t, vz[kk]);
     }
   }
 #pragma unroll
@@ -1361,8 +1373,7 @@ __device__ __forceinline__ void blk_phase_z(const ApplyArgs<float>& A, const Blk
 #pragma unroll
     for (int kk = 0; kk < NK; ++kk) {
       const float d = ok(kk) ? C::D(dO + (K0 + kk) * N + l) : 0.f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) dz[kk][i] += d * t[i];
+      axpy_line<N>(d, t, dz[kk]);
     }
   }
   if (!store) return;
