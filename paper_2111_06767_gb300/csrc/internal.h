@@ -52,7 +52,8 @@ const char* null_handle_error();
 cudaStream_t alloc_stream();
 // Programmatic dependent launch for the launches made on this thread while a scope with on = true
 // is alive (pdl_enabled() in pdl.cuh); pdl_vcycle_mode(): which FP32 V-cycle launches open one
-// (DG_PDL_COARSE: 0 none, 1 the coarse levels' smoothing, 2 every level and the transfers).
+// (DG_PDL_COARSE: 0 none, 1 the coarse levels' smoothing, 2 every level and the transfers, 3 the
+// coarse levels and the fine level's scatter).
 struct PdlScope {
   bool on;
   explicit PdlScope(bool on_);

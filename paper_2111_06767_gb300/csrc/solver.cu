@@ -400,6 +400,8 @@ void schwarz_smooth(dg_domain* dom, int level, const T* b, T* u, int iterations,
       }
     }
     {
+      // mode 3: the fine level's scatter also overlaps the GEMM before it
+      const PdlScope pdl_scatter(sizeof(T) == 4 && level == 0 && pdl_vcycle_mode() == 3);
       PhaseScope ps(dom->prof, DG_PHASE_SCATTER, s, vec + 2.0 * L.ndof * sz, 0.0);
       launch_scatter_tab<T, T>(sw.geom, W.duS.get(), sw.col_of_elem.get(), sw.xform_of_elem.get(),
                                dom->orient_inv.get(), shares<T>(dom), u, s);
