@@ -1070,7 +1070,7 @@ __device__ __forceinline__ BlkElem blk_elem(const OpGeom<float>& g, int ec, int 
 // the block are read from constant memory with a warp-uniform index.
 template <int N, int B, int EPB>
 __device__ __forceinline__ void blk_phase_y(const ApplyArgs<float>& A, const BlkElem& c, int jb, int k, bool act,
-                                            float* us, float* vs, float* ps) {
+                                            int el, float* us, float* vs, float* ps) {
   using S = BlkShape<N, B, EPB>;
   using C = CTab<float>;
   constexpr int N2 = N * N, dO = dtab_off(N), wO = wtab_off(N);
@@ -1081,33 +1081,47 @@ __device__ __forceinline__ void blk_phase_y(const ApplyArgs<float>& A, const Blk
   const OpGeom<float>& g = A.g;
   const float* __restrict__ u = A.u;
   const float wk = C::w(wO + k);  // k is a runtime index: one constant-cache read per thread
+  // the CTA's elements (a contiguous run) into their padded shared blocks, with coalesced loads by
+  // all threads (a thread's own lines are 128-byte runs one plane apart, so loading them per
+  // thread would touch a separate line per lane); past the last element, element E - 1 again
+  {
+    constexpr int N3 = N2 * N, VE = LineVec<N, float>::per;  // values per vector move
+    using V = typename LineVec<N, float>::V;
+    const int e0 = blockIdx.x * EPB;
+    float* us0 = us - el * S::ES;  // the first element's block
+    for (int idx = threadIdx.x; idx < EPB * N3 / VE; idx += S::THREADS) {
+      const int el2 = idx / (N3 / VE), o = (idx - el2 * (N3 / VE)) * VE;
+      const int e2 = min(e0 + el2, A.E - 1);
+      const V v = *reinterpret_cast<const V*>(u + (int64_t)e2 * N3 + o);
+      *reinterpret_cast<V*>(us0 + el2 * S::ES + (o / N2) * S::PS + ((o / N) % N) * S::LS + o % N) = v;
+    }
+  }
+  __syncthreads();  // every element is staged
   float U[NJ][N];
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
     if (ok(jj)) {
-      gld_line<N>(u + c.base + k * N2 + (J0 + jj) * N, U[jj]);
+      sld_line<N>(us + k * S::PS + (J0 + jj) * S::LS, U[jj]);
     } else {
 #pragma unroll
       for (int i = 0; i < N; ++i) U[jj][i] = 0.f;
     }
   }
-  if (act) {
-#pragma unroll
-    for (int jj = 0; jj < NJ; ++jj)
-      if (ok(jj)) sst_line<N>(us + k * S::PS + (J0 + jj) * S::LS, U[jj]);
-  }
   // x: neighbour traces, gradient, lifting, face fluxes and divergence in registers, line by line;
-  // the result goes to the partial-result buffer
+  // the result goes to the partial-result buffer. An x-neighbour inside the CTA's run is read from
+  // its staged block (where it is not the element's neighbour, the face uses the ghost state).
 #pragma unroll
   for (int jj = 0; jj < NJ; ++jj) {
     if (!ok(jj)) continue;
     float t[N];
-    gld_line<N>(u + (int64_t)c.nb[0] * N2 * N + k * N2 + (J0 + jj) * N, t);
+    if (el > 0) sld_line<N>(us - S::ES + k * S::PS + (J0 + jj) * S::LS, t);
+    else gld_line<N>(u + (int64_t)c.nb[0] * N2 * N + k * N2 + (J0 + jj) * N, t);
     const float uxm = t[N - 1];
     float gxm = 0.f;
 #pragma unroll
     for (int l = 0; l < N; ++l) gxm += C::D(dO + (N - 1) * N + l) * t[l];
-    gld_line<N>(u + (int64_t)c.nb[1] * N2 * N + k * N2 + (J0 + jj) * N, t);
+    if (el + 1 < EPB) sld_line<N>(us + S::ES + k * S::PS + (J0 + jj) * S::LS, t);
+    else gld_line<N>(u + (int64_t)c.nb[1] * N2 * N + k * N2 + (J0 + jj) * N, t);
     const float uxp = t[0];
     float gxp = 0.f;
 #pragma unroll
@@ -1476,7 +1490,7 @@ __global__ void __launch_bounds__(BlkShape<N, B, EPB>::THREADS) apply_blk_kernel
       s_map[el2][sl] = m;
     }
   }
-  blk_phase_y<N, B, EPB>(A, c, grp, q, act, us, vs, ps);
+  blk_phase_y<N, B, EPB>(A, c, grp, q, act, el, us, vs, ps);
   __syncthreads();  // the partial results (and the subdomain tables) are in shared memory
   const bool store = act && e < A.E;
   blk_phase_z<N, B, EPB>(A, c, grp, q, act, store, us, vs, ps, s_col[el], s_map[el]);
