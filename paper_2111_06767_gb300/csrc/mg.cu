@@ -5,7 +5,8 @@
 // (the child spans the parent in that dimension). Restriction R = P^T (no mass matrices, since
 // it acts on DG residuals that already carry them). Both are sum-factorised: three 1-D passes of
 // N^4 work per element, one CTA per element (at most 512 threads), data staged in shared memory. The restriction
-// gathers its (up to 8) children in a fixed order: deterministic, no atomics.
+// gathers its (up to 8) children in a fixed order: deterministic, no atomics; up to N = 8 (one
+// point per thread) it reads all children's values before the first pass.
 #include "internal.h"
 #include "pdl.cuh"
 
@@ -93,41 +94,66 @@ __global__ void __launch_bounds__(XferShape<N>::threads) restrict_kernel(XferGeo
   for (int t = tid; t < N3; t += NT) sacc[t] = T(0);
   const int px = ec % x.nc[0], py = (ec / x.nc[0]) % x.nc[1], pz = ec / (x.nc[0] * x.nc[1]);
   const int rx = x.nf[0] == x.nc[0] ? 1 : 2, ry = x.nf[1] == x.nc[1] ? 1 : 2, rz = x.nf[2] == x.nc[2] ? 1 : 2;
+  const int nch = rx * ry * rz;
+  // child c (x fastest) of the parent: its element index and the half it occupies per dimension
+  auto child = [&](int c, int& ef, int& hx, int& hy, int& hz) {
+    const int dx = c % rx, dy = (c / rx) % ry, dz = c / (rx * ry);
+    const int cx = rx == 2 ? 2 * px + dx : px, cy = ry == 2 ? 2 * py + dy : py, cz = rz == 2 ? 2 * pz + dz : pz;
+    hx = rx == 2 ? dx : 2;
+    hy = ry == 2 ? dy : 2;
+    hz = rz == 2 ? dz : 2;
+    ef = cx + x.nf[0] * (cy + x.nf[1] * cz);
+  };
   pdl_launch_dependents();
   pdl_wait();
-  for (int dz = 0; dz < rz; ++dz)
-    for (int dy = 0; dy < ry; ++dy)
-      for (int dx = 0; dx < rx; ++dx) {
-        const int cx = rx == 2 ? 2 * px + dx : px, cy = ry == 2 ? 2 * py + dy : py, cz = rz == 2 ? 2 * pz + dz : pz;
-        const int hx = rx == 2 ? dx : 2, hy = ry == 2 ? dy : 2, hz = rz == 2 ? dz : 2;
-        const int ef = cx + x.nf[0] * (cy + x.nf[1] * cz);
-        __syncthreads();
-        for (int t = tid; t < N3; t += NT) s0[t] = rf[(int64_t)ef * N3 + t];
-        __syncthreads();
-        for (int t = tid; t < N3; t += NT) {  // s1[k][j][a] = sum_i Ix[i][a] r[k][j][i]
-          const int i = t % N, j = (t / N) % N, k = t / N2;
-          T a = 0;
+  // one point per thread (N <= 8): every child's value is read up front, so the children cost one
+  // round trip to memory instead of one each
+  constexpr bool kPre = N3 <= NT;
+  T pre[8];
+  if constexpr (kPre) {
 #pragma unroll
-          for (int l = 0; l < N; ++l) a += interp<N, T>(sI, hx, l, i) * s0[(k * N + j) * N + l];
-          s1[t] = a;
-        }
-        __syncthreads();
-        for (int t = tid; t < N3; t += NT) {  // s0[k][b][a] = sum_j Iy[j][b] s1[k][j][a]
-          const int i = t % N, j = (t / N) % N, k = t / N2;
-          T a = 0;
+    for (int c = 0; c < 8; ++c) {
+      int ef, hx, hy, hz;
+      child(c < nch ? c : 0, ef, hx, hy, hz);
+      pre[c] = c < nch && tid < N3 ? rf[(int64_t)ef * N3 + tid] : T(0);
+    }
+  }
 #pragma unroll
-          for (int l = 0; l < N; ++l) a += interp<N, T>(sI, hy, l, j) * s1[(k * N + l) * N + i];
-          s0[t] = a;
-        }
-        __syncthreads();
-        for (int t = tid; t < N3; t += NT) {  // sum_k Iz[k][c] s0[k][b][a]
-          const int i = t % N, j = (t / N) % N, k = t / N2;
-          T a = 0;
+  for (int c = 0; c < 8; ++c) {
+    if (c >= nch) break;
+    int ef, hx, hy, hz;
+    child(c, ef, hx, hy, hz);
+    __syncthreads();
+    if constexpr (kPre) {
+      if (tid < N3) s0[tid] = pre[c];
+    } else {
+      for (int t = tid; t < N3; t += NT) s0[t] = rf[(int64_t)ef * N3 + t];
+    }
+    __syncthreads();
+    for (int t = tid; t < N3; t += NT) {  // s1[k][j][a] = sum_i Ix[i][a] r[k][j][i]
+      const int i = t % N, j = (t / N) % N, k = t / N2;
+      T a = 0;
 #pragma unroll
-          for (int l = 0; l < N; ++l) a += interp<N, T>(sI, hz, l, k) * s0[(l * N + j) * N + i];
-          sacc[t] += a;
-        }
-      }
+      for (int l = 0; l < N; ++l) a += interp<N, T>(sI, hx, l, i) * s0[(k * N + j) * N + l];
+      s1[t] = a;
+    }
+    __syncthreads();
+    for (int t = tid; t < N3; t += NT) {  // s0[k][b][a] = sum_j Iy[j][b] s1[k][j][a]
+      const int i = t % N, j = (t / N) % N, k = t / N2;
+      T a = 0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a += interp<N, T>(sI, hy, l, j) * s1[(k * N + l) * N + i];
+      s0[t] = a;
+    }
+    __syncthreads();
+    for (int t = tid; t < N3; t += NT) {  // sum_k Iz[k][c] s0[k][b][a]
+      const int i = t % N, j = (t / N) % N, k = t / N2;
+      T a = 0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) a += interp<N, T>(sI, hz, l, k) * s0[(l * N + j) * N + i];
+      sacc[t] += a;
+    }
+  }
   __syncthreads();
   for (int t = tid; t < N3; t += NT) bc[(int64_t)ec * N3 + t] = sacc[t];
 }
